@@ -1,0 +1,342 @@
+"""Pins of the FP64 oracle against closed forms, the paper's printed numbers,
+invariants and a brute-force dense solve -- nothing here compares the oracle
+with itself.  CPU only."""
+import numpy as np
+import pytest
+
+from paper_2211_08263_gb300 import inputs
+from oracle import analytic, dense, green, medium, newmark, pcg, spectral
+
+rel = lambda a, b: float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+# --------------------------------------------------------------------------
+# spectral derivative and operator assembly
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N", [6, 7, 8, 9, 16])
+def test_closed_form_diff_matrix_differentiates_trig_exactly(N):
+    """The closed-form matrix differentiates every resolved Fourier mode exactly
+    (and kills the Nyquist cosine, the even-N reading)."""
+    L = 1.7
+    x = (np.arange(N) + 0.5) * L / N
+    D = dense.diff_matrix_1d(N, L)
+    for m in range(1, (N - 1) // 2 + 1):
+        k = 2 * np.pi * m / L
+        assert np.allclose(D @ np.sin(k * x), k * np.cos(k * x), atol=1e-12 * k)
+        assert np.allclose(D @ np.cos(k * x), -k * np.sin(k * x), atol=1e-12 * k)
+    if N % 2 == 0:
+        assert np.allclose(D @ np.cos(np.pi * N * x / L), 0.0, atol=1e-12)
+    assert np.allclose(D, -D.T)
+
+
+@pytest.mark.parametrize("N", [6, 7, 8, 64])
+def test_fft_derivative_equals_closed_form_matrix(N):
+    rng = np.random.default_rng(N)
+    f = rng.standard_normal(N)
+    med = medium.Medium(1, (N,), (2.0,), np.ones((1, 1, 1, 1, 1)), np.zeros(N, np.int64), np.ones(N))
+    sp = spectral.Spectral(med)
+    assert np.allclose(sp.deriv(f, 0), dense.diff_matrix_1d(N, 2.0) @ f, atol=1e-12 * N)
+
+
+CASES = [(2, (8, 6, 1)), (2, (7, 9, 1)), (3, (6, 5, 4)), (3, (4, 4, 4)), (3, (5, 4, 1))]
+
+
+@pytest.mark.parametrize("d,n", CASES)
+def test_fft_operator_equals_dense_operator(d, n):
+    """Eq. Fourier_ND_A via FFTs equals the FFT-free assembled matrix."""
+    rng = np.random.default_rng(sum(n) + d)
+    prob = inputs.random_problem(rng, d, n, nphase=3)
+    med = medium.medium_from_problem(prob)
+    sp = spectral.Spectral(med)
+    th = 0.25 * prob.dt ** 2
+    A = dense.dense_operator(med, th)
+    u = rng.standard_normal((d,) + med.shape)
+    assert rel(spectral.apply_A(med, sp, u, th).reshape(-1), A @ u.reshape(-1)) < 1e-13
+
+
+@pytest.mark.parametrize("d,n", CASES[:3])
+def test_operator_symmetric_positive_definite(d, n):
+    rng = np.random.default_rng(7 + d)
+    prob = inputs.random_problem(rng, d, n, nphase=4, contrast=6.0)
+    med = medium.medium_from_problem(prob)
+    sp = spectral.Spectral(med)
+    th = 0.25 * (10 * prob.dt) ** 2
+    for _ in range(3):
+        x = rng.standard_normal((d,) + med.shape)
+        y = rng.standard_normal((d,) + med.shape)
+        Ax, Ay = spectral.apply_A(med, sp, x, th), spectral.apply_A(med, sp, y, th)
+        assert abs(np.vdot(y, Ax) - np.vdot(x, Ay)) <= 1e-13 * abs(np.vdot(x, Ax))
+        assert np.vdot(x, Ax) > 0
+
+
+def test_voigt_tensor_has_no_shear_factor():
+    """C_ijkl = Cv[voigt(ij), voigt(kl)] and isotropic C gives sigma = lam tr(e) I + 2 mu e."""
+    lam, mu = 50e9, 30e9
+    C = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(inputs.isotropic_lame_voigt(lam, mu)))
+    rng = np.random.default_rng(0)
+    e = rng.standard_normal((3, 3))
+    e = 0.5 * (e + e.T)
+    sig = np.einsum("ijkl,kl->ij", C, e)
+    assert np.allclose(sig, lam * np.trace(e) * np.eye(3) + 2 * mu * e, rtol=1e-14, atol=0)
+
+
+# --------------------------------------------------------------------------
+# preconditioner
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,aniso", [(2, False), (3, False), (3, True)])
+def test_preconditioner_is_exact_inverse_for_homogeneous_medium(d, aniso):
+    """Eq. precond is the exact solution operator of a homogeneous medium
+    (Eq. A_oper_inv_homog in 1-D): M A u = u, and masked-free PCG stops after 1 iteration."""
+    rng = np.random.default_rng(3)
+    if aniso:
+        Cv = inputs.rotate_voigt(inputs.cubic_voigt(*inputs.NI_CUBIC), inputs.random_rotations(rng, 1)[0])
+    else:
+        Cv = inputs.isotropic_voigt(200e9, 0.3)
+    C = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(Cv))
+    shape = (6, 8) if d == 2 else (4, 6, 8)
+    med = medium.homogeneous_medium(d, shape, (6e-3, 8e-3, 4e-3)[:d][::-1][::-1], C, 7800.0)
+    sp = spectral.Spectral(med)
+    th = 0.25 * (4e-7) ** 2
+    u = rng.standard_normal((d,) + shape)
+    Au = spectral.apply_A(med, sp, u, th)
+    assert rel(spectral.apply_M(med, sp, Au, th), u) < 1e-13
+    mask = np.zeros((d,) + shape, bool)
+    x, info = pcg.masked_pcg(lambda v: spectral.apply_A(med, sp, v, th),
+                             lambda v: spectral.apply_M(med, sp, v, th), Au, np.zeros_like(u), mask,
+                             np.zeros_like(u), 1e-12)
+    assert info["iters"] == 1 and rel(x, u) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# plane waves: operator symbol + Newmark against closed forms
+# --------------------------------------------------------------------------
+
+def test_cubic_christoffel_matches_textbook_speeds():
+    c11, c12, c44 = inputs.NI_CUBIC
+    rho = inputs.NI_RHO
+    C = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(inputs.cubic_voigt(c11, c12, c44)))
+    ref = analytic.cubic_speeds(c11, c12, c44, rho)
+    dirs = {"100": [1, 0, 0], "110": [1, 1, 0], "111": [1, 1, 1]}
+    rng = np.random.default_rng(5)
+    R = inputs.random_rotations(rng, 1)[0]
+    Cr = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(inputs.rotate_voigt(inputs.cubic_voigt(c11, c12, c44), R)))
+    for k, dvec in dirs.items():
+        n = np.array(dvec, float) / np.linalg.norm(dvec)
+        w2, _ = analytic.christoffel(C, rho, n)
+        assert np.allclose(np.sort(w2), ref[k], rtol=1e-12)
+        w2r, _ = analytic.christoffel(Cr, rho, R @ n)  # rotated crystal, rotated direction
+        assert np.allclose(np.sort(w2r), ref[k], rtol=1e-12)
+
+
+@pytest.mark.parametrize("d,aniso,pol", [(2, False, 0), (2, False, 1), (3, False, 2), (3, True, 0), (3, True, 1)])
+def test_plane_wave_follows_discrete_newmark_closed_form(d, aniso, pol):
+    """u_0 = a cos(xi.x) on a grid wave vector, v_0 = 0, a_0 = -omega^2 u_0:
+    beta-Newmark gives u_n = u_0 cos(n phi) exactly (cos phi closed form)."""
+    rng = np.random.default_rng(11)
+    if aniso:
+        Cv = inputs.rotate_voigt(inputs.cubic_voigt(*inputs.NI_CUBIC), inputs.random_rotations(rng, 1)[0])
+        rho = inputs.NI_RHO
+    else:
+        Cv, rho = inputs.isotropic_voigt(200e9, 0.3), 7800.0
+    C = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(Cv))
+    shape = (10, 8) if d == 2 else (6, 8, 10)
+    h = 1e-3
+    L = tuple(shape[::-1][i] * h for i in range(d))
+    med = medium.homogeneous_medium(d, shape, L, C, rho)
+    m = [2, 1, 1][:d]
+    xi = np.array([2 * np.pi * m[i] / L[i] for i in range(d)])
+    w2, vecs = analytic.christoffel(C, rho, xi)
+    a = vecs[:, pol]
+    grids = np.meshgrid(*[(np.arange(shape[::-1][i]) + 0.5) * h for i in range(d)][::-1], indexing="ij")
+    phase = sum(xi[i] * grids[d - 1 - i] for i in range(d))
+    u0 = np.stack([a[i] * np.cos(phase) for i in range(d)])
+    dt = 3e-7
+    nm = newmark.NewmarkOracle(med, np.zeros((d,) + shape, bool), dt, tol=1e-13)
+    s = newmark.State(u0.copy(), np.zeros_like(u0), -w2[pol] * u0)
+    cphi = analytic.newmark_cos_phi(np.sqrt(w2[pol]) * dt)
+    phi = np.arccos(cphi)
+    nsteps = 400 if d == 2 else 120
+    for n in range(1, nsteps + 1):
+        s, info = nm.step(s, np.zeros(3))
+        assert info["iters"] <= 2  # 1, or 2 when the mode passes near zero (rounding vs ref)
+    assert rel(s.u, u0 * np.cos(nsteps * phi)) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# energy invariant of undamped Newmark (beta = 1/4, gamma = 1/2)
+# --------------------------------------------------------------------------
+
+def test_energy_conserved_in_free_vibration():
+    rng = np.random.default_rng(21)
+    prob = inputs.random_problem(rng, 2, (12, 10, 1), nphase=3, mask_width=0, contrast=4.0)
+    nm = newmark.oracle_from_problem(prob, tol=1e-13)
+    med = nm.med
+    sp = nm.sp
+    h = prob.h[0]
+    filt = np.exp(-2.0 * h * h * (sp.xi[0] ** 2 + sp.xi[1] ** 2))  # band-limited, no rigid (DC) mode
+    filt.reshape(-1)[0] = 0.0
+    u0 = np.stack([sp.inv(sp.fwd(rng.standard_normal(med.shape)) * filt) for _ in range(2)]) * 1e-6
+    s = newmark.State(u0, np.zeros_like(u0), np.zeros_like(u0))
+    # consistent a_0 = -rho^-1 (A u_0 - rho u_0) / theta  (free vibration)
+    s.a = -(nm.A(u0) - med.rho[None] * u0) / nm.theta / med.rho[None]
+    E0 = nm.energy(s)
+    for _ in range(40):
+        s, _ = nm.step(s, np.zeros(3))
+    assert abs(nm.energy(s) - E0) <= 1e-10 * E0
+
+
+def test_energy_balance_with_prescribed_displacement():
+    """E_n - E_{n-1} = 1/2 (u_n - u_{n-1}) . (f_n + f_{n-1}), f = reaction on Gamma."""
+    rng = np.random.default_rng(22)
+    prob = inputs.random_problem(rng, 2, (12, 10, 1), nphase=3, mask_width=2, contrast=4.0, nsteps=12)
+    prob.U[:, 0] = 1e-6 * np.sin(np.linspace(0.2, 2.0, 12))
+    prob.U[:, 1] = 0.3e-6 * np.cos(np.linspace(0.2, 2.0, 12))
+    nm = newmark.oracle_from_problem(prob, tol=1e-13)
+    s = nm.zero_state()
+    f_prev = np.zeros_like(s.u)
+    E_prev = 0.0
+    worst = 0.0
+    for n in range(prob.nsteps):
+        ut, b = nm.predictor(s)
+        s_new, _ = nm.step(s, prob.U[n])
+        f = nm.reaction_field(s_new, b)
+        assert np.abs(np.where(nm.mask, 0, f)).max() <= 1e-8 * np.abs(f).max()
+        E = nm.energy(s_new)
+        work = 0.5 * np.vdot(s_new.u - s.u, f + f_prev)
+        worst = max(worst, abs((E - E_prev) - work) / max(abs(work), abs(E)))
+        s, f_prev, E_prev = s_new, f, E
+    assert worst < 1e-9
+
+
+# --------------------------------------------------------------------------
+# prescribed-displacement region: paper's Green's matrix vs masked PCG vs dense
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,n,width", [(2, (8, 8, 1), 2), (3, (6, 6, 6), 1)])
+def test_green_matrix_masked_pcg_and_dense_agree(d, n, width):
+    rng = np.random.default_rng(31 + d)
+    prob = inputs.random_problem(rng, d, n, nphase=3, mask_width=width, nsteps=3, contrast=4.0)
+    s1, infos = newmark.oracle_from_problem(prob, tol=1e-14).run(prob.U)
+    gr = green.GreenNewmark(newmark.oracle_from_problem(prob), tol=1e-15)
+    s2, forces = gr.run(prob.U)
+    s3 = dense.DenseNewmark(newmark.oracle_from_problem(prob)).run(prob.U)
+    assert rel(s1.u, s3.u) < 1e-12 and rel(s2.u, s3.u) < 1e-12
+    assert rel(s1.v, s3.v) < 1e-10 and rel(s1.a, s3.a) < 1e-10
+    # A is symmetric, so the Green's matrix is symmetric up to the PCG tolerance
+    assert np.abs(gr.G - gr.G.T).max() <= 1e-12 * np.abs(gr.G).max()
+    # Gamma forces of Eq. L-determination_ND sum to the momentum balance sum_x rho a_n
+    V = gr.nm.med.nvox
+    sumF = [forces[-1][gr.gam // V == j].sum() for j in range(d)]
+    assert np.allclose(sumF, infos[-1]["reaction"], rtol=1e-8)
+
+
+def test_plane_strain_equals_3d_with_singleton_axis():
+    rng = np.random.default_rng(41)
+    p2 = inputs.random_problem(rng, 2, (8, 6, 1), nphase=3, mask_width=2, nsteps=3, anisotropic=False)
+    s2, _ = newmark.oracle_from_problem(p2, tol=1e-14).run(p2.U)
+    mask3 = np.zeros((3, 1, 6, 8), np.uint8)
+    mask3[:2] = p2.mask
+    mask3[2, :, :, :2] = 1
+    p3 = inputs.Problem("p3", 3, (8, 6, 1), p2.h, p2.dt, 0.25, 0.5, p2.C, p2.rho, p2.phase, mask3,
+                        np.concatenate([p2.U[:, :2], np.zeros((3, 1))], 1))
+    s3, _ = newmark.oracle_from_problem(p3, tol=1e-14).run(p3.U)
+    assert rel(s3.u[:2, 0], s2.u) < 1e-13
+    assert np.abs(s3.u[2]).max() <= 1e-20
+
+
+def test_translation_and_linearity():
+    rng = np.random.default_rng(51)
+    prob = inputs.random_problem(rng, 3, (6, 5, 4), nphase=3, mask_width=2, nsteps=2)
+    s, _ = newmark.oracle_from_problem(prob, tol=1e-14).run(prob.U)
+    sh = inputs.Problem("sh", 3, prob.n, prob.h, prob.dt, 0.25, 0.5, prob.C, prob.rho,
+                        np.roll(prob.phase, 1, axis=-1), np.roll(prob.mask, 1, axis=-1), prob.U)
+    ss, _ = newmark.oracle_from_problem(sh, tol=1e-14).run(sh.U)
+    assert rel(ss.u, np.roll(s.u, 1, axis=-1)) < 1e-12
+    sc = inputs.Problem("sc", 3, prob.n, prob.h, prob.dt, 0.25, 0.5, prob.C, prob.rho, prob.phase, prob.mask,
+                        -2.5 * prob.U)
+    s2, _ = newmark.oracle_from_problem(sc, tol=1e-14).run(sc.U)
+    assert rel(s2.u, -2.5 * s.u) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# the paper's printed numbers
+# --------------------------------------------------------------------------
+
+AL = (70.3e9, 2700.0)
+
+
+def _bar_run(ratio):
+    E, rho = AL
+    L, N = 2.0, 6561
+    c0 = np.sqrt(E / rho)
+    h = L / N
+    omega = 5 * np.pi * c0 / L
+    Uf = lambda t: inputs.bell_pulse(t, 1e-3, omega, 4)
+    med = medium.Medium(1, (N,), (L,), np.full((1, 1, 1, 1, 1), E), np.zeros(N, np.int64), np.full(N, rho))
+    mask = np.zeros((1, N), bool)
+    mask[0, 0] = True
+    dt = ratio * h / c0
+    nsteps = int(round(3.919e-4 / dt))
+    nm = newmark.NewmarkOracle(med, mask, dt, tol=1e-12)
+    U = np.zeros((nsteps, 3))
+    U[:, 0] = Uf(dt * np.arange(1, nsteps + 1))
+    s, _ = nm.run(U)
+    x = (np.arange(N) + 0.5) * h
+    ua = analytic.dalembert_periodic(x, nsteps * dt, 0.0, c0, L, Uf)
+    return rel(s.u[0], ua)
+
+
+@pytest.mark.parametrize("ratio,paper", [(5, 2.09e-3), (10, 5.36e-3)])
+def test_1d_aluminium_bar_reproduces_table_2(ratio, paper):
+    """Sec. 3.1, Table 2 (implicit FFT column): Al bar, N = 6561, bell pulse at
+    x0 = 0 (Eq. prescribed_displacement), error of Eq. normL2 at the final time
+    against the d'Alembert solution (App. C), within a factor 1.5."""
+    err = _bar_run(ratio)
+    assert paper / 1.5 < err < paper * 1.5, err
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ratio,paper", [(1, 2.59e-3), (2, 2.48e-3)])
+def test_1d_aluminium_bar_reproduces_table_2_small_dt(ratio, paper):
+    err = _bar_run(ratio)
+    assert paper / 1.5 < err < paper * 1.5, err
+
+
+def test_3d_plane_wave_speeds_match_table_4():
+    """Sec. 3.2 / Table 4 analogue: homogeneous Al (E = 70.3 GPa, nu = 0.345),
+    a plane source on the x_1 = 0 voxel plane, dt = 10 CFL; the pulse centroid
+    moves at c_L = 6395.5 m/s (P) and c_S = 3111.1 m/s (S), within 1e-2."""
+    E, rho = AL
+    nu = 0.345
+    lam, mu = analytic.lame(E, nu)
+    cL, cS = analytic.isotropic_speeds(lam, mu, rho)
+    assert abs(cL - 6395.5) < 1.0 and abs(cS - 3111.1) < 1.0
+    C = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(inputs.isotropic_voigt(E, nu)))
+    N1, h = 2187, 1e-3  # as Table 4 (the pulse then spans ~44 steps at 10 CFL)
+    shape = (1, 3, N1)
+    med = medium.homogeneous_medium(3, shape, (N1 * h, 3 * h, h), C, rho)
+    mask = np.zeros((3,) + shape, bool)
+    mask[:, :, :, 0] = True
+    for comp, c in ((0, cL), (1, cS)):
+        dt = 10 * h / c
+        omega = 5 * np.pi * c / (N1 * h)
+        Uf = lambda t: inputs.bell_pulse(t, 1e-6, omega, 4)
+        # the two pulses (right-going, and left-going through the periodic image)
+        # stay apart in x < L/2 and x > L/2 until t = L/(2c): track 0.25 .. 0.4 L/c
+        nsteps = int(0.4 * N1 * h / c / dt)
+        U = np.zeros((nsteps, 3))
+        U[:, comp] = Uf(dt * np.arange(1, nsteps + 1))
+        nm = newmark.NewmarkOracle(med, mask, dt, tol=1e-12)
+        x = (np.arange(N1) + 0.5) * h
+        cents = {}
+
+        def cb(n, s, info):
+            w = s.u[comp, 0, 1] ** 2 * (x < 0.5 * N1 * h)
+            cents[n] = np.sum(w * x) / np.sum(w)
+
+        nm.run(U, callback=cb)
+        n1, n2 = int(0.25 * N1 * h / c / dt), nsteps
+        speed = (cents[n2] - cents[n1]) / ((n2 - n1) * dt)
+        assert abs(speed - c) / c < 1e-2, (comp, speed, c)
