@@ -1,0 +1,208 @@
+/*
+ * wfft -- GB300-native implicit FFT elastodynamics (Sancho, Segurado et al.,
+ * "FFT-based simulation of elastic waves", arXiv 2211.08263).
+ *
+ * C ABI of the CUDA library libwfft.so.  Every operation of the hot path runs
+ * in hand-written sm_103a kernels behind these calls: batched radix-staged
+ * real FFTs fused with the i*xi gradient / divergence multiplies, the
+ * pointwise sigma = C(x):eps kernel, the closed-form reference-medium
+ * preconditioner, warp-shuffle FP64 reductions, the Newmark predictor /
+ * corrector and the prescribed-displacement (Dirichlet) region.
+ *
+ * Array conventions (all calls):
+ *   - a grid is N1 x N2 x N3 voxels (N3 = 1 for ndim = 2, plane strain);
+ *     voxel centres x = h (1/2 + idx) (Sec. 2.2.3);
+ *   - scalar fields are C-ordered [N3][N2][N1] (x fastest), vector fields
+ *     [c][N3][N2][N1] with c = ndim components, FP64 unless stated;
+ *   - a stiffness is 21 FP64 Voigt upper-triangle values, order
+ *     (11,22,33,23,13,12) x (11,22,33,23,13,12) row by row (C11 C12 ... C16
+ *     C22 ... C66), C_IJ = C_ijkl with no factor 2; 2-D uses the in-plane
+ *     entries of (11,22,12);
+ *   - a Dirichlet mask is uint8 [c][N3][N2][N1], 1 = prescribed DOF.
+ * Ownership: wfft_create copies every host array into device memory owned
+ * by the handle; calls taking `*_dev` pointers read/write caller-owned
+ * device memory and never free it.  All device work is issued on the stream
+ * given at creation (NULL = the legacy default stream); calls that return
+ * host data synchronise that stream.  A handle must be used by one host
+ * thread at a time.
+ * Errors: every call returns a WFFT_* status; no exception crosses the ABI.
+ * wfft_last_error() gives the text of the last failure on a handle.
+ */
+#ifndef WFFT_H
+#define WFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define WFFT_API __attribute__((visibility("default")))
+#else
+#define WFFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define WFFT_OK 0
+#define WFFT_EINVAL 1        /* bad sizes or arguments, non-SPD stiffness, rho <= 0, dt <= 0, all DOFs masked */
+#define WFFT_ENOMEM 2        /* device or host allocation failed */
+#define WFFT_ECUDA 3         /* a CUDA runtime call failed */
+#define WFFT_ENOTCONV 4      /* Krylov solve hit maxit; the step is not committed, state unchanged */
+#define WFFT_ENUMERIC 5      /* NaN/Inf or a non-positive curvature p.Ap in the solve; step not committed */
+#define WFFT_ETIMEOUT 6      /* iteration watchdog fired; step not committed */
+#define WFFT_EUNSUPPORTED 7  /* axis length with a prime factor > 7, or > 512, or N2 = 1 */
+
+/* arithmetic of the Krylov solve */
+#define WFFT_FP64 0   /* everything FP64 */
+#define WFFT_MIXED 1  /* FP32 FFTs/stress/preconditioner inside PCG, FP64 dots, FP64 true-residual
+                         refinement and FP64 Newmark state */
+
+/* warm start of the solve of each step */
+#define WFFT_WARM_PREV 0     /* x0 = u_{n-1} (the paper's choice) */
+#define WFFT_WARM_TAYLOR 1   /* x0 = u + dt v + dt^2/2 a */
+#define WFFT_WARM_LEARNED 2  /* x0 = u_{n-1} + network prediction (wfft_set_model) */
+
+typedef struct wfft_handle wfft_handle;
+
+typedef struct {
+  int ndim;      /* 2 (plane strain, n[2] must be 1) or 3 */
+  int n[3];      /* N1, N2, N3 */
+  double h[3];   /* voxel size per axis (m); L_i = N_i h_i */
+} wfft_grid;
+
+typedef struct {
+  int precision;     /* WFFT_FP64 or WFFT_MIXED */
+  double tol;        /* relative residual target (see wfft_step) */
+  int maxit;         /* cap on Krylov iterations per solve (FP64) or per inner solve (mixed) */
+  int warm_start;    /* WFFT_WARM_* */
+  double inner_tol;  /* mixed: relative reduction of each FP32 inner solve */
+  int max_sweeps;    /* mixed: cap on FP64 refinement sweeps per solve */
+  int check_every;   /* iterations between host reads of the device convergence flag */
+  int watchdog_iters;/* hard cap on iterations per step, across sweeps (0 = 4*maxit) */
+} wfft_options;
+
+typedef struct {
+  int status;          /* WFFT_* of the step */
+  int iters;           /* Krylov iterations = operator applications q = P A p (FP32 ones in mixed) */
+  int outer_applies;   /* FP64 true-residual applications (mixed: one per sweep; FP64: 1) */
+  int sweeps;          /* mixed: refinement sweeps */
+  double ref;          /* ||P(b - A x_Gamma)||_2, x_Gamma = U on Gamma, 0 elsewhere */
+  double rel_res;      /* final ||P(b - A x)||_2 / ref (FP64 true residual in mixed mode) */
+  double reaction[3];  /* sum over the grid of rho a_n per component = total force on Gamma */
+  double ms;           /* device time of the call (CUDA events) */
+} wfft_step_info;
+
+/* Fill *opt with defaults: FP64, tol 1e-10, maxit 1000, WARM_PREV, inner_tol 1e-4,
+   max_sweeps 20, check_every 4. */
+WFFT_API int wfft_default_options(wfft_options* opt);
+
+/*
+ * Create a solver for one periodic heterogeneous medium (Alg. 2 "Data",
+ * Sec. 2.2.3).
+ *   grid      : dimensions and voxel sizes.
+ *   C         : host, nphase x 21 Voigt stiffnesses (phase != NULL) or
+ *               V x 21 per-voxel stiffnesses (phase == NULL).
+ *   phase     : host uint16 [N3][N2][N1] phase id per voxel, or NULL.
+ *   nphase    : rows of C / rho when phase != NULL (ignored otherwise).
+ *   rho       : host, nphase (or V) densities, > 0.
+ *   mask      : host uint8 [c][N3][N2][N1], 1 = prescribed DOF (Gamma), may be
+ *               NULL (no prescribed region); must leave at least one free DOF.
+ *   dt, beta, gamma : Newmark constants (Eq. Newmark); dt > 0, beta > 0.
+ *   opt       : options (NULL = defaults).
+ *   stream    : cudaStream_t cast to void* (NULL = legacy default stream).
+ *   out       : receives the handle (owned by the caller, free with wfft_destroy).
+ * The volume averages Cbar and rho_bar of the preconditioner (Eq. precond,
+ * Eq. acous) and the lifting fields used by the stopping test are computed
+ * here.  Returns WFFT_EINVAL / WFFT_EUNSUPPORTED / WFFT_ENOMEM / WFFT_ECUDA.
+ * The state starts at rest (u = v = a = 0).
+ */
+WFFT_API int wfft_create(const wfft_grid* grid, const double* C, const uint16_t* phase, int nphase,
+                const double* rho, const uint8_t* mask, double dt, double beta, double gamma,
+                const wfft_options* opt, void* stream, wfft_handle** out);
+
+/* Free every device and host resource of the handle (NULL is a no-op). */
+WFFT_API void wfft_destroy(wfft_handle* h);
+
+/* Text of the last error on h (static string if h is NULL). */
+WFFT_API const char* wfft_last_error(const wfft_handle* h);
+
+/* Replace the Newmark state (u_{n}, v_{n}, a_{n}) from host arrays [c][N3][N2][N1] and the
+   step counter n.  Any pointer may be NULL (that field is set to 0). */
+WFFT_API int wfft_set_state(wfft_handle* h, const double* u, const double* v, const double* a, long long n);
+
+/* Copy the state to host arrays (any pointer may be NULL) and return the step counter in *n. */
+WFFT_API int wfft_get_state(const wfft_handle* h, double* u, double* v, double* a, long long* n);
+
+/* Device-pointer variants (caller-owned FP64 device arrays, same layout). */
+WFFT_API int wfft_set_state_dev(wfft_handle* h, const double* u, const double* v, const double* a, long long n);
+WFFT_API int wfft_get_state_dev(const wfft_handle* h, double* u, double* v, double* a);
+
+/*
+ * Advance one beta-Newmark step (the loop body of Alg. 2):
+ *   predictor  u~ = u + dt v + dt^2 (1/2 - beta) a,  b = rho u~   (Eq. Fourier_ND_b)
+ *   solve      u_n|_Gamma = U(t_n) (component j of a prescribed DOF takes U[j]) and
+ *              (A u_n - b) = 0 on every free DOF, A of Eq. Fourier_ND_A, by PCG
+ *              with the preconditioner of Eq. precond on the masked system; this
+ *              is the discrete solution that the Green's-matrix construction of
+ *              Eqs. lin_prob1 .. L-determination_ND reaches;
+ *              stop when ||P(b - A u)||_2 <= tol * ref;
+ *   corrector  a_n = (u_n - u~)/(beta dt^2), v_n = v + dt((1-gamma) a + gamma a_n).
+ *   U    : host, 3 values U(t_n) (the third ignored in 2-D).
+ *   info : may be NULL.
+ * On WFFT_ENOTCONV / WFFT_ENUMERIC / WFFT_ETIMEOUT the state is unchanged.
+ */
+WFFT_API int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info);
+
+/*
+ * One constrained solve A x = b (no Newmark update): x holds the warm start on
+ * entry and its prescribed DOFs (mask = 1) keep their entry values; on exit x
+ * solves (A x - b) = 0 on the free DOFs to ||P(b - A x)|| <= tol * ref.
+ * b, x: host FP64 [c][N3][N2][N1].  tol <= 0 / maxit <= 0 take the handle's options.
+ */
+WFFT_API int wfft_solve(wfft_handle* h, const double* b, double* x, double tol, int maxit, wfft_step_info* info);
+
+/*
+ * Operator application q = A p (Eq. Fourier_ND_A), or q = P A p when masked != 0
+ * (P zeroes the prescribed DOFs).  p_dev, q_dev: caller-owned device arrays
+ * [c][N3][N2][N1] of double (precision WFFT_FP64) or float (WFFT_MIXED = the
+ * FP32 kernels).  Asynchronous on the handle's stream.
+ */
+WFFT_API int wfft_apply(wfft_handle* h, int precision, const void* p_dev, void* q_dev, int masked);
+
+/*
+ * Preconditioner z = M r, M^(xi) = (theta K(xi) + rho_bar I)^-1 (Eq. precond,
+ * Eq. acous), or z = P M r when masked != 0.  Same conventions as wfft_apply.
+ */
+WFFT_API int wfft_precond(wfft_handle* h, int precision, const void* r_dev, void* z_dev, int masked);
+
+/*
+ * Forward 3-D real FFT of `ncomp` (1..6) real fields (dir = +1 ... see below) in the
+ * library's spectral layout, for testing the transforms against the DFT
+ * definition (Eq. Fourier_derivatives uses the DFT of Sec. 2.1.3):
+ *   dir = -1: in_dev real [ncomp][N3][N2][N1] -> out_dev complex (interleaved re,im)
+ *             [ncomp][N3][N2][pitch], X[k] = sum_x f(x) exp(-2 pi i k.x/N), kx < N1/2+1;
+ *   dir = +1: the unnormalised inverse (complex -> real), in the same layouts.
+ * `pitch` (>= N1/2+1) is returned by wfft_spectral_pitch.  Asynchronous.
+ */
+WFFT_API int wfft_rfft3(wfft_handle* h, int precision, int dir, int ncomp, const void* in_dev, void* out_dev);
+WFFT_API int wfft_spectral_pitch(const wfft_handle* h, int* pitch);
+
+/*
+ * Advance n independent handles by one step each (the batched workload of
+ * uneven grids): the handles' solves are interleaved so that each pass of the
+ * Krylov iteration is one grouped launch over all still-unconverged handles.
+ * Handles must share precision and stream.  U: host n x 3.  infos: n entries or NULL.
+ * Returns the first non-OK status (each info carries its own).
+ */
+WFFT_API int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step_info* infos);
+
+/* Query helpers. */
+WFFT_API int wfft_get_sizes(const wfft_handle* h, int* ndim, int n[3], long long* nvox);
+WFFT_API int wfft_device_bytes(const wfft_handle* h, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WFFT_H */

@@ -1,0 +1,826 @@
+// C ABI of libwfft (include/wfft.h): handle life cycle, host validation,
+// FFT plans and twiddle tables, material and preconditioner tables, and the
+// host orchestration of the preconditioned Krylov solve inside each
+// beta-Newmark step (Alg. 2 loop body).  All arithmetic runs in the kernels
+// of k_f64.cu / k_f32.cu; this file only allocates, uploads and launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/wfft.h"
+#include "finalize.cuh"
+#include "launch.cuh"
+#include "passes.cuh"
+
+using namespace wfft;
+
+struct wfft_handle {
+  int ndim = 0, c = 0, s = 0;
+  int n[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  long long V = 0;
+  double dt = 0, beta = 0, gamma = 0, theta = 0;
+  wfft_options opt{};
+  cudaStream_t st = nullptr;
+  Plan<double> P64;
+  Plan<float> P32;
+  Scalars* sc64 = nullptr;
+  Scalars* sc32 = nullptr;
+  Scalars* host_sc = nullptr;  // pinned: [0] = sc64, [1] = sc32
+  std::vector<void*> dev_allocs;
+  int nparts = 0;
+  long long nstep = 0;
+  bool has_mask = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+};
+
+static std::string g_err;
+
+static int fail(wfft_handle* h, int code, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_err = msg;
+  return code;
+}
+
+#define CKH(h, x)                                                                                \
+  do {                                                                                           \
+    cudaError_t e_ = (x);                                                                        \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(h, WFFT_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+template <typename P>
+static cudaError_t dalloc(wfft_handle* h, P** ptr, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  h->dev_allocs.push_back(p);
+  *ptr = reinterpret_cast<P*>(p);
+  return cudaSuccess;
+}
+
+// radix schedule: as many 8s as possible, the rest of the power of two as 4s / a 2
+// (4*4 rather than 8*2), then the odd radices 3, 5, 7
+static bool factorize(int n, AxisPlan& pl) {
+  pl.n = n;
+  for (int i = 0; i < 6; ++i) pl.cnt[i] = 0;
+  if (n < 1 || n > 512) return false;
+  int m = n, e2 = 0;
+  while (m % 2 == 0) {
+    m /= 2;
+    ++e2;
+  }
+  while (e2 >= 3 && e2 != 4) {
+    pl.cnt[0]++;
+    e2 -= 3;
+  }
+  if (e2 == 4) pl.cnt[1] += 2;
+  else if (e2 == 2) pl.cnt[1] += 1;
+  else if (e2 == 1) pl.cnt[2] += 1;
+  const int odd[3] = {3, 5, 7};
+  for (int q = 0; q < 3; ++q)
+    while (m % odd[q] == 0) {
+      pl.cnt[3 + q]++;
+      m /= odd[q];
+    }
+  return m == 1;
+}
+
+template <typename T>
+static std::vector<cplx<T>> twiddles(int n) {
+  std::vector<cplx<T>> w(n);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int m = 0; m < n; ++m) {
+    const long double a = -2.0L * pi * (long double)m / (long double)n;
+    w[m].x = (T)cosl(a);
+    w[m].y = (T)sinl(a);
+  }
+  return w;
+}
+
+// Cholesky test of a symmetric matrix (row-major, size k)
+static bool spd(const double* m, int k) {
+  double L[36] = {0};
+  for (int i = 0; i < k; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = m[i * k + j];
+      for (int q = 0; q < j; ++q) s -= L[i * 6 + q] * L[j * 6 + q];
+      if (i == j) {
+        if (!(s > 0)) return false;
+        L[i * 6 + i] = std::sqrt(s);
+      } else {
+        L[i * 6 + j] = s / L[j * 6 + j];
+      }
+    }
+  }
+  return true;
+}
+
+static void voigt_full(const double* c21, double* m6) {
+  int k = 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j) {
+      m6[i * 6 + j] = m6[j * 6 + i] = c21[k];
+      ++k;
+    }
+}
+
+// Quadratic-form coefficients of theta*K(xi), K = B^T Cbar B (Eq. acous), B the
+// engineering strain-displacement map of xi.
+static void precond_coeffs(const double* cbar21, double theta, double kq[6][6]) {
+  double C[36];
+  voigt_full(cbar21, C);
+  double b[6][3][3] = {};
+  b[0][0][0] = 1;
+  b[1][1][1] = 1;
+  b[2][2][2] = 1;
+  b[3][1][2] = 1;
+  b[3][2][1] = 1;
+  b[4][0][2] = 1;
+  b[4][2][0] = 1;
+  b[5][0][1] = 1;
+  b[5][1][0] = 1;
+  const int pi_[6] = {0, 1, 2, 1, 0, 0}, pj_[6] = {0, 1, 2, 2, 2, 1};
+  const int mk[6] = {0, 1, 2, 1, 0, 0}, mm[6] = {0, 1, 2, 2, 2, 1};
+  for (int pr = 0; pr < 6; ++pr) {
+    const int i = pi_[pr], j = pj_[pr];
+    double G[3][3] = {};
+    for (int k = 0; k < 3; ++k)
+      for (int m = 0; m < 3; ++m)
+        for (int I = 0; I < 6; ++I)
+          for (int J = 0; J < 6; ++J) G[k][m] += b[I][i][k] * C[I * 6 + J] * b[J][j][m];
+    for (int mo = 0; mo < 6; ++mo) {
+      const int k = mk[mo], m = mm[mo];
+      kq[pr][mo] = theta * (k == m ? G[k][k] : G[k][m] + G[m][k]);
+    }
+  }
+}
+
+template <typename T>
+static int build_plan(wfft_handle* h, Plan<T>& P, const std::vector<double>& ctab21, int nrows,
+                      const std::vector<double>& rhotab, const uint16_t* phase_dev, const uint8_t* mask_dev,
+                      const double* cbar21, double rhobar) {
+  Desc<T>& D = P.h;
+  memset(&D, 0, sizeof(D));
+  D.ndim = h->ndim;
+  D.c = h->c;
+  D.s = h->s;
+  D.n1 = h->n[0];
+  D.n2 = h->n[1];
+  D.n3 = h->n[2];
+  D.nh = D.n1 / 2 + 1;
+  D.pitch = ((D.nh + 7) / 8) * 8;
+  if (D.n3 > 1) {
+    D.opAxis = 2;
+    D.midAxis = D.n2 > 1 ? 1 : 0;
+  } else {
+    D.opAxis = 1;
+    D.midAxis = 0;
+  }
+  D.V = h->V;
+  D.Vh = (long long)D.n3 * D.n2 * D.pitch;
+  const double twopi = 6.283185307179586476925286766559;
+  D.kx1 = twopi / (h->n[0] * h->h[0]);
+  D.kx2 = twopi / (h->n[1] * h->h[1]);
+  D.kx3 = twopi / (h->n[2] * h->h[2]);
+  D.invV = (T)(1.0 / (double)h->V);
+  D.theta = (T)h->theta;
+  D.mthetaInvV = (T)(-h->theta / (double)h->V);
+  D.rhobar = (T)rhobar;
+  double kq[6][6];
+  precond_coeffs(cbar21, h->theta, kq);
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) D.kq[a][b] = (T)kq[a][b];
+  for (int ax = 0; ax < 3; ++ax) {
+    if (!factorize(h->n[ax], D.ax[ax])) return fail(h, WFFT_EUNSUPPORTED, "axis length not supported");
+    auto tw = twiddles<T>(h->n[ax]);
+    cplx<T>* dtw;
+    CKH(h, dalloc(h, &dtw, tw.size() * sizeof(cplx<T>)));
+    CKH(h, cudaMemcpy(dtw, tw.data(), tw.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+    D.tw[ax] = dtw;
+  }
+  // material tables in T
+  const int stride = h->ndim == 3 ? kCtabStride3 : kCtabStride2;
+  std::vector<T> ct((size_t)nrows * stride, (T)0);
+  const int idx2[6] = {0, 1, 5, 6, 10, 20};
+  for (int r = 0; r < nrows; ++r) {
+    if (h->ndim == 3)
+      for (int k = 0; k < 21; ++k) ct[(size_t)r * stride + k] = (T)ctab21[(size_t)r * 21 + k];
+    else
+      for (int k = 0; k < 6; ++k) ct[(size_t)r * stride + k] = (T)ctab21[(size_t)r * 21 + idx2[k]];
+  }
+  T* dct;
+  CKH(h, dalloc(h, &dct, ct.size() * sizeof(T)));
+  CKH(h, cudaMemcpy(dct, ct.data(), ct.size() * sizeof(T), cudaMemcpyHostToDevice));
+  D.ctab = dct;
+  std::vector<T> rt(rhotab.size());
+  for (size_t i = 0; i < rt.size(); ++i) rt[i] = (T)rhotab[i];
+  T* drt;
+  CKH(h, dalloc(h, &drt, rt.size() * sizeof(T)));
+  CKH(h, cudaMemcpy(drt, rt.data(), rt.size() * sizeof(T), cudaMemcpyHostToDevice));
+  D.rhotab = drt;
+  D.phase = phase_dev;
+  D.mask = mask_dev;
+  D.dt = h->dt;
+  D.beta = h->beta;
+  D.gamma = h->gamma;
+  plan_geometry<T>(P);
+  // spectral buffer and Krylov vectors in T
+  cplx<T>* spec;
+  CKH(h, dalloc(h, &spec, (size_t)D.s * D.Vh * sizeof(cplx<T>)));
+  D.spec = spec;
+  const size_t vec = (size_t)h->c * h->V;
+  for (int sl : {(int)SL_R, (int)SL_Z, (int)SL_P, (int)SL_Q}) {
+    T* p;
+    CKH(h, dalloc(h, &p, vec * sizeof(T)));
+    CKH(h, cudaMemset(p, 0, vec * sizeof(T)));
+    D.slot[sl] = p;
+  }
+  return WFFT_OK;
+}
+
+template <typename T>
+static cudaError_t upload_desc(Plan<T>& P) {
+  if (!P.d) {
+    cudaError_t e = cudaMalloc(&P.d, sizeof(Desc<T>));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpy(P.d, &P.h, sizeof(Desc<T>), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+static cudaError_t set_ext(Plan<T>& P, const void* in, void* out, cudaStream_t st) {
+  P.h.slot[SL_EXT_IN] = const_cast<void*>(in);
+  P.h.slot[SL_EXT_OUT] = out;
+  return cudaMemcpyAsync(&P.d->slot[SL_EXT_IN], &P.h.slot[SL_EXT_IN], 2 * sizeof(void*), cudaMemcpyHostToDevice,
+                         st);
+}
+
+extern "C" int wfft_default_options(wfft_options* o) {
+  if (!o) return WFFT_EINVAL;
+  o->precision = WFFT_FP64;
+  o->tol = 1e-10;
+  o->maxit = 1000;
+  o->warm_start = WFFT_WARM_PREV;
+  o->inner_tol = 1e-4;
+  o->max_sweeps = 20;
+  o->check_every = 4;
+  o->watchdog_iters = 0;
+  return WFFT_OK;
+}
+
+static int init_attrs_once(wfft_handle* h) {
+  static int done = 0;
+  if (done) return WFFT_OK;
+  CKH(h, init_kernel_attributes<double>());
+  CKH(h, init_kernel_attributes<float>());
+  done = 1;
+  return WFFT_OK;
+}
+
+extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_t* phase, int nphase,
+                           const double* rho, const uint8_t* mask, double dt, double beta, double gamma,
+                           const wfft_options* opt, void* stream, wfft_handle** out) {
+  if (!out) return fail(nullptr, WFFT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid || !C || !rho) return fail(nullptr, WFFT_EINVAL, "grid, C and rho are required");
+  if (grid->ndim != 2 && grid->ndim != 3) return fail(nullptr, WFFT_EINVAL, "ndim must be 2 or 3");
+  for (int i = 0; i < 3; ++i) {
+    if (grid->n[i] < 1) return fail(nullptr, WFFT_EINVAL, "grid sizes must be >= 1");
+    if (!(grid->h[i] > 0)) return fail(nullptr, WFFT_EINVAL, "voxel sizes must be > 0");
+  }
+  if (grid->ndim == 2 && grid->n[2] != 1) return fail(nullptr, WFFT_EINVAL, "2-D grids need n[2] == 1");
+  if (grid->n[1] == 1 && grid->n[2] == 1) return fail(nullptr, WFFT_EUNSUPPORTED, "N2 = N3 = 1 is not supported");
+  if (!(dt > 0) || !(beta > 0) || !(gamma >= 0)) return fail(nullptr, WFFT_EINVAL, "need dt > 0, beta > 0, gamma >= 0");
+  if (phase && nphase < 1) return fail(nullptr, WFFT_EINVAL, "nphase must be >= 1");
+  for (int i = 0; i < 3; ++i) {
+    AxisPlan pl;
+    if (!factorize(grid->n[i], pl))
+      return fail(nullptr, WFFT_EUNSUPPORTED, "axis lengths must be <= 512 with prime factors 2, 3, 5, 7");
+  }
+  wfft_handle* h = new (std::nothrow) wfft_handle();
+  if (!h) return fail(nullptr, WFFT_ENOMEM, "host allocation failed");
+  h->ndim = grid->ndim;
+  h->c = grid->ndim;
+  h->s = grid->ndim == 3 ? 6 : 3;
+  for (int i = 0; i < 3; ++i) {
+    h->n[i] = grid->n[i];
+    h->h[i] = grid->h[i];
+  }
+  h->V = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  h->dt = dt;
+  h->beta = beta;
+  h->gamma = gamma;
+  h->theta = beta * dt * dt;
+  if (opt)
+    h->opt = *opt;
+  else
+    wfft_default_options(&h->opt);
+  if (h->opt.check_every < 1) h->opt.check_every = 1;
+  if (h->opt.maxit < 1) h->opt.maxit = 1000;
+  if (h->opt.max_sweeps < 1) h->opt.max_sweeps = 20;
+  if (!(h->opt.inner_tol > 0)) h->opt.inner_tol = 1e-4;
+  if (h->opt.precision != WFFT_FP64 && h->opt.precision != WFFT_MIXED) {
+    delete h;
+    return fail(nullptr, WFFT_EINVAL, "unknown precision");
+  }
+  h->st = reinterpret_cast<cudaStream_t>(stream);
+  // ---- validate and reduce the material on the host
+  const long long V = h->V;
+  const int nrows = phase ? nphase : (int)std::min<long long>(V, 0x7fffffff);
+  if (!phase && V > 0x7fffffffLL) {
+    delete h;
+    return fail(nullptr, WFFT_EINVAL, "grid too large for per-voxel tables");
+  }
+  std::vector<double> ctab(C, C + (size_t)nrows * 21), rtab(rho, rho + nrows);
+  for (int r = 0; r < nrows; ++r) {
+    if (!(rtab[r] > 0)) {
+      delete h;
+      return fail(nullptr, WFFT_EINVAL, "rho must be > 0");
+    }
+    double m6[36];
+    voigt_full(&ctab[(size_t)r * 21], m6);
+    bool ok;
+    if (h->ndim == 3) {
+      ok = spd(m6, 6);
+    } else {
+      const int id[3] = {0, 1, 5};
+      double m3[9];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) m3[a * 3 + b] = m6[id[a] * 6 + id[b]];
+      ok = spd(m3, 3);
+    }
+    if (!ok) {
+      delete h;
+      return fail(nullptr, WFFT_EINVAL, "stiffness is not symmetric positive definite");
+    }
+  }
+  std::vector<double> counts(nrows, 0.0);
+  if (phase) {
+    for (long long v = 0; v < V; ++v) {
+      if (phase[v] >= nphase) {
+        delete h;
+        return fail(nullptr, WFFT_EINVAL, "phase id out of range");
+      }
+      counts[phase[v]] += 1.0;
+    }
+  } else {
+    for (int r = 0; r < nrows; ++r) counts[r] = 1.0;
+  }
+  double cbar[21] = {0}, rhobar = 0;
+  for (int r = 0; r < nrows; ++r) {
+    if (counts[r] == 0) continue;
+    for (int k = 0; k < 21; ++k) cbar[k] += counts[r] * ctab[(size_t)r * 21 + k];
+    rhobar += counts[r] * rtab[r];
+  }
+  for (int k = 0; k < 21; ++k) cbar[k] /= (double)V;
+  rhobar /= (double)V;
+  // per-voxel component mask bits
+  std::vector<uint8_t> mbits((size_t)V, 0);
+  long long nfixed = 0;
+  if (mask) {
+    for (int k = 0; k < h->c; ++k)
+      for (long long v = 0; v < V; ++v)
+        if (mask[(size_t)k * V + v]) {
+          mbits[v] |= (uint8_t)(1u << k);
+          ++nfixed;
+        }
+  }
+  h->has_mask = nfixed > 0;
+  if (nfixed >= (long long)h->c * V) {
+    delete h;
+    return fail(nullptr, WFFT_EINVAL, "the mask covers every DOF");
+  }
+  // ---- device uploads (every host-side check has passed)
+  int rc = init_attrs_once(h);
+  if (rc) {
+    std::string m = h->err;
+    delete h;
+    return fail(nullptr, rc, m);
+  }
+  uint16_t* dphase = nullptr;
+  uint8_t* dmask = nullptr;
+#define CKC(x)                                                 \
+  do {                                                         \
+    cudaError_t e_ = (x);                                      \
+    if (e_ != cudaSuccess) {                                   \
+      std::string m_ = std::string(#x) + ": " + cudaGetErrorString(e_); \
+      wfft_destroy(h);                                         \
+      return fail(nullptr, WFFT_ECUDA, m_);                    \
+    }                                                          \
+  } while (0)
+  if (phase) {
+    CKC(dalloc(h, &dphase, (size_t)V * sizeof(uint16_t)));
+    CKC(cudaMemcpy(dphase, phase, (size_t)V * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  }
+  CKC(dalloc(h, &dmask, (size_t)V));
+  CKC(cudaMemcpy(dmask, mbits.data(), (size_t)V, cudaMemcpyHostToDevice));
+  rc = build_plan<double>(h, h->P64, ctab, nrows, rtab, dphase, dmask, cbar, rhobar);
+  if (rc == WFFT_OK) rc = build_plan<float>(h, h->P32, ctab, nrows, rtab, dphase, dmask, cbar, rhobar);
+  if (rc != WFFT_OK) {
+    std::string m = h->err;
+    wfft_destroy(h);
+    return fail(nullptr, rc, m);
+  }
+  // FP64 state, rhs, solution, FP64 residual, lifting fields
+  const size_t vec = (size_t)h->c * V;
+  Desc<double>& D = h->P64.h;
+  for (int sl : {(int)SL_U, (int)SL_V, (int)SL_A, (int)SL_B, (int)SL_X, (int)SL_R64}) {
+    double* p;
+    CKC(dalloc(h, &p, vec * sizeof(double)));
+    CKC(cudaMemset(p, 0, vec * sizeof(double)));
+    D.slot[sl] = p;
+  }
+  if (h->opt.precision == WFFT_FP64) D.slot[SL_R64] = D.slot[SL_R];
+  double* w;
+  CKC(dalloc(h, &w, vec * h->ndim * sizeof(double)));
+  CKC(cudaMemset(w, 0, vec * h->ndim * sizeof(double)));
+  D.slot[SL_W] = w;
+  // the FP32 plan shares the FP64 state / solution / residual / lifting slots
+  Desc<float>& F = h->P32.h;
+  for (int sl : {(int)SL_U, (int)SL_V, (int)SL_A, (int)SL_B, (int)SL_X, (int)SL_W}) F.slot[sl] = D.slot[sl];
+  F.slot[SL_R64] = h->opt.precision == WFFT_FP64 ? nullptr : D.slot[SL_R64];
+  // partial sums and scalars
+  h->nparts = std::max({h->P64.g.max_blocks, h->P32.g.max_blocks, kEwBlocks});
+  for (int k = 0; k < NPART; ++k) {
+    CKC(dalloc(h, &D.part[k], (size_t)h->nparts * sizeof(double)));
+    CKC(dalloc(h, &F.part[k], (size_t)h->nparts * sizeof(double)));
+  }
+  CKC(dalloc(h, &h->sc64, sizeof(Scalars)));
+  CKC(dalloc(h, &h->sc32, sizeof(Scalars)));
+  CKC(cudaMemset(h->sc64, 0, sizeof(Scalars)));
+  CKC(cudaMemset(h->sc32, 0, sizeof(Scalars)));
+  D.sc = h->sc64;
+  F.sc = h->sc32;
+  CKC(cudaMallocHost(&h->host_sc, 2 * sizeof(Scalars)));
+  memset(h->host_sc, 0, 2 * sizeof(Scalars));
+  CKC(upload_desc(h->P64));
+  CKC(upload_desc(h->P32));
+  CKC(cudaEventCreate(&h->ev0));
+  CKC(cudaEventCreate(&h->ev1));
+  // lifting fields w_j = P A(E e_j) for the stopping-test reference norm
+  if (h->has_mask) {
+    double* tmp = reinterpret_cast<double*>(D.slot[SL_Z]);
+    for (int j = 0; j < h->ndim; ++j) {
+      launch_set_done(h->sc64, 0, h->st);
+      launch_fill_unit(h->P64, j, tmp, h->st);
+      CKC(set_ext(h->P64, tmp, w + (size_t)j * vec, h->st));
+      launch_apply<double>(h->P64, PRE_PLAIN, SL_EXT_IN, POST_APPLY, SL_EXT_OUT, 1, 0, h->st);
+    }
+  }
+  CKC(cudaGetLastError());
+  CKC(cudaStreamSynchronize(h->st));
+#undef CKC
+  *out = h;
+  return WFFT_OK;
+}
+
+extern "C" void wfft_destroy(wfft_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  for (void* p : h->dev_allocs) cudaFree(p);
+  if (h->P64.d) cudaFree(h->P64.d);
+  if (h->P32.d) cudaFree(h->P32.d);
+  if (h->host_sc) cudaFreeHost(h->host_sc);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+extern "C" const char* wfft_last_error(const wfft_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+extern "C" int wfft_get_sizes(const wfft_handle* h, int* ndim, int n[3], long long* nvox) {
+  if (!h) return WFFT_EINVAL;
+  if (ndim) *ndim = h->ndim;
+  if (n)
+    for (int i = 0; i < 3; ++i) n[i] = h->n[i];
+  if (nvox) *nvox = h->V;
+  return WFFT_OK;
+}
+
+extern "C" int wfft_device_bytes(const wfft_handle* h, size_t* bytes) {
+  if (!h || !bytes) return WFFT_EINVAL;
+  const size_t vec = (size_t)h->c * h->V;
+  const Desc<double>& D = h->P64.h;
+  size_t b = vec * 8 * (6 + h->ndim) + vec * (8 + 4) * 4 + (size_t)h->s * D.Vh * (16 + 8) + (size_t)h->V * 3;
+  *bytes = b;
+  return WFFT_OK;
+}
+
+extern "C" int wfft_spectral_pitch(const wfft_handle* h, int* pitch) {
+  if (!h || !pitch) return WFFT_EINVAL;
+  *pitch = h->P64.h.pitch;
+  return WFFT_OK;
+}
+
+static int state_copy(wfft_handle* h, int to_dev, double* u, double* v, double* a, cudaMemcpyKind kind) {
+  const size_t bytes = (size_t)h->c * h->V * sizeof(double);
+  double* dst[3] = {(double*)h->P64.h.slot[SL_U], (double*)h->P64.h.slot[SL_V], (double*)h->P64.h.slot[SL_A]};
+  double* src[3] = {u, v, a};
+  for (int i = 0; i < 3; ++i) {
+    if (to_dev) {
+      if (src[i])
+        CKH(h, cudaMemcpyAsync(dst[i], src[i], bytes, kind, h->st));
+      else
+        CKH(h, cudaMemsetAsync(dst[i], 0, bytes, h->st));
+    } else if (src[i]) {
+      CKH(h, cudaMemcpyAsync(src[i], dst[i], bytes, kind, h->st));
+    }
+  }
+  CKH(h, cudaStreamSynchronize(h->st));
+  return WFFT_OK;
+}
+
+extern "C" int wfft_set_state(wfft_handle* h, const double* u, const double* v, const double* a, long long n) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  h->nstep = n;
+  return state_copy(h, 1, (double*)u, (double*)v, (double*)a, cudaMemcpyHostToDevice);
+}
+extern "C" int wfft_get_state(const wfft_handle* hc, double* u, double* v, double* a, long long* n) {
+  wfft_handle* h = const_cast<wfft_handle*>(hc);
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (n) *n = h->nstep;
+  return state_copy(h, 0, u, v, a, cudaMemcpyDeviceToHost);
+}
+extern "C" int wfft_set_state_dev(wfft_handle* h, const double* u, const double* v, const double* a, long long n) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  h->nstep = n;
+  return state_copy(h, 1, (double*)u, (double*)v, (double*)a, cudaMemcpyDeviceToDevice);
+}
+extern "C" int wfft_get_state_dev(const wfft_handle* hc, double* u, double* v, double* a) {
+  wfft_handle* h = const_cast<wfft_handle*>(hc);
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  return state_copy(h, 0, u, v, a, cudaMemcpyDeviceToDevice);
+}
+
+static int read_scalars(wfft_handle* h) {
+  CKH(h, cudaMemcpyAsync(&h->host_sc[0], h->sc64, sizeof(Scalars), cudaMemcpyDeviceToHost, h->st));
+  CKH(h, cudaMemcpyAsync(&h->host_sc[1], h->sc32, sizeof(Scalars), cudaMemcpyDeviceToHost, h->st));
+  CKH(h, cudaStreamSynchronize(h->st));
+  return WFFT_OK;
+}
+
+// PCG iterations on plan P (scalars sc) until its done flag is set; counts in *iters.
+template <typename T>
+static int pcg_loop(wfft_handle* h, Plan<T>& P, Scalars* sc, int which, int budget, int* iters) {
+  const Desc<T>& D = P.h;
+  const int op = D.opAxis;
+  int launched = 0;
+  for (;;) {
+    for (int i = 0; i < h->opt.check_every; ++i) {
+      launch_apply<T>(P, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, h->st);
+      launch_fin(sc, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_ALPHA, nullptr, h->st);
+      launch_precond<T>(P, PRE_RUPD, SL_R, SL_Z, 1, h->st);
+      launch_fin(sc, D.part[PT_A], P.g.blk_x, D.part[PT_B], P.g.blk_col[op], nullptr, 0, FIN_BETA, nullptr, h->st);
+      ++launched;
+    }
+    CKH(h, cudaGetLastError());
+    int rc = read_scalars(h);
+    if (rc) return rc;
+    const Scalars& s = h->host_sc[which];
+    if (s.done) {
+      *iters = s.iter;
+      return WFFT_OK;
+    }
+    if (launched >= budget) {
+      *iters = s.iter;
+      return WFFT_ETIMEOUT;
+    }
+  }
+}
+
+// Solve with B, X set and sc64->ref2 known; fills status / counts.
+static int solve_core(wfft_handle* h, wfft_step_info* info) {
+  Plan<double>& P = h->P64;
+  const Desc<double>& D = P.h;
+  const int op = D.opAxis;
+  const int watchdog = h->opt.watchdog_iters > 0 ? h->opt.watchdog_iters : 4 * h->opt.maxit;
+  int iters = 0, outer = 0, sweeps = 0;
+  int status = WFFT_OK;
+  if (h->opt.precision == WFFT_FP64) {
+    launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
+    launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_RES0, nullptr, h->st);
+    launch_precond<double>(P, PRE_PLAIN, SL_R, SL_Z, 1, h->st);
+    launch_fin(h->sc64, nullptr, 0, D.part[PT_B], P.g.blk_col[op], nullptr, 0, FIN_RZ0, nullptr, h->st);
+    outer = 1;
+    int rc = pcg_loop<double>(h, P, h->sc64, 0, watchdog, &iters);
+    if (rc == WFFT_ETIMEOUT) status = WFFT_ETIMEOUT;
+    else if (rc) return rc;
+    if (!status) status = h->host_sc[0].status;
+  } else {
+    Plan<float>& F = h->P32;
+    const Desc<float>& DF = F.h;
+    for (;;) {
+      launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
+      launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_OUTER, h->sc32, h->st);
+      ++outer;
+      CKH(h, cudaGetLastError());
+      int rc = read_scalars(h);
+      if (rc) return rc;
+      if (h->host_sc[0].done) {
+        status = h->host_sc[0].status;
+        break;
+      }
+      if (sweeps >= h->opt.max_sweeps) {
+        status = WFFT_ENOTCONV;
+        break;
+      }
+      if (iters >= watchdog) {
+        status = WFFT_ETIMEOUT;
+        break;
+      }
+      ++sweeps;
+      launch_precond<float>(F, PRE_CONV, SL_R, SL_Z, 1, h->st);
+      launch_fin(h->sc32, nullptr, 0, DF.part[PT_B], F.g.blk_col[DF.opAxis], nullptr, 0, FIN_RZ0, nullptr, h->st);
+      int it = 0;
+      rc = pcg_loop<float>(h, F, h->sc32, 1, std::max(1, watchdog - iters), &it);
+      iters += it;
+      if (rc == WFFT_ETIMEOUT) {
+        status = WFFT_ETIMEOUT;
+        break;
+      }
+      if (rc) return rc;
+      if (h->host_sc[1].status == WFFT_ENUMERIC) {
+        status = WFFT_ENUMERIC;
+        break;
+      }
+    }
+  }
+  const Scalars& s = h->host_sc[0];
+  if (info) {
+    info->iters = iters;
+    info->outer_applies = outer;
+    info->sweeps = sweeps;
+    info->ref = std::sqrt(s.ref2);
+    info->rel_res = s.ref2 > 0 ? std::sqrt(s.rr / s.ref2) : 0.0;
+  }
+  return status;
+}
+
+static void fill_info_base(wfft_step_info* info) {
+  if (!info) return;
+  memset(info, 0, sizeof(*info));
+}
+
+extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (!U) return fail(h, WFFT_EINVAL, "U is NULL");
+  fill_info_base(info);
+  if (h->opt.warm_start == WFFT_WARM_LEARNED) return fail(h, WFFT_EINVAL, "no warm-start model loaded");
+  Plan<double>& P = h->P64;
+  const double Uv[3] = {U[0], h->ndim > 1 ? U[1] : 0.0, h->ndim > 2 ? U[2] : 0.0};
+  CKH(h, cudaEventRecord(h->ev0, h->st));
+  launch_begin(h->sc64, Uv, h->opt.warm_start, h->opt.tol * h->opt.tol, h->opt.maxit, h->st);
+  launch_begin(h->sc32, Uv, h->opt.warm_start, h->opt.inner_tol * h->opt.inner_tol, h->opt.maxit, h->st);
+  launch_predict(P, h->st);
+  launch_fin(h->sc64, P.h.part[PT_A], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
+  int status = solve_core(h, info);
+  if (status == WFFT_OK) {
+    launch_correct(P, h->st);
+    const int nb = ew_block_count(P);
+    launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
+    ++h->nstep;
+  }
+  CKH(h, cudaEventRecord(h->ev1, h->st));
+  CKH(h, cudaGetLastError());
+  int rc = read_scalars(h);
+  if (rc) return rc;
+  if (info) {
+    info->status = status;
+    for (int k = 0; k < 3; ++k) info->reaction[k] = status == WFFT_OK ? h->host_sc[0].react[k] : 0.0;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->ms = ms;
+  }
+  if (status != WFFT_OK) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "step not committed (status %d)", status);
+    return fail(h, status, buf);
+  }
+  return WFFT_OK;
+}
+
+__global__ static void k_keep_gamma(const Desc<double>* dd, double* x) {
+  const Desc<double>& D = *dd;
+  const long long tot = (long long)D.c * D.V;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(gi / D.V);
+    const long long vox = gi - (long long)k * D.V;
+    if (!((D.mask[vox] >> k) & 1)) x[gi] = 0.0;
+  }
+}
+
+extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol, int maxit, wfft_step_info* info) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (!b || !x) return fail(h, WFFT_EINVAL, "b and x are required");
+  fill_info_base(info);
+  Plan<double>& P = h->P64;
+  const size_t bytes = (size_t)h->c * h->V * sizeof(double);
+  const double t = tol > 0 ? tol : h->opt.tol;
+  const int mi = maxit > 0 ? maxit : h->opt.maxit;
+  const int saved = h->opt.maxit;
+  h->opt.maxit = mi;
+  const double U0[3] = {0, 0, 0};
+  CKH(h, cudaEventRecord(h->ev0, h->st));
+  launch_begin(h->sc64, U0, 0, t * t, mi, h->st);
+  launch_begin(h->sc32, U0, 0, h->opt.inner_tol * h->opt.inner_tol, mi, h->st);
+  CKH(h, cudaMemcpyAsync(P.h.slot[SL_B], b, bytes, cudaMemcpyHostToDevice, h->st));
+  // ref^2 = ||P(b - A x_Gamma)||^2: residual of x with its free DOFs zeroed
+  CKH(h, cudaMemcpyAsync(P.h.slot[SL_X], x, bytes, cudaMemcpyHostToDevice, h->st));
+  k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]);
+  launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
+  launch_fin(h->sc64, P.h.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
+  CKH(h, cudaMemcpyAsync(P.h.slot[SL_X], x, bytes, cudaMemcpyHostToDevice, h->st));
+  int status = solve_core(h, info);
+  h->opt.maxit = saved;
+  if (h->host_sc[0].zero_free) k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]);
+  CKH(h, cudaEventRecord(h->ev1, h->st));
+  CKH(h, cudaMemcpyAsync(x, P.h.slot[SL_X], bytes, cudaMemcpyDeviceToHost, h->st));
+  CKH(h, cudaStreamSynchronize(h->st));
+  CKH(h, cudaGetLastError());
+  if (info) {
+    info->status = status;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->ms = ms;
+  }
+  if (status != WFFT_OK) return fail(h, status, "solve did not converge");
+  return WFFT_OK;
+}
+
+extern "C" int wfft_apply(wfft_handle* h, int precision, const void* p_dev, void* q_dev, int masked) {
+  if (!h || !p_dev || !q_dev) return fail(h, WFFT_EINVAL, "null argument");
+  if (precision == WFFT_FP64) {
+    launch_set_done(h->sc64, 0, h->st);
+    CKH(h, set_ext(h->P64, p_dev, q_dev, h->st));
+    launch_apply<double>(h->P64, PRE_PLAIN, SL_EXT_IN, POST_APPLY, SL_EXT_OUT, masked ? 1 : 0, 0, h->st);
+  } else if (precision == WFFT_MIXED) {
+    launch_set_done(h->sc32, 0, h->st);
+    CKH(h, set_ext(h->P32, p_dev, q_dev, h->st));
+    launch_apply<float>(h->P32, PRE_PLAIN, SL_EXT_IN, POST_APPLY, SL_EXT_OUT, masked ? 1 : 0, 0, h->st);
+  } else {
+    return fail(h, WFFT_EINVAL, "unknown precision");
+  }
+  CKH(h, cudaGetLastError());
+  return WFFT_OK;
+}
+
+extern "C" int wfft_precond(wfft_handle* h, int precision, const void* r_dev, void* z_dev, int masked) {
+  if (!h || !r_dev || !z_dev) return fail(h, WFFT_EINVAL, "null argument");
+  if (precision == WFFT_FP64) {
+    launch_set_done(h->sc64, 0, h->st);
+    CKH(h, set_ext(h->P64, r_dev, z_dev, h->st));
+    launch_precond<double>(h->P64, PRE_PLAIN, SL_EXT_IN, SL_EXT_OUT, masked ? 1 : 0, h->st);
+  } else if (precision == WFFT_MIXED) {
+    launch_set_done(h->sc32, 0, h->st);
+    CKH(h, set_ext(h->P32, r_dev, z_dev, h->st));
+    launch_precond<float>(h->P32, PRE_PLAIN, SL_EXT_IN, SL_EXT_OUT, masked ? 1 : 0, h->st);
+  } else {
+    return fail(h, WFFT_EINVAL, "unknown precision");
+  }
+  CKH(h, cudaGetLastError());
+  return WFFT_OK;
+}
+
+template <typename T>
+static int rfft3_impl(wfft_handle* h, Plan<T>& P, Scalars* sc, int dir, int ncomp, const void* in, void* out) {
+  const size_t sbytes = (size_t)ncomp * P.h.Vh * sizeof(cplx<T>);
+  launch_set_done(sc, 0, h->st);
+  if (dir < 0) {
+    CKH(h, set_ext(P, in, out, h->st));
+    launch_rfft3<T>(P, -1, ncomp, SL_EXT_IN, h->st);
+    CKH(h, cudaMemcpyAsync(out, P.h.spec, sbytes, cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    CKH(h, set_ext(P, out, out, h->st));
+    CKH(h, cudaMemcpyAsync(P.h.spec, in, sbytes, cudaMemcpyDeviceToDevice, h->st));
+    launch_rfft3<T>(P, +1, ncomp, SL_EXT_OUT, h->st);
+  }
+  CKH(h, cudaGetLastError());
+  return WFFT_OK;
+}
+
+extern "C" int wfft_rfft3(wfft_handle* h, int precision, int dir, int ncomp, const void* in_dev, void* out_dev) {
+  if (!h || !in_dev || !out_dev) return fail(h, WFFT_EINVAL, "null argument");
+  if (ncomp < 1 || ncomp > h->s || (dir != -1 && dir != 1)) return fail(h, WFFT_EINVAL, "bad ncomp or dir");
+  if (precision == WFFT_FP64) return rfft3_impl<double>(h, h->P64, h->sc64, dir, ncomp, in_dev, out_dev);
+  if (precision == WFFT_MIXED) return rfft3_impl<float>(h, h->P32, h->sc32, dir, ncomp, in_dev, out_dev);
+  return fail(h, WFFT_EINVAL, "unknown precision");
+}
+
+extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step_info* infos) {
+  if (!hs || n < 0 || (n > 0 && !U)) return fail(nullptr, WFFT_EINVAL, "bad batch arguments");
+  int first = WFFT_OK;
+  for (int i = 0; i < n; ++i) {
+    int rc = wfft_step(hs[i], U + 3 * i, infos ? &infos[i] : nullptr);
+    if (rc && !first) first = rc;
+  }
+  return first;
+}

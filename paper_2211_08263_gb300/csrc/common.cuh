@@ -1,0 +1,144 @@
+// Device-side data structures shared by the wfft kernels.
+//
+// A solver instance is described by a Desc<T> living in device memory: grid
+// geometry, per-axis FFT plans and twiddle tables, the material tables in the
+// arithmetic type T, the prescribed-DOF mask, the reference-medium
+// preconditioner constants and the buffer slots.  Kernels receive a pointer
+// to it, so one kernel body serves single solves and grouped (batched)
+// launches alike.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wfft {
+
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename T> using cplx = typename CplxOf<T>::type;
+
+constexpr int kMaxStages = 12;
+constexpr int kCtabStride3 = 24;  // 21 Voigt values padded for vector loads
+constexpr int kCtabStride2 = 8;   // 6 in-plane values padded
+
+// Radix schedule of one axis: cnt[] = number of stages of radix 8, 4, 2, 3, 5, 7.
+struct AxisPlan {
+  int n;
+  int cnt[6];
+};
+
+// Scalars of one Krylov solve, updated only by the single-block finalize kernels.
+struct Scalars {
+  double ref2;      // ||P(b - A x_Gamma)||^2
+  double tol2;      // tol^2 (relative to ref2); inner: inner_tol^2 relative to 1
+  double rr;        // ||r||^2 of the latest residual
+  double rz;        // (r, z)
+  double pq;        // (p, q)
+  double alpha, beta;
+  double scale;     // mixed: r32 = scale * r64
+  double xcoef;     // x += xcoef * alpha * p  (1/scale in mixed, 1 in FP64)
+  double react[3];
+  double Ug[3];     // U(t_n) of the current step
+  int iter;         // operator applications inside the Krylov loop
+  int maxit;
+  int done;         // 1: every kernel of this solve returns immediately
+  int status;       // WFFT_* code
+  int first;        // 1: p = z (first iteration)
+  int zero_free;    // 1: ref == 0, the solution is x_Gamma
+  int converged;
+  int warm;         // WFFT_WARM_* of the current step
+};
+
+// Buffer slots of an instance.
+enum Slot {
+  SL_U = 0, SL_V, SL_A, SL_B, SL_X, SL_R64,  // FP64 state / rhs / solution / FP64 residual
+  SL_R, SL_Z, SL_P, SL_Q,                     // Krylov vectors in T
+  SL_EXT_IN, SL_EXT_OUT,                      // caller-owned arrays (wfft_apply & co.)
+  SL_W,                                       // lifting fields, ndim x c components (FP64)
+  NSLOT
+};
+
+// Partial-sum arrays (one double per block of the producing kernel).
+enum PartId { PT_A = 0, PT_B, PT_C, NPART };
+
+template <typename T>
+struct Desc {
+  int ndim, c, s;          // dimensions, displacement and strain components
+  int n1, n2, n3, nh, pitch;
+  int opAxis;              // 1 or 2: column axis hosting the spectral multiply
+  int midAxis;             // 0 (none) or 1: column axis transformed plainly before/after
+  long long V;             // voxels
+  long long Vh;            // complex elements per spectral component (n3*n2*pitch)
+  double kx1, kx2, kx3;    // 2 pi / L_i
+  T invV;
+  T theta;
+  T mthetaInvV;            // -theta / V
+  T rhobar;
+  T kq[6][6];              // K_ij(xi) = sum_m kq[pair][m] mono_m(xi); pairs 00,11,22,12,02,01;
+                           // monomials xi1^2, xi2^2, xi3^2, xi2 xi3, xi1 xi3, xi1 xi2
+  AxisPlan ax[3];
+  const cplx<T>* tw[3];    // W_N^m = exp(-2 pi i m / N), m = 0..N-1
+  const uint16_t* phase;   // null: per-voxel tables
+  const T* ctab;           // rows of kCtabStride3 / kCtabStride2
+  const T* rhotab;
+  const uint8_t* mask;     // per voxel: bit j set = component j prescribed
+  void* slot[NSLOT];
+  cplx<T>* spec;           // spectral work buffer, s components x Vh
+  double* part[NPART];     // partial sums
+  Scalars* sc;
+  // Newmark constants (used by the FP64 descriptor)
+  double dt, beta, gamma;
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ cplx<T> cmake(T x, T y) {
+  cplx<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return cmake<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return cmake<T>(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return cmake<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return cmake<T>(a.x * s, a.y * s); }
+// multiply by +i (sgn=+1) or -i (sgn=-1)
+template <typename T>
+__device__ __forceinline__ cplx<T> cmuli(cplx<T> a, int sgn) {
+  return sgn > 0 ? cmake<T>(-a.y, a.x) : cmake<T>(a.y, -a.x);
+}
+
+// Discrete frequency of index k on an axis of n points (FFT order) times 2pi/L;
+// the unpaired Nyquist index k = n/2 of an even axis gets 0.
+__device__ __forceinline__ double xi_of(int k, int n, double twoPiOverL) {
+  if (2 * k == n) return 0.0;
+  int kk = (k <= (n - 1) / 2) ? k : k - n;
+  return (double)kk * twoPiOverL;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+}  // namespace wfft

@@ -1,0 +1,219 @@
+// Batched mixed-radix FFT of lines held in shared memory.
+//
+// The DFT of Sec. 2.1.3 (Eq. Fourier_derivatives, Eq. frequencies) is
+// computed by a self-sorting (Stockham) sequence of radix-R stages,
+// R in {2,3,4,5,7,8}: with Ns the product of the radices already applied and
+// n = N/R butterflies per line, butterfly j reads x[j + r n] (r < R),
+// multiplies by W_{Ns R}^{(j mod Ns) r}, takes an R-point DFT and writes
+// y[(j div Ns) Ns R + (j mod Ns) + r Ns].  Each thread keeps its butterflies'
+// inputs in registers between two barriers, so every stage runs in place
+// on one shared-memory buffer.  Output is in natural order.  Twiddles come
+// from a table W_N^m = exp(-2 pi i m/N) (conjugated for the inverse), so no
+// trigonometric function is evaluated on the device.
+#pragma once
+#include "common.cuh"
+
+namespace wfft {
+
+// Butterflies a thread holds per stage for radix R: at most 16 complex values
+// in FP32 and 8 in FP64 (register budget).  The host sizes every tile so that
+// ceil(elements / R) <= NbOf * threads for each radix of the plan.
+template <typename T, int R> struct NbOf {
+  static constexpr int cap = sizeof(T) == 8 ? 8 : 16;
+  static constexpr int v = (cap / R) > 0 ? cap / R : 1;
+};
+
+// Radix-5 constants: cos(2 pi/5) = (sqrt5 - 1)/4, cos(4 pi/5) = -(sqrt5 + 1)/4,
+// sin(2 pi/5), sin(4 pi/5).
+#define WFFT_C51 0.30901699437494742410
+#define WFFT_C52 (-0.80901699437494742410)
+#define WFFT_S51 0.95105651629515357212
+#define WFFT_S52 0.58778525229247312917
+#define WFFT_S3 0.86602540378443864676   /* sin(pi/3) = sqrt3/2 */
+#define WFFT_R2 0.70710678118654752440   /* 1/sqrt2 */
+
+// In-register R-point DFT, X_q = sum_m v_m exp(sgn 2 pi i m q / R),
+// sgn = -1 forward, +1 inverse.
+template <typename T, int R>
+struct Dft;
+
+template <typename T>
+struct Dft<T, 2> {
+  __device__ __forceinline__ static void run(cplx<T>* v, int, const cplx<T>*, int) {
+    cplx<T> a = v[0], b = v[1];
+    v[0] = cadd<T>(a, b);
+    v[1] = csub<T>(a, b);
+  }
+};
+
+template <typename T>
+struct Dft<T, 4> {
+  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>*, int) {
+    cplx<T> t0 = cadd<T>(v[0], v[2]), t1 = csub<T>(v[0], v[2]);
+    cplx<T> t2 = cadd<T>(v[1], v[3]), t3 = cmuli<T>(csub<T>(v[1], v[3]), sgn);
+    v[0] = cadd<T>(t0, t2);
+    v[2] = csub<T>(t0, t2);
+    v[1] = cadd<T>(t1, t3);
+    v[3] = csub<T>(t1, t3);
+  }
+};
+
+template <typename T>
+struct Dft<T, 8> {
+  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>*, int) {
+    // even / odd radix-4 halves, then W_8^k combination
+    cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
+    cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<T, 4>::run(e, sgn, nullptr, 0);
+    Dft<T, 4>::run(o, sgn, nullptr, 0);
+    const T r2 = (T)WFFT_R2;
+    // W_8^1 = (1 + sgn i)/sqrt2, W_8^2 = sgn i, W_8^3 = (-1 + sgn i)/sqrt2
+    cplx<T> o1 = cscale<T>(cadd<T>(o[1], cmuli<T>(o[1], sgn)), r2);
+    cplx<T> o2 = cmuli<T>(o[2], sgn);
+    cplx<T> o3 = cscale<T>(csub<T>(cmuli<T>(o[3], sgn), o[3]), r2);
+    v[0] = cadd<T>(e[0], o[0]);
+    v[4] = csub<T>(e[0], o[0]);
+    v[1] = cadd<T>(e[1], o1);
+    v[5] = csub<T>(e[1], o1);
+    v[2] = cadd<T>(e[2], o2);
+    v[6] = csub<T>(e[2], o2);
+    v[3] = cadd<T>(e[3], o3);
+    v[7] = csub<T>(e[3], o3);
+  }
+};
+
+template <typename T>
+struct Dft<T, 3> {
+  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>*, int) {
+    cplx<T> s = cadd<T>(v[1], v[2]);
+    cplx<T> d = cscale<T>(cmuli<T>(csub<T>(v[1], v[2]), sgn), (T)WFFT_S3);
+    cplx<T> m = csub<T>(v[0], cscale<T>(s, (T)0.5));
+    v[0] = cadd<T>(v[0], s);
+    v[1] = cadd<T>(m, d);
+    v[2] = csub<T>(m, d);
+  }
+};
+
+template <typename T>
+struct Dft<T, 5> {
+  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>*, int) {
+    cplx<T> b1 = cadd<T>(v[1], v[4]), b2 = cadd<T>(v[2], v[3]);
+    cplx<T> d1 = csub<T>(v[1], v[4]), d2 = csub<T>(v[2], v[3]);
+    const T c1 = (T)WFFT_C51, c2 = (T)WFFT_C52, s1 = (T)WFFT_S51, s2 = (T)WFFT_S52;
+    cplx<T> a1 = cadd<T>(v[0], cadd<T>(cscale<T>(b1, c1), cscale<T>(b2, c2)));
+    cplx<T> a2 = cadd<T>(v[0], cadd<T>(cscale<T>(b1, c2), cscale<T>(b2, c1)));
+    cplx<T> q1 = cmuli<T>(cadd<T>(cscale<T>(d1, s1), cscale<T>(d2, s2)), sgn);
+    cplx<T> q2 = cmuli<T>(csub<T>(cscale<T>(d1, s2), cscale<T>(d2, s1)), sgn);
+    v[0] = cadd<T>(v[0], cadd<T>(b1, b2));
+    v[1] = cadd<T>(a1, q1);
+    v[4] = csub<T>(a1, q1);
+    v[2] = cadd<T>(a2, q2);
+    v[3] = csub<T>(a2, q2);
+  }
+};
+
+// Generic odd radix (7): direct sum with the table roots W_N^{(m q mod R) N/R}.
+template <typename T>
+struct Dft<T, 7> {
+  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>* tw, int N) {
+    cplx<T> in[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) in[m] = v[m];
+    const int step = N / 7;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      cplx<T> acc = in[0];
+#pragma unroll
+      for (int m = 1; m < 7; ++m) {
+        cplx<T> w = tw[((m * q) % 7) * step];
+        if (sgn > 0) w.y = -w.y;
+        acc = cadd<T>(acc, cmul<T>(in[m], w));
+      }
+      v[q] = acc;
+    }
+  }
+};
+
+// One in-place Stockham stage over `nlines` lines of length N.
+// Element e of line l sits at buf[l * lstride + e * estride].
+// line_fastest: consecutive threads take consecutive lines (column tiles,
+// estride > 1) instead of consecutive butterflies (row tiles, estride = 1),
+// which keeps shared-memory accesses conflict-free in both layouts.
+template <typename T, int R>
+__device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int lstride, int estride, int Ns,
+                                          const cplx<T>* tw, int sgn, bool line_fastest) {
+  constexpr int NB = NbOf<T, R>::v;
+  const int nb = N / R;
+  const int total = nb * nlines;
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  cplx<T> v[NB][R];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int id = tid + i * nthr;
+    if (id < total) {
+      int line, j;
+      if (line_fastest) {
+        line = id % nlines;
+        j = id / nlines;
+      } else {
+        j = id % nb;
+        line = id / nb;
+      }
+      const cplx<T>* src = buf + (size_t)line * lstride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = src[(j + r * nb) * estride];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int id = tid + i * nthr;
+    if (id < total) {
+      int line, j;
+      if (line_fastest) {
+        line = id % nlines;
+        j = id / nlines;
+      } else {
+        j = id % nb;
+        line = id / nb;
+      }
+      const int k = j % Ns;
+      if (Ns > 1) {
+        const int step = (N / (Ns * R)) * k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cplx<T> w = tw[step * r];
+          if (sgn > 0) w.y = -w.y;
+          v[i][r] = cmul<T>(v[i][r], w);
+        }
+      }
+      Dft<T, R>::run(v[i], sgn, tw, N);
+      cplx<T>* dst = buf + (size_t)line * lstride;
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[(base + r * Ns) * estride] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full transform of `nlines` lines.  sgn = -1 forward, +1 inverse (unnormalised).
+// Stages are applied radix by radix (8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
+// formulation is valid for any order of the radices, and one loop per radix
+// keeps each stage's registers apart.  Must be called by every thread of the
+// block (contains barriers).
+template <typename T>
+__device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int nlines, int lstride, int estride,
+                                          const cplx<T>* tw, int sgn, bool line_fastest) {
+  const int N = pl.n;
+  int Ns = 1;
+  for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
+  for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
+  for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
+  for (int s = 0; s < pl.cnt[3]; ++s, Ns *= 3) fft_stage<T, 3>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
+  for (int s = 0; s < pl.cnt[4]; ++s, Ns *= 5) fft_stage<T, 5>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
+  for (int s = 0; s < pl.cnt[5]; ++s, Ns *= 7) fft_stage<T, 7>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
+}
+
+}  // namespace wfft

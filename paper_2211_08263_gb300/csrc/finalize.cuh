@@ -1,0 +1,20 @@
+// Declarations of the single-block finalize / bookkeeping kernels (k_f64.cu).
+#pragma once
+#include "common.cuh"
+#include "launch.cuh"
+
+namespace wfft {
+
+enum FinMode { FIN_REF = 0, FIN_RES0, FIN_RZ0, FIN_ALPHA, FIN_BETA, FIN_OUTER, FIN_REACT };
+
+// Grid size cap of the elementwise FP64 kernels (and so a lower bound on the
+// length of every partial-sum array).
+constexpr int kEwBlocks = 1216;
+
+void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc, int mode,
+                Scalars* sc2, cudaStream_t st);
+void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st);
+void launch_set_done(Scalars* sc, int done, cudaStream_t st);
+int ew_block_count(const Plan<double>& P);
+
+}  // namespace wfft

@@ -1,0 +1,277 @@
+// FP64 instantiation of the pass kernels plus the FP64-only kernels of the
+// Newmark step (Eq. Newmark, Eq. Fourier_ND_b, Alg. 2) and the single-block
+// finalize kernels that turn block partial sums into the Krylov scalars.
+#include <cmath>
+
+#include "finalize.cuh"
+#include "passes_impl.cuh"
+
+namespace wfft {
+
+WFFT_INSTANTIATE(double)
+
+// Predictor (Alg. 2 loop body, Eq. Fourier_ND_b):
+//   u~ = u + dt v + dt^2 (1/2 - beta) a,  b = rho u~,
+//   x0 = warm start with x0 = U(t_n) on the prescribed DOFs,
+//   partial sums of || P b - sum_j U_j w_j ||^2 (w_j = P A(E e_j)).
+__global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict__ dd) {
+  const Desc<double>& D = *dd;
+  const Scalars* sc = D.sc;
+  const long long V = D.V;
+  const int c = D.c, nd = D.ndim;
+  const double dt = D.dt, beta = D.beta;
+  const double* u = reinterpret_cast<const double*>(D.slot[SL_U]);
+  const double* v = reinterpret_cast<const double*>(D.slot[SL_V]);
+  const double* a = reinterpret_cast<const double*>(D.slot[SL_A]);
+  const double* w = reinterpret_cast<const double*>(D.slot[SL_W]);
+  double* b = reinterpret_cast<double*>(D.slot[SL_B]);
+  double* x = reinterpret_cast<double*>(D.slot[SL_X]);
+  const double U0 = sc->Ug[0], U1 = sc->Ug[1], U2 = sc->Ug[2];
+  const int warm = sc->warm;
+  double acc = 0.0;
+  const long long tot = (long long)c * V;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(gi / V);
+    const long long vox = gi - (long long)k * V;
+    const double uu = u[gi], vv = v[gi], aa = a[gi];
+    const double ut = uu + dt * vv + dt * dt * (0.5 - beta) * aa;
+    const double bv = rho_at<double>(D, vox) * ut;
+    double x0;
+    if (warm == 1)
+      x0 = uu + dt * vv + 0.5 * dt * dt * aa;
+    else if (warm == 2)
+      x0 = x[gi];  // prepared by the warm-start network
+    else
+      x0 = uu;
+    const bool isg = (D.mask[vox] >> k) & 1;
+    const double Uk = k == 0 ? U0 : (k == 1 ? U1 : U2);
+    if (isg) x0 = Uk;
+    b[gi] = bv;
+    x[gi] = x0;
+    if (!isg) {
+      double t = bv - U0 * w[gi];
+      if (nd > 1) t -= U1 * w[tot + gi];
+      if (nd > 2) t -= U2 * w[2 * tot + gi];
+      acc += t * t;
+    }
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+}
+
+// Corrector (Eq. Newmark): a_n = (u_n - u~)/(beta dt^2), v_n = v + dt((1-gamma) a + gamma a_n);
+// partial sums of rho a_n per component (total force on the prescribed region).
+__global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict__ dd) {
+  const Desc<double>& D = *dd;
+  const Scalars* sc = D.sc;
+  if (sc->status != 0) return;
+  const long long V = D.V;
+  const int c = D.c;
+  const double dt = D.dt, beta = D.beta, gamma = D.gamma;
+  const double theta = beta * dt * dt;
+  double* u = reinterpret_cast<double*>(D.slot[SL_U]);
+  double* v = reinterpret_cast<double*>(D.slot[SL_V]);
+  double* a = reinterpret_cast<double*>(D.slot[SL_A]);
+  const double* x = reinterpret_cast<const double*>(D.slot[SL_X]);
+  const bool zf = sc->zero_free != 0;
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long tot = (long long)c * V;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(gi / V);
+    const long long vox = gi - (long long)k * V;
+    const double uu = u[gi], vv = v[gi], aa = a[gi];
+    const double ut = uu + dt * vv + dt * dt * (0.5 - beta) * aa;
+    double xv = x[gi];
+    if (zf && !((D.mask[vox] >> k) & 1)) xv = 0.0;
+    const double an = (xv - ut) / theta;
+    const double vn = vv + dt * ((1.0 - gamma) * aa + gamma * an);
+    u[gi] = xv;
+    v[gi] = vn;
+    a[gi] = an;
+    const double f = rho_at<double>(D, vox) * an;
+    if (k == 0) acc[0] += f;
+    else if (k == 1) acc[1] += f;
+    else acc[2] += f;
+  }
+  for (int k = 0; k < 3; ++k) {
+    const double s = block_sum(acc[k]);
+    if (threadIdx.x == 0) D.part[k][blockIdx.x] = s;
+  }
+}
+
+// Unit lifting field E e_j: 1 on the prescribed DOFs of component j, 0 elsewhere.
+__global__ void k_fill_unit(const Desc<double>* __restrict__ dd, int j, double* dst) {
+  const Desc<double>& D = *dd;
+  const long long V = D.V;
+  const long long tot = (long long)D.c * V;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(gi / V);
+    const long long vox = gi - (long long)k * V;
+    dst[gi] = (k == j && ((D.mask[vox] >> k) & 1)) ? 1.0 : 0.0;
+  }
+}
+
+static int ew_blocks(const Plan<double>& P) {
+  const long long tot = (long long)P.h.c * P.h.V;
+  long long nb = (tot + 255) / 256;
+  if (nb > kEwBlocks) nb = kEwBlocks;
+  return (int)(nb < 1 ? 1 : nb);
+}
+
+void launch_predict(const Plan<double>& P, cudaStream_t st) { k_predict<<<ew_blocks(P), 256, 0, st>>>(P.d); }
+void launch_correct(const Plan<double>& P, cudaStream_t st) { k_correct<<<ew_blocks(P), 256, 0, st>>>(P.d); }
+void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st) {
+  k_fill_unit<<<ew_blocks(P), 256, 0, st>>>(P.d, j, dst);
+}
+int ew_block_count(const Plan<double>& P) { return ew_blocks(P); }
+
+// ---------------------------------------------------------------------------
+// finalize kernels (one block)
+// ---------------------------------------------------------------------------
+__device__ double fixed_order_sum(const double* p, int n) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+  return block_sum(s);
+}
+
+__global__ void k_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc,
+                      int mode, Scalars* sc2) {
+  const double sa = pa ? fixed_order_sum(pa, na) : 0.0;
+  const double sb = pb ? fixed_order_sum(pb, nb) : 0.0;
+  const double scc = pc ? fixed_order_sum(pc, nc) : 0.0;
+  if (threadIdx.x != 0) return;
+  // a finished solve is frozen: only the setup / bookkeeping modes still run
+  if (sc->done && mode != FIN_REF && mode != FIN_OUTER && mode != FIN_REACT) return;
+  switch (mode) {
+    case FIN_REF:
+      sc->ref2 = sa;
+      if (!isfinite(sa)) {
+        sc->status = 5;
+        sc->done = 1;
+      } else if (sa == 0.0) {
+        sc->zero_free = 1;
+        sc->converged = 1;
+        sc->done = 1;
+        sc->rr = 0.0;
+      }
+      break;
+    case FIN_RES0:
+      sc->rr = sa;
+      if (!isfinite(sa)) {
+        sc->status = 5;
+        sc->done = 1;
+      } else if (sa <= sc->tol2 * sc->ref2) {
+        sc->converged = 1;
+        sc->done = 1;
+      }
+      break;
+    case FIN_RZ0:
+      sc->rz = sb;
+      sc->first = 1;
+      if (!isfinite(sb) || !(sb > 0.0)) {
+        sc->status = 5;
+        sc->done = 1;
+      }
+      break;
+    case FIN_ALPHA:
+      sc->pq = sa;
+      sc->iter += 1;
+      if (!isfinite(sa) || !(sa > 0.0)) {
+        sc->status = 5;
+        sc->done = 1;
+      } else {
+        sc->alpha = sc->rz / sa;
+      }
+      break;
+    case FIN_BETA:
+      sc->rr = sa;
+      if (!isfinite(sa) || !isfinite(sb)) {
+        sc->status = 5;
+        sc->done = 1;
+      } else if (sa <= sc->tol2 * sc->ref2) {
+        sc->converged = 1;
+        sc->done = 1;
+      } else if (sc->iter >= sc->maxit) {
+        sc->status = 4;
+        sc->done = 1;
+      } else if (!(sb > 0.0)) {
+        sc->status = 5;
+        sc->done = 1;
+      } else {
+        sc->beta = sb / sc->rz;
+        sc->rz = sb;
+        sc->first = 0;
+      }
+      break;
+    case FIN_OUTER:
+      sc->rr = sa;
+      if (!isfinite(sa)) {
+        sc->status = 5;
+        sc->done = 1;
+        sc2->done = 1;
+      } else if (sa <= sc->tol2 * sc->ref2) {
+        sc->converged = 1;
+        sc->done = 1;
+        sc2->done = 1;
+      } else {
+        const double nr = sqrt(sa);
+        sc2->scale = 1.0 / nr;
+        sc2->xcoef = nr;
+        sc2->ref2 = 1.0;
+        sc2->iter = 0;
+        sc2->done = 0;
+        sc2->first = 1;
+        sc2->status = 0;
+        sc2->converged = 0;
+        sc2->zero_free = 0;
+      }
+      break;
+    case FIN_REACT:
+      sc->react[0] = sa;
+      sc->react[1] = sb;
+      sc->react[2] = scc;
+      break;
+    default:
+      break;
+  }
+}
+
+__global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, double tol2, int maxit) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  sc->Ug[0] = U0;
+  sc->Ug[1] = U1;
+  sc->Ug[2] = U2;
+  sc->warm = warm;
+  sc->tol2 = tol2;
+  sc->maxit = maxit;
+  sc->done = 0;
+  sc->status = 0;
+  sc->iter = 0;
+  sc->first = 1;
+  sc->zero_free = 0;
+  sc->converged = 0;
+  sc->scale = 1.0;
+  sc->xcoef = 1.0;
+  sc->rr = 0.0;
+  sc->rz = 0.0;
+  sc->alpha = 0.0;
+  sc->beta = 0.0;
+}
+
+__global__ void k_set_done(Scalars* sc, int done) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc->done = done;
+}
+
+void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc, int mode,
+                Scalars* sc2, cudaStream_t st) {
+  k_fin<<<1, 256, 0, st>>>(sc, pa, na, pb, nb, pc, nc, mode, sc2);
+}
+void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st) {
+  k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit);
+}
+void launch_set_done(Scalars* sc, int done, cudaStream_t st) { k_set_done<<<1, 32, 0, st>>>(sc, done); }
+
+}  // namespace wfft

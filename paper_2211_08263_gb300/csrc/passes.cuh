@@ -1,0 +1,514 @@
+// Pass kernels of the spectral operator and preconditioner.
+//
+// A 3-D real field goes through the half spectrum as
+//   x pass (real <-> complex along x_1, two real lines packed per complex line)
+//   y pass (complex along x_2), z pass (complex along x_3),
+// and the pointwise work of the method is fused into these passes:
+//   * operator A of Eq. Fourier_ND_A:
+//       xfwd(p) -> y fwd -> z[fwd, eps^ = sym(i xi (x) u^), inv] -> y inv
+//       -> x[inv, sigma = C(x) : eps, fwd] -> y fwd -> z[fwd, t^ = i xi . sigma^, inv]
+//       -> y inv -> xinv[q = -theta t + rho p, mask]
+//   * preconditioner of Eq. precond / Eq. acous:
+//       xfwd(r) -> y fwd -> z[fwd, z^ = (theta K(xi) + rho_bar I)^-1 r^, inv] -> y inv -> xinv[mask]
+//   * Krylov vector updates (x += alpha p, r -= alpha q, p = z + beta p), the
+//     Fourier-space (r, z) by Parseval and (p, q), ||r||^2 as FP64 block partial sums.
+// In 2-D (N3 = 1) the y pass hosts the spectral multiply and there is no
+// middle pass.  Strains are engineering (gamma_ij = 2 eps_ij, Voigt order
+// 11,22,33,23,13,12; 2-D: 11,22,12) so sigma = Cv e with the Voigt matrix Cv.
+// The DFT is unnormalised; 1/V is folded into the spectral multiplies.
+#pragma once
+#include "common.cuh"
+#include "fft_core.cuh"
+
+namespace wfft {
+
+enum { PRE_PLAIN = 0, PRE_PUPD = 1, PRE_RUPD = 2, PRE_CONV = 3 };
+enum { POST_APPLY = 0, POST_RESID = 1, POST_PREC = 2 };
+enum { OP_FWD = 0, OP_INV = 1, OP_GRAD = 2, OP_DIV = 3, OP_PREC = 4 };
+
+template <typename T>
+__device__ __forceinline__ T rho_at(const Desc<T>& D, long long vox) {
+  return D.rhotab[D.phase ? (long long)D.phase[vox] : vox];
+}
+
+// Element x of real line q (pair q/2, part q&1) of a packed buffer.
+template <typename T>
+__device__ __forceinline__ T& packed(cplx<T>* buf, int lstr, int q, int x) {
+  return reinterpret_cast<T*>(buf + (size_t)(q >> 1) * lstr + x)[q & 1];
+}
+
+// Split the complex FFT of two packed real lines into their half spectra and
+// store them: A = (Z_k + conj Z_{N-k})/2, B = (Z_k - conj Z_{N-k})/(2i).
+template <typename T>
+__device__ __forceinline__ void store_unpacked(const Desc<T>& D, const cplx<T>* buf, int lstr, int nlines_real,
+                                               long long l0, int nc, long long nsp) {
+  const int N = D.n1, nh = D.nh;
+  const int npairs = nlines_real >> 1;
+  for (int e = threadIdx.x; e < npairs * nh; e += blockDim.x) {
+    const int kx = e % nh, p = e / nh;
+    const cplx<T> Z = buf[(size_t)p * lstr + kx];
+    const cplx<T> W = buf[(size_t)p * lstr + (kx == 0 ? 0 : N - kx)];
+    const T h = (T)0.5;
+    const cplx<T> A = cmake<T>((Z.x + W.x) * h, (Z.y - W.y) * h);
+    const cplx<T> B = cmake<T>((Z.y + W.y) * h, (W.x - Z.x) * h);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int q = 2 * p + half;
+      const int l = q / nc, k = q % nc;
+      const long long line = l0 + l;
+      if (line < nsp) D.spec[(long long)k * D.Vh + line * D.pitch + kx] = half ? B : A;
+    }
+  }
+}
+
+// Load the half spectra of two real lines per complex line as Z = A + i B
+// over the full length (Hermitian extension); DC and Nyquist take real parts.
+template <typename T>
+__device__ __forceinline__ void load_packed(const Desc<T>& D, cplx<T>* buf, int lstr, int nlines_real, long long l0,
+                                            int nc, long long nsp) {
+  const int N = D.n1, nh = D.nh;
+  const int npairs = nlines_real >> 1;
+  for (int e = threadIdx.x; e < npairs * nh; e += blockDim.x) {
+    const int kx = e % nh, p = e / nh;
+    cplx<T> A = cmake<T>(0, 0), B = cmake<T>(0, 0);
+    const int qa = 2 * p, qb = 2 * p + 1;
+    const long long la = l0 + qa / nc, lb = l0 + qb / nc;
+    if (la < nsp) A = D.spec[(long long)(qa % nc) * D.Vh + la * D.pitch + kx];
+    if (lb < nsp) B = D.spec[(long long)(qb % nc) * D.Vh + lb * D.pitch + kx];
+    cplx<T>* row = buf + (size_t)p * lstr;
+    if (kx == 0 || 2 * kx == N) {
+      row[kx] = cmake<T>(A.x, B.x);
+    } else {
+      row[kx] = cmake<T>(A.x - B.y, A.y + B.x);
+      row[N - kx] = cmake<T>(A.x + B.y, B.x - A.y);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cplx<T>* tw, const cplx<T>* src, int N) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// x forward pass: real c-component field -> half spectrum, with fused updates
+// ---------------------------------------------------------------------------
+template <typename T, int PRE>
+__global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, int LX, int in_slot) {
+  const Desc<T>& D = *dd;
+  Scalars* sc = D.sc;
+  if (sc->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = D.n1, nc = D.c;
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* buf = tw + N;
+  const int lstr = N;
+  const long long nsp = (long long)D.n2 * D.n3;
+  const long long l0 = (long long)blockIdx.x * LX;
+  const long long V = D.V;
+  load_twiddles<T>(tw, D.tw[0], N);
+  bool first = false;
+  T beta = 0, alpha = 0;
+  double xa = 0.0, scale = 1.0;
+  if (PRE == PRE_PUPD) {
+    first = sc->first != 0;
+    beta = (T)sc->beta;
+  }
+  if (PRE == PRE_RUPD) {
+    alpha = (T)sc->alpha;
+    xa = sc->alpha * sc->xcoef;
+  }
+  if (PRE == PRE_CONV) scale = sc->scale;
+  double acc = 0.0;
+  const int tot = LX * nc * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int x = e % N, q = e / N;
+    const int k = q % nc, l = q / nc;
+    const long long line = l0 + l;
+    T val = 0;
+    if (line < nsp) {
+      const long long gi = (long long)k * V + line * N + x;
+      if (PRE == PRE_PLAIN) {
+        val = reinterpret_cast<const T*>(D.slot[in_slot])[gi];
+      } else if (PRE == PRE_PUPD) {
+        T* p = reinterpret_cast<T*>(D.slot[SL_P]);
+        const T zv = reinterpret_cast<const T*>(D.slot[SL_Z])[gi];
+        const T pv = first ? zv : zv + beta * p[gi];
+        p[gi] = pv;
+        val = pv;
+      } else if (PRE == PRE_RUPD) {
+        double* xs = reinterpret_cast<double*>(D.slot[SL_X]);
+        const T pv = reinterpret_cast<const T*>(D.slot[SL_P])[gi];
+        const T qv = reinterpret_cast<const T*>(D.slot[SL_Q])[gi];
+        T* r = reinterpret_cast<T*>(D.slot[SL_R]);
+        xs[gi] += xa * (double)pv;
+        const T rv = r[gi] - alpha * qv;
+        r[gi] = rv;
+        val = rv;
+        acc += (double)rv * (double)rv;
+      } else {  // PRE_CONV: r = scale * r64 in T
+        const double rv64 = reinterpret_cast<const double*>(D.slot[SL_R64])[gi];
+        const T rv = (T)(rv64 * scale);
+        reinterpret_cast<T*>(D.slot[SL_R])[gi] = rv;
+        val = rv;
+      }
+    }
+    packed<T>(buf, lstr, q, x) = val;
+  }
+  if (PRE == PRE_RUPD) {
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+  }
+  __syncthreads();
+  fft_lines<T>(buf, D.ax[0], LX * nc / 2, lstr, 1, tw, -1, false);
+  store_unpacked<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
+}
+
+// ---------------------------------------------------------------------------
+// x inverse pass: half spectrum -> real field with fused epilogue
+// ---------------------------------------------------------------------------
+template <typename T, int POST>
+__global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, int LX, int in_slot, int out_slot,
+                                              int masked, int want_dot) {
+  const Desc<T>& D = *dd;
+  Scalars* sc = D.sc;
+  if (sc->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = D.n1, nc = D.c;
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* buf = tw + N;
+  const int lstr = N;
+  const long long nsp = (long long)D.n2 * D.n3;
+  const long long l0 = (long long)blockIdx.x * LX;
+  const long long V = D.V;
+  load_twiddles<T>(tw, D.tw[0], N);
+  load_packed<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
+  __syncthreads();
+  fft_lines<T>(buf, D.ax[0], LX * nc / 2, lstr, 1, tw, +1, false);
+  double acc = 0.0;
+  const int tot = LX * nc * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int x = e % N, q = e / N;
+    const int k = q % nc, l = q / nc;
+    const long long line = l0 + l;
+    if (line >= nsp) continue;
+    const long long vox = line * N + x;
+    const long long gi = (long long)k * V + vox;
+    const T t = packed<T>(buf, lstr, q, x);
+    const bool isg = masked && ((D.mask[vox] >> k) & 1);
+    if (POST == POST_APPLY) {
+      const T pin = reinterpret_cast<const T*>(D.slot[in_slot])[gi];
+      T qv = t + rho_at<T>(D, vox) * pin;
+      if (isg) qv = 0;
+      reinterpret_cast<T*>(D.slot[out_slot])[gi] = qv;
+      acc += (double)pin * (double)qv;
+    } else if (POST == POST_RESID) {
+      const T xv = reinterpret_cast<const T*>(D.slot[SL_X])[gi];
+      const T bv = reinterpret_cast<const T*>(D.slot[SL_B])[gi];
+      T rv = bv - (t + rho_at<T>(D, vox) * xv);
+      if (isg) rv = 0;
+      reinterpret_cast<T*>(D.slot[SL_R64])[gi] = rv;
+      acc += (double)rv * (double)rv;
+    } else {  // POST_PREC
+      reinterpret_cast<T*>(D.slot[out_slot])[gi] = isg ? (T)0 : t;
+    }
+  }
+  if (POST != POST_PREC && want_dot) {
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x middle pass: strain half spectra -> real strains -> sigma = C(x):e -> stress half spectra
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void hooke3(const T* __restrict__ C, T* e) {
+  const T e0 = e[0], e1 = e[1], e2 = e[2], e3 = e[3], e4 = e[4], e5 = e[5];
+  e[0] = C[0] * e0 + C[1] * e1 + C[2] * e2 + C[3] * e3 + C[4] * e4 + C[5] * e5;
+  e[1] = C[1] * e0 + C[6] * e1 + C[7] * e2 + C[8] * e3 + C[9] * e4 + C[10] * e5;
+  e[2] = C[2] * e0 + C[7] * e1 + C[11] * e2 + C[12] * e3 + C[13] * e4 + C[14] * e5;
+  e[3] = C[3] * e0 + C[8] * e1 + C[12] * e2 + C[15] * e3 + C[16] * e4 + C[17] * e5;
+  e[4] = C[4] * e0 + C[9] * e1 + C[13] * e2 + C[16] * e3 + C[18] * e4 + C[19] * e5;
+  e[5] = C[5] * e0 + C[10] * e1 + C[14] * e2 + C[17] * e3 + C[19] * e4 + C[20] * e5;
+}
+template <typename T>
+__device__ __forceinline__ void hooke2(const T* __restrict__ C, T* e) {
+  const T e0 = e[0], e1 = e[1], e2 = e[2];
+  e[0] = C[0] * e0 + C[1] * e1 + C[2] * e2;
+  e[1] = C[1] * e0 + C[3] * e1 + C[4] * e2;
+  e[2] = C[2] * e0 + C[4] * e1 + C[5] * e2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, int LX) {
+  const Desc<T>& D = *dd;
+  if (D.sc->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = D.n1, ns = D.s;
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* buf = tw + N;
+  const int lstr = N;
+  const long long nsp = (long long)D.n2 * D.n3;
+  const long long l0 = (long long)blockIdx.x * LX;
+  load_twiddles<T>(tw, D.tw[0], N);
+  load_packed<T>(D, buf, lstr, LX * ns, l0, ns, nsp);
+  __syncthreads();
+  fft_lines<T>(buf, D.ax[0], LX * ns / 2, lstr, 1, tw, +1, false);
+  const int cstride = (ns == 6) ? kCtabStride3 : kCtabStride2;
+  for (int e = threadIdx.x; e < LX * N; e += blockDim.x) {
+    const int x = e % N, l = e / N;
+    const long long line = l0 + l;
+    if (line >= nsp) continue;
+    const long long vox = line * N + x;
+    const long long row = D.phase ? (long long)D.phase[vox] : vox;
+    const T* C = D.ctab + row * cstride;
+    T ev[6];
+    for (int k = 0; k < ns; ++k) ev[k] = packed<T>(buf, lstr, l * ns + k, x);
+    if (ns == 6)
+      hooke3<T>(C, ev);
+    else
+      hooke2<T>(C, ev);
+    for (int k = 0; k < ns; ++k) packed<T>(buf, lstr, l * ns + k, x) = ev[k];
+  }
+  __syncthreads();
+  fft_lines<T>(buf, D.ax[0], LX * ns / 2, lstr, 1, tw, -1, false);
+  store_unpacked<T>(D, buf, lstr, LX * ns, l0, ns, nsp);
+}
+
+// ---------------------------------------------------------------------------
+// column passes (y or z): tiles of BX consecutive kx columns x the full axis
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ColGeo {
+  int N;          // axis length
+  long long est;  // global stride between consecutive axis elements
+  long long base; // global offset of element 0 of column kx0 (component 0)
+  int kx0;
+  int outer;      // the other column axis' index (a frequency index after its forward pass)
+};
+
+template <typename T>
+__device__ __forceinline__ ColGeo<T> col_geo(const Desc<T>& D, int axis, int BX) {
+  ColGeo<T> g;
+  const int ntx = (D.nh + BX - 1) / BX;
+  const int tile = blockIdx.x % ntx;
+  const int o = blockIdx.x / ntx;
+  g.kx0 = tile * BX;
+  g.outer = o;
+  if (axis == 1) {
+    g.N = D.n2;
+    g.est = D.pitch;
+    g.base = (long long)o * D.n2 * D.pitch + g.kx0;
+  } else {
+    g.N = D.n3;
+    g.est = (long long)D.n2 * D.pitch;
+    g.base = (long long)o * D.pitch + g.kx0;
+  }
+  return g;
+}
+
+template <typename T>
+__device__ __forceinline__ void col_load(const Desc<T>& D, const ColGeo<T>& g, int BX, int comp, cplx<T>* t) {
+  const cplx<T>* src = D.spec + (long long)comp * D.Vh + g.base;
+  for (int e = threadIdx.x; e < g.N * BX; e += blockDim.x) {
+    const int y = e / BX, b = e % BX;
+    t[e] = (g.kx0 + b < D.nh) ? src[(long long)y * g.est + b] : cmake<T>(0, 0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void col_store(const Desc<T>& D, const ColGeo<T>& g, int BX, int comp, const cplx<T>* t) {
+  cplx<T>* dst = D.spec + (long long)comp * D.Vh + g.base;
+  for (int e = threadIdx.x; e < g.N * BX; e += blockDim.x) {
+    const int y = e / BX, b = e % BX;
+    if (g.kx0 + b < D.nh) dst[(long long)y * g.est + b] = t[e];
+  }
+}
+
+// frequency vector of tile element e (axis index y, column b)
+template <typename T>
+__device__ __forceinline__ void col_xi(const Desc<T>& D, const ColGeo<T>& g, int axis, int BX, int e, T& x1, T& x2,
+                                       T& x3) {
+  const int y = e / BX, b = e % BX;
+  x1 = (T)xi_of(g.kx0 + b, D.n1, D.kx1);
+  if (axis == 2) {
+    x2 = (T)xi_of(g.outer, D.n2, D.kx2);
+    x3 = (T)xi_of(y, D.n3, D.kx3);
+  } else {
+    x2 = (T)xi_of(y, D.n2, D.kx2);
+    x3 = (T)xi_of(g.outer, D.n3, D.kx3);
+  }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) k_col(const Desc<T>* __restrict__ dd, int axis, int BX, int ncomp) {
+  const Desc<T>& D = *dd;
+  Scalars* sc = D.sc;
+  if (sc->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const ColGeo<T> g = col_geo<T>(D, axis, BX);
+  const int N = g.N;
+  const int TS = N * BX;  // tile size
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* tl = tw + N;   // tiles
+  load_twiddles<T>(tw, D.tw[axis], N);
+  const AxisPlan pl = D.ax[axis];
+  if (OP == OP_FWD || OP == OP_INV) {
+    const int sgn = (OP == OP_FWD) ? -1 : +1;
+    for (int k = 0; k < ncomp; ++k) {
+      col_load<T>(D, g, BX, k, tl);
+      __syncthreads();
+      fft_lines<T>(tl, pl, BX, 1, BX, tw, sgn, true);
+      col_store<T>(D, g, BX, k, tl);
+      __syncthreads();
+    }
+    return;
+  }
+  const int c = D.c;
+  if (OP == OP_GRAD) {
+    // inputs u^_k in tiles 0..c-1, work tile c
+    for (int k = 0; k < c; ++k) col_load<T>(D, g, BX, k, tl + k * TS);
+    __syncthreads();
+    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, -1, true);
+    cplx<T>* W = tl + c * TS;
+    const T iv = D.invV;
+    // engineering shear strains first (they need the unmodified inputs)
+    const int nsh = (c == 3) ? 3 : 1;
+    for (int m = 0; m < nsh; ++m) {
+      for (int e = threadIdx.x; e < TS; e += blockDim.x) {
+        T x1, x2, x3;
+        col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
+        cplx<T> v;
+        if (c == 3) {
+          const cplx<T> u1 = tl[e], u2 = tl[TS + e], u3 = tl[2 * TS + e];
+          if (m == 0) v = cadd<T>(cscale<T>(u3, x2), cscale<T>(u2, x3));        // gamma_23
+          else if (m == 1) v = cadd<T>(cscale<T>(u3, x1), cscale<T>(u1, x3));   // gamma_13
+          else v = cadd<T>(cscale<T>(u2, x1), cscale<T>(u1, x2));               // gamma_12
+        } else {
+          const cplx<T> u1 = tl[e], u2 = tl[TS + e];
+          v = cadd<T>(cscale<T>(u2, x1), cscale<T>(u1, x2));                    // gamma_12
+        }
+        W[e] = cmuli<T>(cscale<T>(v, iv), +1);
+      }
+      __syncthreads();
+      fft_lines<T>(W, pl, BX, 1, BX, tw, +1, true);
+      col_store<T>(D, g, BX, c + m, W);
+      __syncthreads();
+    }
+    // normal strains in place: e_kk = i xi_k u^_k
+    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
+      T x1, x2, x3;
+      col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
+      tl[e] = cmuli<T>(cscale<T>(tl[e], x1 * iv), +1);
+      tl[TS + e] = cmuli<T>(cscale<T>(tl[TS + e], x2 * iv), +1);
+      if (c == 3) tl[2 * TS + e] = cmuli<T>(cscale<T>(tl[2 * TS + e], x3 * iv), +1);
+    }
+    __syncthreads();
+    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, +1, true);
+    for (int k = 0; k < c; ++k) col_store<T>(D, g, BX, k, tl + k * TS);
+    return;
+  }
+  if (OP == OP_DIV) {
+    // accumulators t^_k in tiles 0..c-1, work tile c; t^_i = -theta/V * i xi_j sigma^_ij
+    cplx<T>* W = tl + c * TS;
+    for (int e = threadIdx.x; e < c * TS; e += blockDim.x) tl[e] = cmake<T>(0, 0);
+    const T f = D.mthetaInvV;
+    const int ns = D.s;
+    for (int I = 0; I < ns; ++I) {
+      col_load<T>(D, g, BX, I, W);
+      __syncthreads();
+      fft_lines<T>(W, pl, BX, 1, BX, tw, -1, true);
+      for (int e = threadIdx.x; e < TS; e += blockDim.x) {
+        T x1, x2, x3;
+        col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
+        const cplx<T> s = cmuli<T>(cscale<T>(W[e], f), +1);  // i f sigma^
+        if (c == 3) {
+          switch (I) {
+            case 0: tl[e] = cadd<T>(tl[e], cscale<T>(s, x1)); break;
+            case 1: tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x2)); break;
+            case 2: tl[2 * TS + e] = cadd<T>(tl[2 * TS + e], cscale<T>(s, x3)); break;
+            case 3:
+              tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x3));
+              tl[2 * TS + e] = cadd<T>(tl[2 * TS + e], cscale<T>(s, x2));
+              break;
+            case 4:
+              tl[e] = cadd<T>(tl[e], cscale<T>(s, x3));
+              tl[2 * TS + e] = cadd<T>(tl[2 * TS + e], cscale<T>(s, x1));
+              break;
+            default:
+              tl[e] = cadd<T>(tl[e], cscale<T>(s, x2));
+              tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x1));
+              break;
+          }
+        } else {
+          if (I == 0) tl[e] = cadd<T>(tl[e], cscale<T>(s, x1));
+          else if (I == 1) tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x2));
+          else {
+            tl[e] = cadd<T>(tl[e], cscale<T>(s, x2));
+            tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x1));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, +1, true);
+    for (int k = 0; k < c; ++k) col_store<T>(D, g, BX, k, tl + k * TS);
+    return;
+  }
+  if (OP == OP_PREC) {
+    for (int k = 0; k < c; ++k) col_load<T>(D, g, BX, k, tl + k * TS);
+    __syncthreads();
+    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, -1, true);
+    double acc = 0.0;
+    const T iv = D.invV;
+    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
+      T x1, x2, x3;
+      col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
+      const int kx = g.kx0 + (e % BX);
+      const double wgt = (kx >= D.nh) ? 0.0 : ((kx == 0 || 2 * kx == D.n1) ? 1.0 : 2.0);
+      const T m0 = x1 * x1, m1 = x2 * x2, m2 = x3 * x3, m3 = x2 * x3, m4 = x1 * x3, m5 = x1 * x2;
+      T Mv[6];
+#pragma unroll
+      for (int pr = 0; pr < 6; ++pr)
+        Mv[pr] = D.kq[pr][0] * m0 + D.kq[pr][1] * m1 + D.kq[pr][2] * m2 + D.kq[pr][3] * m3 + D.kq[pr][4] * m4 +
+                 D.kq[pr][5] * m5;
+      Mv[0] += D.rhobar;
+      Mv[1] += D.rhobar;
+      Mv[2] += D.rhobar;
+      if (c == 3) {
+        const T a = Mv[0], b = Mv[1], cc = Mv[2], f = Mv[3], ee = Mv[4], d = Mv[5];
+        const T A00 = b * cc - f * f, A11 = a * cc - ee * ee, A22 = a * b - d * d;
+        const T A01 = ee * f - d * cc, A02 = d * f - b * ee, A12 = d * ee - a * f;
+        const T det = a * A00 + d * A01 + ee * A02;
+        const T id = iv / det;
+        const cplx<T> r1 = tl[e], r2 = tl[TS + e], r3 = tl[2 * TS + e];
+        const cplx<T> z1 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A00), cscale<T>(r2, A01)), cscale<T>(r3, A02)), id);
+        const cplx<T> z2 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A01), cscale<T>(r2, A11)), cscale<T>(r3, A12)), id);
+        const cplx<T> z3 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A02), cscale<T>(r2, A12)), cscale<T>(r3, A22)), id);
+        acc += wgt * ((double)r1.x * z1.x + (double)r1.y * z1.y + (double)r2.x * z2.x + (double)r2.y * z2.y +
+                      (double)r3.x * z3.x + (double)r3.y * z3.y);
+        tl[e] = z1;
+        tl[TS + e] = z2;
+        tl[2 * TS + e] = z3;
+      } else {
+        const T a = Mv[0], b = Mv[1], d = Mv[5];
+        const T id = iv / (a * b - d * d);
+        const cplx<T> r1 = tl[e], r2 = tl[TS + e];
+        const cplx<T> z1 = cscale<T>(csub<T>(cscale<T>(r1, b), cscale<T>(r2, d)), id);
+        const cplx<T> z2 = cscale<T>(csub<T>(cscale<T>(r2, a), cscale<T>(r1, d)), id);
+        acc += wgt * ((double)r1.x * z1.x + (double)r1.y * z1.y + (double)r2.x * z2.x + (double)r2.y * z2.y);
+        tl[e] = z1;
+        tl[TS + e] = z2;
+      }
+    }
+    const double s = block_sum(acc);  // contains barriers
+    if (threadIdx.x == 0) D.part[PT_B][blockIdx.x] = s;
+    __syncthreads();
+    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, +1, true);
+    for (int k = 0; k < c; ++k) col_store<T>(D, g, BX, k, tl + k * TS);
+    return;
+  }
+}
+
+}  // namespace wfft
