@@ -578,7 +578,7 @@ static int pcg_loop(wfft_handle* h, Plan<T>& P, Scalars* sc, int which, int budg
       launch_apply<T>(P, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, h->st);
       launch_fin(sc, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_ALPHA, nullptr, h->st);
       launch_precond<T>(P, PRE_RUPD, SL_R, SL_Z, 1, h->st);
-      launch_fin(sc, D.part[PT_A], P.g.blk_x, D.part[PT_B], P.g.blk_col[op], nullptr, 0, FIN_BETA, nullptr, h->st);
+      launch_fin(sc, D.part[PT_A], P.g.blk_x, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_BETA, nullptr, h->st);
       ++launched;
     }
     CKH(h, cudaGetLastError());
@@ -608,7 +608,7 @@ static int solve_core(wfft_handle* h, wfft_step_info* info) {
     launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
     launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_RES0, nullptr, h->st);
     launch_precond<double>(P, PRE_PLAIN, SL_R, SL_Z, 1, h->st);
-    launch_fin(h->sc64, nullptr, 0, D.part[PT_B], P.g.blk_col[op], nullptr, 0, FIN_RZ0, nullptr, h->st);
+    launch_fin(h->sc64, nullptr, 0, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, h->st);
     outer = 1;
     int rc = pcg_loop<double>(h, P, h->sc64, 0, watchdog, &iters);
     if (rc == WFFT_ETIMEOUT) status = WFFT_ETIMEOUT;
@@ -638,7 +638,7 @@ static int solve_core(wfft_handle* h, wfft_step_info* info) {
       }
       ++sweeps;
       launch_precond<float>(F, PRE_CONV, SL_R, SL_Z, 1, h->st);
-      launch_fin(h->sc32, nullptr, 0, DF.part[PT_B], F.g.blk_col[DF.opAxis], nullptr, 0, FIN_RZ0, nullptr, h->st);
+      launch_fin(h->sc32, nullptr, 0, DF.part[PT_B], F.g.blk_col[DF.opAxis][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, h->st);
       int it = 0;
       rc = pcg_loop<float>(h, F, h->sc32, 1, std::max(1, watchdog - iters), &it);
       iters += it;

@@ -135,34 +135,39 @@ struct Dft<T, 7> {
 };
 
 // One in-place Stockham stage over `nlines` lines of length N.
-// Element e of line l sits at buf[l * lstride + e * estride].
-// line_fastest: consecutive threads take consecutive lines (column tiles,
-// estride > 1) instead of consecutive butterflies (row tiles, estride = 1),
-// which keeps shared-memory accesses conflict-free in both layouts.
-template <typename T, int R>
-__device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int lstride, int estride, int Ns,
-                                          const cplx<T>* tw, int sgn, bool line_fastest) {
+// Row tiles (ES == 1): element e of line l at buf[l * lstride + e]; consecutive
+// threads take consecutive butterflies of a line.  Column tiles (ES > 1):
+// element e of line l at buf[l + e * ES]; consecutive threads take consecutive
+// lines.  Both keep shared-memory accesses conflict-free; a compile-time ES
+// keeps the address arithmetic to shifts.
+template <typename T, int R, int ES>
+__device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int lstride, int Ns, const cplx<T>* tw,
+                                          int sgn) {
   constexpr int NB = NbOf<T, R>::v;
+  constexpr bool LF = ES > 1;
   const int nb = N / R;
   const int total = nb * nlines;
   const int nthr = blockDim.x;
-  const int tid = threadIdx.x;
+  // read the thread index opaquely: keeps the compiler from hoisting every
+  // stage's index arithmetic out of the callers' loops (register pressure)
+  int tid;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
   cplx<T> v[NB][R];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int id = tid + i * nthr;
     if (id < total) {
       int line, j;
-      if (line_fastest) {
+      if (LF) {
         line = id % nlines;
         j = id / nlines;
       } else {
         j = id % nb;
         line = id / nb;
       }
-      const cplx<T>* src = buf + (size_t)line * lstride;
+      const cplx<T>* src = LF ? buf + line : buf + (size_t)line * lstride;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = src[(j + r * nb) * estride];
+      for (int r = 0; r < R; ++r) v[i][r] = src[(j + r * nb) * ES];
     }
   }
   __syncthreads();
@@ -171,7 +176,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
     const int id = tid + i * nthr;
     if (id < total) {
       int line, j;
-      if (line_fastest) {
+      if (LF) {
         line = id % nlines;
         j = id / nlines;
       } else {
@@ -189,10 +194,10 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
         }
       }
       Dft<T, R>::run(v[i], sgn, tw, N);
-      cplx<T>* dst = buf + (size_t)line * lstride;
+      cplx<T>* dst = LF ? buf + line : buf + (size_t)line * lstride;
       const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[(base + r * Ns) * estride] = v[i][r];
+      for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ES] = v[i][r];
     }
   }
   __syncthreads();
@@ -201,19 +206,20 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
 // Full transform of `nlines` lines.  sgn = -1 forward, +1 inverse (unnormalised).
 // Stages are applied radix by radix (8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
 // formulation is valid for any order of the radices, and one loop per radix
-// keeps each stage's registers apart.  Must be called by every thread of the
-// block (contains barriers).
-template <typename T>
-__device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int nlines, int lstride, int estride,
-                                          const cplx<T>* tw, int sgn, bool line_fastest) {
+// keeps each stage's registers apart.  ES = 1: row tiles with line stride
+// `lstride`; ES > 1: column tiles (line stride 1, element stride ES).
+// Must be called by every thread of the block (contains barriers).
+template <typename T, int ES>
+__device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int nlines, int lstride, const cplx<T>* tw,
+                                          int sgn) {
   const int N = pl.n;
   int Ns = 1;
-  for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
-  for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
-  for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
-  for (int s = 0; s < pl.cnt[3]; ++s, Ns *= 3) fft_stage<T, 3>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
-  for (int s = 0; s < pl.cnt[4]; ++s, Ns *= 5) fft_stage<T, 5>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
-  for (int s = 0; s < pl.cnt[5]; ++s, Ns *= 7) fft_stage<T, 7>(buf, N, nlines, lstride, estride, Ns, tw, sgn, line_fastest);
+  for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[3]; ++s, Ns *= 3) fft_stage<T, 3, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[4]; ++s, Ns *= 5) fft_stage<T, 5, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[5]; ++s, Ns *= 7) fft_stage<T, 7, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
 }
 
 }  // namespace wfft

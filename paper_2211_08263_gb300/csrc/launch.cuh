@@ -10,13 +10,13 @@
 namespace wfft {
 
 struct PassGeo {
-  int LX, LXm;         // spatial x lines per block (c-component passes / s-component pass)
-  int BX;              // kx columns per column tile
-  int thr;             // threads per block
-  int blk_x, blk_xm;   // grid sizes of the x passes
-  int blk_col[3];      // grid size of a column pass along axis 1, 2
-  size_t sm_x, sm_xm;  // dynamic shared memory
-  size_t sm_col[3][5]; // [axis][op]
+  int LX, LXm;          // spatial x lines per block (c-component passes / s-component pass)
+  int thr;              // threads per block of the x passes
+  int blk_x, blk_xm;    // grid sizes of the x passes
+  size_t sm_x, sm_xm;   // dynamic shared memory of the x passes
+  int bx[3][5];         // [axis][op] kx columns per column tile
+  int blk_col[3][5];    // [axis][op] grid size (x dimension)
+  size_t sm_col[3][5];  // [axis][op] dynamic shared memory
   int max_blocks;
 };
 

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, in
     if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
   }
   __syncthreads();
-  fft_lines<T>(buf, D.ax[0], LX * nc / 2, lstr, 1, tw, -1, false);
+  fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, lstr, tw, -1);
   store_unpacked<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
 }
 
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, in
   load_twiddles<T>(tw, D.tw[0], N);
   load_packed<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
   __syncthreads();
-  fft_lines<T>(buf, D.ax[0], LX * nc / 2, lstr, 1, tw, +1, false);
+  fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, lstr, tw, +1);
   double acc = 0.0;
   const int tot = LX * nc * N;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, in
   load_twiddles<T>(tw, D.tw[0], N);
   load_packed<T>(D, buf, lstr, LX * ns, l0, ns, nsp);
   __syncthreads();
-  fft_lines<T>(buf, D.ax[0], LX * ns / 2, lstr, 1, tw, +1, false);
+  fft_lines<T, 1>(buf, D.ax[0], LX * ns / 2, lstr, tw, +1);
   const int cstride = (ns == 6) ? kCtabStride3 : kCtabStride2;
   for (int e = threadIdx.x; e < LX * N; e += blockDim.x) {
     const int x = e % N, l = e / N;
@@ -272,13 +272,20 @@ __global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, in
     for (int k = 0; k < ns; ++k) packed<T>(buf, lstr, l * ns + k, x) = ev[k];
   }
   __syncthreads();
-  fft_lines<T>(buf, D.ax[0], LX * ns / 2, lstr, 1, tw, -1, false);
+  fft_lines<T, 1>(buf, D.ax[0], LX * ns / 2, lstr, tw, -1);
   store_unpacked<T>(D, buf, lstr, LX * ns, l0, ns, nsp);
 }
 
 // ---------------------------------------------------------------------------
-// column passes (y or z): tiles of BX consecutive kx columns x the full axis
+// column passes (y or z): tiles of BX consecutive kx columns x the full axis.
+// The tiles of all components a pass needs sit interleaved in shared memory,
+// element (slot t, axis index y, column b) at  y * NS * BX + t * BX + b,  so that
+// each kernel runs exactly one forward and one inverse batched FFT over all of
+// its lines (line stride 1, element stride NS * BX).
 // ---------------------------------------------------------------------------
+constexpr int kColThreadsPlain = 256;  // plain transforms (one component per block)
+constexpr int kColThreadsOp = 512;     // fused gradient / divergence / preconditioner
+
 template <typename T>
 struct ColGeo {
   int N;          // axis length
@@ -308,29 +315,29 @@ __device__ __forceinline__ ColGeo<T> col_geo(const Desc<T>& D, int axis, int BX)
   return g;
 }
 
-template <typename T>
-__device__ __forceinline__ void col_load(const Desc<T>& D, const ColGeo<T>& g, int BX, int comp, cplx<T>* t) {
+template <typename T, int BX, int ES>
+__device__ __forceinline__ void col_load(const Desc<T>& D, const ColGeo<T>& g, int comp, cplx<T>* tl, int slot) {
   const cplx<T>* src = D.spec + (long long)comp * D.Vh + g.base;
   for (int e = threadIdx.x; e < g.N * BX; e += blockDim.x) {
     const int y = e / BX, b = e % BX;
-    t[e] = (g.kx0 + b < D.nh) ? src[(long long)y * g.est + b] : cmake<T>(0, 0);
+    tl[y * ES + slot * BX + b] = (g.kx0 + b < D.nh) ? src[(long long)y * g.est + b] : cmake<T>(0, 0);
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void col_store(const Desc<T>& D, const ColGeo<T>& g, int BX, int comp, const cplx<T>* t) {
+template <typename T, int BX, int ES>
+__device__ __forceinline__ void col_store(const Desc<T>& D, const ColGeo<T>& g, int comp, const cplx<T>* tl,
+                                          int slot) {
   cplx<T>* dst = D.spec + (long long)comp * D.Vh + g.base;
   for (int e = threadIdx.x; e < g.N * BX; e += blockDim.x) {
     const int y = e / BX, b = e % BX;
-    if (g.kx0 + b < D.nh) dst[(long long)y * g.est + b] = t[e];
+    if (g.kx0 + b < D.nh) dst[(long long)y * g.est + b] = tl[y * ES + slot * BX + b];
   }
 }
 
-// frequency vector of tile element e (axis index y, column b)
+// frequency vector of tile element (axis index y, column b)
 template <typename T>
-__device__ __forceinline__ void col_xi(const Desc<T>& D, const ColGeo<T>& g, int axis, int BX, int e, T& x1, T& x2,
+__device__ __forceinline__ void col_xi(const Desc<T>& D, const ColGeo<T>& g, int axis, int y, int b, T& x1, T& x2,
                                        T& x3) {
-  const int y = e / BX, b = e % BX;
   x1 = (T)xi_of(g.kx0 + b, D.n1, D.kx1);
   if (axis == 2) {
     x2 = (T)xi_of(g.outer, D.n2, D.kx2);
@@ -341,131 +348,90 @@ __device__ __forceinline__ void col_xi(const Desc<T>& D, const ColGeo<T>& g, int
   }
 }
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(256) k_col(const Desc<T>* __restrict__ dd, int axis, int BX, int ncomp) {
+// Plain transform of one component (blockIdx.y) along `axis`.
+template <typename T, int OP, int BX>
+__global__ void __launch_bounds__(kColThreadsPlain) k_colplain(const Desc<T>* __restrict__ dd, int axis) {
+  const Desc<T>& D = *dd;
+  if (D.sc->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const ColGeo<T> g = col_geo<T>(D, axis, BX);
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* tl = tw + g.N;
+  load_twiddles<T>(tw, D.tw[axis], g.N);
+  const AxisPlan pl = D.ax[axis];
+  const int comp = blockIdx.y;
+  col_load<T, BX, BX>(D, g, comp, tl, 0);
+  __syncthreads();
+  fft_lines<T, BX>(tl, pl, BX, 1, tw, OP == OP_FWD ? -1 : +1);
+  col_store<T, BX, BX>(D, g, comp, tl, 0);
+}
+
+// Fused column pass along the axis hosting the spectral multiply; NS slots.
+//   OP_GRAD: c inputs u^ -> s engineering strains e^ = (i/V) B(xi) u^
+//   OP_DIV : s stresses sig^ -> c tractions t^ = (-theta/V) i B(xi)^T sig^
+//   OP_PREC: c residuals r^ -> z^ = (1/V) (theta K(xi) + rho_bar I)^-1 r^, with the
+//            Parseval partial sum of (r, z) over the half spectrum
+template <typename T, int OP, int BX, int NS>
+__global__ void __launch_bounds__(kColThreadsOp) k_colop(const Desc<T>* __restrict__ dd, int axis) {
+  constexpr int ES = NS * BX;
   const Desc<T>& D = *dd;
   Scalars* sc = D.sc;
   if (sc->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const ColGeo<T> g = col_geo<T>(D, axis, BX);
   const int N = g.N;
-  const int TS = N * BX;  // tile size
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* tl = tw + N;   // tiles
+  cplx<T>* tl = tw + N;
   load_twiddles<T>(tw, D.tw[axis], N);
   const AxisPlan pl = D.ax[axis];
-  if (OP == OP_FWD || OP == OP_INV) {
-    const int sgn = (OP == OP_FWD) ? -1 : +1;
-    for (int k = 0; k < ncomp; ++k) {
-      col_load<T>(D, g, BX, k, tl);
-      __syncthreads();
-      fft_lines<T>(tl, pl, BX, 1, BX, tw, sgn, true);
-      col_store<T>(D, g, BX, k, tl);
-      __syncthreads();
-    }
-    return;
-  }
   const int c = D.c;
-  if (OP == OP_GRAD) {
-    // inputs u^_k in tiles 0..c-1, work tile c
-    for (int k = 0; k < c; ++k) col_load<T>(D, g, BX, k, tl + k * TS);
-    __syncthreads();
-    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, -1, true);
-    cplx<T>* W = tl + c * TS;
-    const T iv = D.invV;
-    // engineering shear strains first (they need the unmodified inputs)
-    const int nsh = (c == 3) ? 3 : 1;
-    for (int m = 0; m < nsh; ++m) {
-      for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-        T x1, x2, x3;
-        col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
-        cplx<T> v;
-        if (c == 3) {
-          const cplx<T> u1 = tl[e], u2 = tl[TS + e], u3 = tl[2 * TS + e];
-          if (m == 0) v = cadd<T>(cscale<T>(u3, x2), cscale<T>(u2, x3));        // gamma_23
-          else if (m == 1) v = cadd<T>(cscale<T>(u3, x1), cscale<T>(u1, x3));   // gamma_13
-          else v = cadd<T>(cscale<T>(u2, x1), cscale<T>(u1, x2));               // gamma_12
-        } else {
-          const cplx<T> u1 = tl[e], u2 = tl[TS + e];
-          v = cadd<T>(cscale<T>(u2, x1), cscale<T>(u1, x2));                    // gamma_12
-        }
-        W[e] = cmuli<T>(cscale<T>(v, iv), +1);
+  const int nin = (OP == OP_DIV) ? D.s : c;
+  const int nout = (OP == OP_GRAD) ? D.s : c;
+  for (int k = 0; k < nin; ++k) col_load<T, BX, ES>(D, g, k, tl, k);
+  __syncthreads();
+  fft_lines<T, ES>(tl, pl, nin * BX, 1, tw, -1);
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < N * BX; e += blockDim.x) {
+    const int y = e / BX, b = e % BX;
+    cplx<T>* el = tl + y * ES + b;  // slot t at el[t * BX]
+    T x1, x2, x3;
+    col_xi<T>(D, g, axis, y, b, x1, x2, x3);
+    if (OP == OP_GRAD) {
+      const T iv = D.invV;
+      if (c == 3) {
+        const cplx<T> u1 = el[0], u2 = el[BX], u3 = el[2 * BX];
+        el[0] = cmuli<T>(cscale<T>(u1, x1 * iv), +1);
+        el[BX] = cmuli<T>(cscale<T>(u2, x2 * iv), +1);
+        el[2 * BX] = cmuli<T>(cscale<T>(u3, x3 * iv), +1);
+        el[3 * BX] = cmuli<T>(cscale<T>(cadd<T>(cscale<T>(u3, x2), cscale<T>(u2, x3)), iv), +1);  // gamma_23
+        el[4 * BX] = cmuli<T>(cscale<T>(cadd<T>(cscale<T>(u3, x1), cscale<T>(u1, x3)), iv), +1);  // gamma_13
+        el[5 * BX] = cmuli<T>(cscale<T>(cadd<T>(cscale<T>(u2, x1), cscale<T>(u1, x2)), iv), +1);  // gamma_12
+      } else {
+        const cplx<T> u1 = el[0], u2 = el[BX];
+        el[0] = cmuli<T>(cscale<T>(u1, x1 * iv), +1);
+        el[BX] = cmuli<T>(cscale<T>(u2, x2 * iv), +1);
+        el[2 * BX] = cmuli<T>(cscale<T>(cadd<T>(cscale<T>(u2, x1), cscale<T>(u1, x2)), iv), +1);  // gamma_12
       }
-      __syncthreads();
-      fft_lines<T>(W, pl, BX, 1, BX, tw, +1, true);
-      col_store<T>(D, g, BX, c + m, W);
-      __syncthreads();
-    }
-    // normal strains in place: e_kk = i xi_k u^_k
-    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-      T x1, x2, x3;
-      col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
-      tl[e] = cmuli<T>(cscale<T>(tl[e], x1 * iv), +1);
-      tl[TS + e] = cmuli<T>(cscale<T>(tl[TS + e], x2 * iv), +1);
-      if (c == 3) tl[2 * TS + e] = cmuli<T>(cscale<T>(tl[2 * TS + e], x3 * iv), +1);
-    }
-    __syncthreads();
-    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, +1, true);
-    for (int k = 0; k < c; ++k) col_store<T>(D, g, BX, k, tl + k * TS);
-    return;
-  }
-  if (OP == OP_DIV) {
-    // accumulators t^_k in tiles 0..c-1, work tile c; t^_i = -theta/V * i xi_j sigma^_ij
-    cplx<T>* W = tl + c * TS;
-    for (int e = threadIdx.x; e < c * TS; e += blockDim.x) tl[e] = cmake<T>(0, 0);
-    const T f = D.mthetaInvV;
-    const int ns = D.s;
-    for (int I = 0; I < ns; ++I) {
-      col_load<T>(D, g, BX, I, W);
-      __syncthreads();
-      fft_lines<T>(W, pl, BX, 1, BX, tw, -1, true);
-      for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-        T x1, x2, x3;
-        col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
-        const cplx<T> s = cmuli<T>(cscale<T>(W[e], f), +1);  // i f sigma^
-        if (c == 3) {
-          switch (I) {
-            case 0: tl[e] = cadd<T>(tl[e], cscale<T>(s, x1)); break;
-            case 1: tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x2)); break;
-            case 2: tl[2 * TS + e] = cadd<T>(tl[2 * TS + e], cscale<T>(s, x3)); break;
-            case 3:
-              tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x3));
-              tl[2 * TS + e] = cadd<T>(tl[2 * TS + e], cscale<T>(s, x2));
-              break;
-            case 4:
-              tl[e] = cadd<T>(tl[e], cscale<T>(s, x3));
-              tl[2 * TS + e] = cadd<T>(tl[2 * TS + e], cscale<T>(s, x1));
-              break;
-            default:
-              tl[e] = cadd<T>(tl[e], cscale<T>(s, x2));
-              tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x1));
-              break;
-          }
-        } else {
-          if (I == 0) tl[e] = cadd<T>(tl[e], cscale<T>(s, x1));
-          else if (I == 1) tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x2));
-          else {
-            tl[e] = cadd<T>(tl[e], cscale<T>(s, x2));
-            tl[TS + e] = cadd<T>(tl[TS + e], cscale<T>(s, x1));
-          }
-        }
+    } else if (OP == OP_DIV) {
+      const T f = D.mthetaInvV;
+      if (c == 3) {
+        const cplx<T> s11 = el[0], s22 = el[BX], s33 = el[2 * BX], s23 = el[3 * BX], s13 = el[4 * BX],
+                      s12 = el[5 * BX];
+        const cplx<T> t1 = cadd<T>(cadd<T>(cscale<T>(s11, x1), cscale<T>(s12, x2)), cscale<T>(s13, x3));
+        const cplx<T> t2 = cadd<T>(cadd<T>(cscale<T>(s12, x1), cscale<T>(s22, x2)), cscale<T>(s23, x3));
+        const cplx<T> t3 = cadd<T>(cadd<T>(cscale<T>(s13, x1), cscale<T>(s23, x2)), cscale<T>(s33, x3));
+        el[0] = cmuli<T>(cscale<T>(t1, f), +1);
+        el[BX] = cmuli<T>(cscale<T>(t2, f), +1);
+        el[2 * BX] = cmuli<T>(cscale<T>(t3, f), +1);
+      } else {
+        const cplx<T> s11 = el[0], s22 = el[BX], s12 = el[2 * BX];
+        const cplx<T> t1 = cadd<T>(cscale<T>(s11, x1), cscale<T>(s12, x2));
+        const cplx<T> t2 = cadd<T>(cscale<T>(s12, x1), cscale<T>(s22, x2));
+        el[0] = cmuli<T>(cscale<T>(t1, f), +1);
+        el[BX] = cmuli<T>(cscale<T>(t2, f), +1);
       }
-      __syncthreads();
-    }
-    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, +1, true);
-    for (int k = 0; k < c; ++k) col_store<T>(D, g, BX, k, tl + k * TS);
-    return;
-  }
-  if (OP == OP_PREC) {
-    for (int k = 0; k < c; ++k) col_load<T>(D, g, BX, k, tl + k * TS);
-    __syncthreads();
-    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, -1, true);
-    double acc = 0.0;
-    const T iv = D.invV;
-    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-      T x1, x2, x3;
-      col_xi<T>(D, g, axis, BX, e, x1, x2, x3);
-      const int kx = g.kx0 + (e % BX);
+    } else {  // OP_PREC
+      const int kx = g.kx0 + b;
       const double wgt = (kx >= D.nh) ? 0.0 : ((kx == 0 || 2 * kx == D.n1) ? 1.0 : 2.0);
       const T m0 = x1 * x1, m1 = x2 * x2, m2 = x3 * x3, m3 = x2 * x3, m4 = x1 * x3, m5 = x1 * x2;
       T Mv[6];
@@ -476,39 +442,41 @@ __global__ void __launch_bounds__(256) k_col(const Desc<T>* __restrict__ dd, int
       Mv[0] += D.rhobar;
       Mv[1] += D.rhobar;
       Mv[2] += D.rhobar;
+      const T iv = D.invV;
       if (c == 3) {
-        const T a = Mv[0], b = Mv[1], cc = Mv[2], f = Mv[3], ee = Mv[4], d = Mv[5];
-        const T A00 = b * cc - f * f, A11 = a * cc - ee * ee, A22 = a * b - d * d;
-        const T A01 = ee * f - d * cc, A02 = d * f - b * ee, A12 = d * ee - a * f;
+        const T a = Mv[0], bb = Mv[1], cc = Mv[2], f = Mv[3], ee = Mv[4], d = Mv[5];
+        const T A00 = bb * cc - f * f, A11 = a * cc - ee * ee, A22 = a * bb - d * d;
+        const T A01 = ee * f - d * cc, A02 = d * f - bb * ee, A12 = d * ee - a * f;
         const T det = a * A00 + d * A01 + ee * A02;
         const T id = iv / det;
-        const cplx<T> r1 = tl[e], r2 = tl[TS + e], r3 = tl[2 * TS + e];
+        const cplx<T> r1 = el[0], r2 = el[BX], r3 = el[2 * BX];
         const cplx<T> z1 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A00), cscale<T>(r2, A01)), cscale<T>(r3, A02)), id);
         const cplx<T> z2 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A01), cscale<T>(r2, A11)), cscale<T>(r3, A12)), id);
         const cplx<T> z3 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A02), cscale<T>(r2, A12)), cscale<T>(r3, A22)), id);
         acc += wgt * ((double)r1.x * z1.x + (double)r1.y * z1.y + (double)r2.x * z2.x + (double)r2.y * z2.y +
                       (double)r3.x * z3.x + (double)r3.y * z3.y);
-        tl[e] = z1;
-        tl[TS + e] = z2;
-        tl[2 * TS + e] = z3;
+        el[0] = z1;
+        el[BX] = z2;
+        el[2 * BX] = z3;
       } else {
-        const T a = Mv[0], b = Mv[1], d = Mv[5];
-        const T id = iv / (a * b - d * d);
-        const cplx<T> r1 = tl[e], r2 = tl[TS + e];
-        const cplx<T> z1 = cscale<T>(csub<T>(cscale<T>(r1, b), cscale<T>(r2, d)), id);
+        const T a = Mv[0], bb = Mv[1], d = Mv[5];
+        const T id = iv / (a * bb - d * d);
+        const cplx<T> r1 = el[0], r2 = el[BX];
+        const cplx<T> z1 = cscale<T>(csub<T>(cscale<T>(r1, bb), cscale<T>(r2, d)), id);
         const cplx<T> z2 = cscale<T>(csub<T>(cscale<T>(r2, a), cscale<T>(r1, d)), id);
         acc += wgt * ((double)r1.x * z1.x + (double)r1.y * z1.y + (double)r2.x * z2.x + (double)r2.y * z2.y);
-        tl[e] = z1;
-        tl[TS + e] = z2;
+        el[0] = z1;
+        el[BX] = z2;
       }
     }
+  }
+  if (OP == OP_PREC) {
     const double s = block_sum(acc);  // contains barriers
     if (threadIdx.x == 0) D.part[PT_B][blockIdx.x] = s;
-    __syncthreads();
-    for (int k = 0; k < c; ++k) fft_lines<T>(tl + k * TS, pl, BX, 1, BX, tw, +1, true);
-    for (int k = 0; k < c; ++k) col_store<T>(D, g, BX, k, tl + k * TS);
-    return;
   }
+  __syncthreads();
+  fft_lines<T, ES>(tl, pl, nout * BX, 1, tw, +1);
+  for (int k = 0; k < nout; ++k) col_store<T, BX, ES>(D, g, k, tl, k);
 }
 
 }  // namespace wfft

@@ -46,27 +46,32 @@ void plan_geometry(Plan<T>& P) {
   const size_t cs = sizeof(cplx<T>);
   g.sm_x = (size_t)(D.n1 + (g.LX * D.c / 2) * D.n1) * cs;
   g.sm_xm = (size_t)(D.n1 + (g.LXm * D.s / 2) * D.n1) * cs;
-  // column passes: BX consecutive kx columns (64-byte rows) within the budget
-  int bx = sizeof(T) == 4 ? 8 : 4;
-  int ecol = budget;
-  for (int ax = 1; ax <= 2; ++ax) ecol = std::min(ecol, max_tile_elems<T>(D.ax[ax], g.thr));
-  const int nmax = std::max(D.n2, D.n3);
-  while (bx > 1 && bx * nmax > ecol) bx >>= 1;
-  g.BX = bx;
-  const int ntx = (D.nh + bx - 1) / bx;
-  g.blk_col[0] = 0;
-  g.blk_col[1] = ntx * D.n3;
-  g.blk_col[2] = ntx * D.n2;
+  // column passes: per axis and op, the widest tile (kx columns) whose every
+  // radix stage fits the register batch and whose slots fit 64 KB of shared memory
+  const int maxbx = sizeof(T) == 4 ? 8 : 4;
+  g.max_blocks = std::max(std::max(g.blk_x, g.blk_xm), 1);
+  for (int ax = 0; ax < 3; ++ax)
+    for (int op = 0; op < 5; ++op) {
+      g.bx[ax][op] = 0;
+      g.blk_col[ax][op] = 0;
+      g.sm_col[ax][op] = 0;
+    }
   for (int ax = 1; ax <= 2; ++ax) {
     const int N = ax == 1 ? D.n2 : D.n3;
-    const size_t tile = (size_t)bx * N * cs;
-    g.sm_col[ax][OP_FWD] = N * cs + tile;
-    g.sm_col[ax][OP_INV] = N * cs + tile;
-    g.sm_col[ax][OP_GRAD] = N * cs + (D.c + 1) * tile;
-    g.sm_col[ax][OP_DIV] = N * cs + (D.c + 1) * tile;
-    g.sm_col[ax][OP_PREC] = N * cs + D.c * tile;
+    const int nouter = ax == 1 ? D.n3 : D.n2;
+    for (int op = 0; op < 5; ++op) {
+      const bool plain = op == OP_FWD || op == OP_INV;
+      const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
+      const int thr = plain ? kColThreadsPlain : kColThreadsOp;
+      const int maxe = max_tile_elems<T>(D.ax[ax], thr);
+      int bx = plain ? maxbx : std::min(maxbx, 4);
+      while (bx > 1 && ((long long)ns * bx * N > maxe || (size_t)ns * bx * N * cs > 64 * 1024)) bx >>= 1;
+      g.bx[ax][op] = bx;
+      g.blk_col[ax][op] = ((D.nh + bx - 1) / bx) * nouter;
+      g.sm_col[ax][op] = (size_t)(N + ns * bx * N) * cs;
+      g.max_blocks = std::max(g.max_blocks, g.blk_col[ax][op]);
+    }
   }
-  g.max_blocks = std::max(std::max(g.blk_x, g.blk_xm), std::max(std::max(g.blk_col[1], g.blk_col[2]), 1));
 }
 
 template <typename T>
@@ -80,18 +85,54 @@ static void launch_xfwd(const Plan<T>& P, int pre, int in_slot, cudaStream_t st)
   }
 }
 
+template <typename T, int BX>
+static void launch_colplain_bx(const Plan<T>& P, int op, int axis, int ncomp, cudaStream_t st) {
+  const PassGeo& g = P.g;
+  const dim3 grid(g.blk_col[axis][op], ncomp);
+  const size_t sm = g.sm_col[axis][op];
+  if (op == OP_FWD)
+    k_colplain<T, OP_FWD, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis);
+  else
+    k_colplain<T, OP_INV, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis);
+}
+
+template <typename T, int OP, int BX>
+static void launch_colop_bx(const Plan<T>& P, int axis, cudaStream_t st) {
+  const PassGeo& g = P.g;
+  const int nb = g.blk_col[axis][OP];
+  const size_t sm = g.sm_col[axis][OP];
+  // slots: c (2 or 3) for the preconditioner, s (3 or 6) for gradient / divergence
+  constexpr int kSmall = OP == OP_PREC ? 2 : 3;
+  constexpr int kLarge = OP == OP_PREC ? 3 : 6;
+  if (P.h.ndim == 2)
+    k_colop<T, OP, BX, kSmall><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
+  else
+    k_colop<T, OP, BX, kLarge><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
+}
+
+template <typename T, int OP>
+static void launch_colop(const Plan<T>& P, int axis, cudaStream_t st) {
+  switch (P.g.bx[axis][OP]) {
+    case 4: launch_colop_bx<T, OP, 4>(P, axis, st); break;
+    case 2: launch_colop_bx<T, OP, 2>(P, axis, st); break;
+    default: launch_colop_bx<T, OP, 1>(P, axis, st); break;
+  }
+}
+
 template <typename T>
 static void launch_col(const Plan<T>& P, int op, int axis, int ncomp, cudaStream_t st) {
-  const PassGeo& g = P.g;
-  const int nb = g.blk_col[axis];
-  const size_t sm = g.sm_col[axis][op];
-  switch (op) {
-    case OP_FWD: k_col<T, OP_FWD><<<nb, g.thr, sm, st>>>(P.d, axis, g.BX, ncomp); break;
-    case OP_INV: k_col<T, OP_INV><<<nb, g.thr, sm, st>>>(P.d, axis, g.BX, ncomp); break;
-    case OP_GRAD: k_col<T, OP_GRAD><<<nb, g.thr, sm, st>>>(P.d, axis, g.BX, ncomp); break;
-    case OP_DIV: k_col<T, OP_DIV><<<nb, g.thr, sm, st>>>(P.d, axis, g.BX, ncomp); break;
-    default: k_col<T, OP_PREC><<<nb, g.thr, sm, st>>>(P.d, axis, g.BX, ncomp); break;
+  if (op == OP_FWD || op == OP_INV) {
+    switch (P.g.bx[axis][op]) {
+      case 8: launch_colplain_bx<T, 8>(P, op, axis, ncomp, st); break;
+      case 4: launch_colplain_bx<T, 4>(P, op, axis, ncomp, st); break;
+      case 2: launch_colplain_bx<T, 2>(P, op, axis, ncomp, st); break;
+      default: launch_colplain_bx<T, 1>(P, op, axis, ncomp, st); break;
+    }
+    return;
   }
+  if (op == OP_GRAD) launch_colop<T, OP_GRAD>(P, axis, st);
+  else if (op == OP_DIV) launch_colop<T, OP_DIV>(P, axis, st);
+  else launch_colop<T, OP_PREC>(P, axis, st);
 }
 
 template <typename T>
@@ -156,12 +197,12 @@ __global__ void __launch_bounds__(256) k_xplain(const Desc<T>* __restrict__ dd, 
       packed<T>(buf, N, q, x) = line < nsp ? f[(long long)k * D.V + line * N + x] : (T)0;
     }
     __syncthreads();
-    fft_lines<T>(buf, D.ax[0], LX * nc / 2, N, 1, tw, -1, false);
+    fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, N, tw, -1);
     store_unpacked<T>(D, buf, N, LX * nc, l0, nc, nsp);
   } else {
     load_packed<T>(D, buf, N, LX * nc, l0, nc, nsp);
     __syncthreads();
-    fft_lines<T>(buf, D.ax[0], LX * nc / 2, N, 1, tw, +1, false);
+    fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, N, tw, +1);
     for (int e = threadIdx.x; e < LX * nc * N; e += blockDim.x) {
       const int x = e % N, q = e / N, k = q % nc, l = q / nc;
       const long long line = l0 + l;
@@ -212,11 +253,25 @@ cudaError_t init_kernel_attributes() {
   WFFT_SETATTR((k_xinv<T, POST_PREC>));
   WFFT_SETATTR((k_xmid<T>));
   WFFT_SETATTR((k_xplain<T>));
-  WFFT_SETATTR((k_col<T, OP_FWD>));
-  WFFT_SETATTR((k_col<T, OP_INV>));
-  WFFT_SETATTR((k_col<T, OP_GRAD>));
-  WFFT_SETATTR((k_col<T, OP_DIV>));
-  WFFT_SETATTR((k_col<T, OP_PREC>));
+#define WFFT_SETATTR_BX(BXV)                  \
+  WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 3>));  \
+  WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 6>));  \
+  WFFT_SETATTR((k_colop<T, OP_DIV, BXV, 3>));   \
+  WFFT_SETATTR((k_colop<T, OP_DIV, BXV, 6>));   \
+  WFFT_SETATTR((k_colop<T, OP_PREC, BXV, 2>));  \
+  WFFT_SETATTR((k_colop<T, OP_PREC, BXV, 3>));
+  WFFT_SETATTR_BX(1)
+  WFFT_SETATTR_BX(2)
+  WFFT_SETATTR_BX(4)
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 1>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 1>));
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 2>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 2>));
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 4>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 4>));
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 8>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 8>));
+#undef WFFT_SETATTR_BX
 #undef WFFT_SETATTR
   return e;
 }
