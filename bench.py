@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit FFT beta-Newmark solver on the 256^3 nickel
+polycrystal (500 seeded Voronoi grains, rotated cubic C11/C12/C44 =
+168.4/121.4/75.4 GPa, rho = 8960, Gaussian pulse of width 50 dt on the 4-voxel
+x-face slab), one GB300.
+
+A step is one Newmark step of the whole hot path: predictor, the masked
+preconditioned Krylov solve to 1e-10 (FFT operator + reference-medium
+preconditioner) and the corrector.  The headline `value` is voxel *
+Krylov-iterations / s of the mixed solve (FP32 inner PCG, FP64 dots, FP64
+true-residual refinement, FP64 state); the plain FP64 solve is measured beside
+it.  Timed with CUDA events on the solver's stream after `--warmup` untimed
+steps; every field is >= 64 MB, so the working set of each pass exceeds L2.
+
+`--impl reference` times the FP64 CPU oracle (the reference implementation
+of this build) on the host cores: one oracle PCG iteration of the same
+256^3 workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "s per Newmark step, voxel·Krylov-iters/s at 256³; plain FP64 vs mixed+learned"
+UNIT = "voxel·Krylov-iters/s"
+WORKLOAD = ("256^3 nickel polycrystal: 500 periodic Voronoi grains (seed 3), uniformly random orientations of "
+            "cubic C11/C12/C44 = 168.4/121.4/75.4 GPa, rho 8960; Gaussian pulse (sigma 50 dt, centre 200 dt) on "
+            "u_x of the 4-voxel x-face slab; dt 2e-7 s, h 1 mm, beta 1/4, gamma 1/2; PCG to 1e-10 relative "
+            "residual")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid edge (the workload is 256)")
+    ap.add_argument("--modes", default="mixed,fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        pw = [num(r[3]) for r in rows if num(r[3])]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2211_08263_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA throughput of a GB300, measured with an FMA-chain microbenchmark
+# (152 SMs x 2 FP64 FMA/clk/SM x 2 flop x ~1.97 GHz); the FP64 kernels are
+# bound by it rather than by HBM.
+FP64_PEAK_GFLOPS = 1195.2
+
+
+def run_mode(wfft, torch, prob, precision, W, K, world, e2e: bool):
+    stream = torch.cuda.current_stream()
+    opt = wfft.default_options(precision=precision, tol=1e-10, maxit=500, check_every=4)
+    s = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
+    for n in range(W):
+        s.step(prob.U[n])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = s.launch_count()
+    s.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for n in range(W, W + K):
+        infos.append(s.step(prob.U[n]))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - l0
+    prof = s.profile_read()
+    s.profile(False)
+    res = {"ms_total": ms, "iters": sum(i["iters"] for i in infos),
+           "outer_applies": sum(i["outer_applies"] for i in infos),
+           "sweeps": sum(i["sweeps"] for i in infos), "rel_res_max": max(i["rel_res"] for i in infos),
+           "launches": launches, "profile": prof, "iters_per_step": [i["iters"] for i in infos]}
+    if e2e:
+        # end to end through the C ABI: U(t_n) from host memory in, the displacement
+        # field u_n copied back to pinned host memory after every step
+        host_u = torch.empty(s.shape, dtype=torch.float64, pin_memory=True).numpy()
+        s2 = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
+        for n in range(W):
+            s2.step(prob.U[n])
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        it2 = 0
+        for n in range(W, W + K):
+            it2 += s2.step(prob.U[n])["iters"]
+            s2.download_u(host_u)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        res["e2e_s"] = t1 - t0
+        res["e2e_iters"] = it2
+        res["d2h_bytes"] = int(host_u.nbytes)
+        s2.close()
+    s.close()
+    return res
+
+
+def roofline(prof, V, hbm_peak, peak_kind):
+    """Dominant kernel (largest device time in the timed region) against its roofline."""
+    best = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    (prec, kind), d = best
+    per = d["ms"] / max(1, d["timed"])
+    if prec == "fp32":
+        achieved = d["bytes"] / max(1, d["timed"]) / (per * 1e-3) / 1e9
+        return {"kernel": f"{kind} ({prec})", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_kind,
+                "alg_bytes_per_launch": d["bytes"] / max(1, d["timed"]), "ms_per_launch": per,
+                "launches": d["timed"], "traffic": None}
+    achieved = d["flops"] / max(1, d["timed"]) / (per * 1e-3) / 1e9
+    return {"kernel": f"{kind} ({prec})", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS, "peak_source": "measured FP64 FMA",
+            "alg_flops_per_launch": d["flops"] / max(1, d["timed"]), "ms_per_launch": per,
+            "launches": d["timed"], "traffic": None}
+
+
+def kernel_table(prof, hbm_peak, total_ms):
+    out = {}
+    for (prec, kind), d in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        if not d["timed"]:
+            continue
+        per = d["ms"] / d["timed"]
+        gbs = d["bytes"] / d["timed"] / (per * 1e-3) / 1e9 if per > 0 else 0.0
+        gfl = d["flops"] / d["timed"] / (per * 1e-3) / 1e9 if per > 0 else 0.0
+        out[f"{prec}:{kind}"] = {"launches": d["timed"], "ms": round(d["ms"], 3),
+                                 "share": round(d["ms"] / total_ms, 4) if total_ms else None,
+                                 "alg_GBps": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 3),
+                                 "alg_GFLOPs": round(gfl, 1)}
+    return out
+
+
+def cpu_oracle_iteration(prob, reps=1):
+    """One FP64 oracle PCG iteration (operator + preconditioner + updates) on the workload."""
+    import numpy as np
+    from oracle import newmark, pcg
+    nm = newmark.oracle_from_problem(prob, tol=1e-10)
+    rng = np.random.default_rng(0)
+    shape = (3,) + tuple(nm.med.shape)
+    p = rng.standard_normal(shape)
+    r = rng.standard_normal(shape)
+    x = np.zeros(shape)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        q = np.where(nm.mask, 0.0, nm.A(p))
+        alpha = pcg.dot(r, r) / pcg.dot(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        z = np.where(nm.mask, 0.0, nm.M(r))
+        beta = pcg.dot(r, z)
+        p = z + 1e-3 * beta * p
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args, prob, rank, world):
+    if rank != 0:
+        return 0
+    V = prob.nvox
+    W, K = args.warmup, args.steps
+    t = cpu_oracle_iteration(prob, reps=W + K)[W:]
+    total = sum(t)
+    value = V * K / total
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * total / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [prob.n[0], prob.n[1], prob.n[2]],
+                       "step": "one FP64 oracle PCG iteration (operator + preconditioner + updates)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{K} PCG iterations of the FP64 NumPy/SciPy oracle at "
+                                       f"{prob.n[0]}^3, scipy.fft workers={cores}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_2211_08263_gb300 import inputs
+    W, K = args.warmup, args.steps
+    prob = inputs.config_c3(nsteps=W + K, n=args.n)
+    if args.impl == "reference":
+        return run_reference(args, prob, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    from paper_2211_08263_gb300 import build, wfft
+    if not os.path.exists(build.LIB):
+        build.build()
+    wfft.load()
+    hbm_peak, peak_kind = load_peaks()
+    V = prob.nvox
+    modes = [m.strip() for m in args.modes.split(",") if m.strip()]
+    clocks = ClockSampler(local)
+    results = {}
+    for m in modes:
+        prec = wfft.MIXED if m == "mixed" else wfft.FP64
+        if m == modes[0]:
+            clocks.start()
+        results[m] = run_mode(wfft, torch, prob, prec, W, K, world, e2e=(m == modes[0] and not args.no_e2e))
+        if m == modes[0]:
+            clk = clocks.stop()
+    head = results[modes[0]]
+    # max over ranks
+    ms = head["ms_total"]
+    iters = head["iters"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        it = torch.tensor([float(iters)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(it, op=torch.distributed.ReduceOp.SUM)
+        iters = float(it.item())
+    value = V * iters / (ms * 1e-3)
+    modes_out = {}
+    for m, r in results.items():
+        modes_out[m] = {"ms_per_step": r["ms_total"] / K, "s_per_step": r["ms_total"] / K / 1e3,
+                        "voxel_iters_per_s": V * r["iters"] / (r["ms_total"] * 1e-3),
+                        "krylov_iters_per_step": r["iters"] / K, "fp64_applies_per_step": r["outer_applies"] / K,
+                        "sweeps_per_step": r["sweeps"] / K, "max_rel_res": r["rel_res_max"],
+                        "iters_per_step": r["iters_per_step"]}
+    rl = roofline(head["profile"], V, hbm_peak, peak_kind)
+    traffic_file = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(traffic_file):
+        tf = json.load(open(traffic_file))
+        if tf.get("csrc_sha") == csrc_hash() and rl["kernel"] in tf.get("kernels", {}):
+            rl["traffic"] = tf["kernels"][rl["kernel"]]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (inner PCG) + f64 (dots, residual refinement, state)" if modes[0] == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [prob.n[0], prob.n[1], prob.n[2]], "mode": modes[0],
+                       "timed_steps": [W + 1, W + K], "tol": 1e-10,
+                       "l2": "inputs larger than L2 (every field >= 64 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "modes": modes_out, "roofline": rl,
+            "kernels": kernel_table(head["profile"], hbm_peak, head["ms_total"]),
+            "gpu_launches": head["launches"], "clocks": clk}
+    if "e2e_s" in head:
+        line["e2e"] = {"value": V * head["e2e_iters"] * world / head["e2e_s"], "unit": UNIT,
+                       "h2d_bytes_per_step": 24, "d2h_bytes_per_step": head["d2h_bytes"],
+                       "note": "wfft_step with host U(t_n) + u_n copied to pinned host memory every step"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = cpu_oracle_iteration(prob, reps=1)
+        line["cpu_baseline"] = {"value": V / t[0], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"1 PCG iteration of the FP64 oracle at {prob.n[0]}^3 "
+                                          f"({t[0]:.1f} s, scipy.fft workers={os.cpu_count()})"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

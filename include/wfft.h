@@ -198,6 +198,39 @@ WFFT_API int wfft_spectral_pitch(const wfft_handle* h, int* pitch);
  */
 WFFT_API int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step_info* infos);
 
+/* Kernel kinds of the launch accounting (wfft_profile_read). */
+#define WFFT_K_XFWD_PLAIN 0   /* x-axis real->half-spectrum pass */
+#define WFFT_K_XFWD_PUPD 1    /* ... fused with p = z + beta p */
+#define WFFT_K_XFWD_RUPD 2    /* ... fused with x += alpha p, r -= alpha q, ||r||^2 */
+#define WFFT_K_XFWD_CONV 3    /* ... fused with the FP64 -> FP32 residual conversion */
+#define WFFT_K_XINV_APPLY 4   /* half-spectrum->real x pass fused with q = -theta t + rho p, mask, (p,q) */
+#define WFFT_K_XINV_RESID 5   /* ... fused with r = P(b - A x), ||r||^2 (FP64) */
+#define WFFT_K_XINV_PREC 6    /* ... fused with z = P(...) */
+#define WFFT_K_XMID 7         /* x inverse + sigma = C(x):eps + x forward */
+#define WFFT_K_COL_FWD 8      /* plain forward column (y / z) pass */
+#define WFFT_K_COL_INV 9      /* plain inverse column pass */
+#define WFFT_K_COL_GRAD 10    /* column pass fused with eps^ = sym(i xi (x) u^) */
+#define WFFT_K_COL_DIV 11     /* column pass fused with t^ = i xi . sigma^ */
+#define WFFT_K_COL_PREC 12    /* column pass fused with (theta K(xi) + rho_bar I)^-1 and Parseval (r,z) */
+#define WFFT_K_NEWMARK 13     /* predictor / corrector */
+#define WFFT_K_SCALAR 14      /* single-block finalize and bookkeeping kernels */
+#define WFFT_K_COUNT 15
+
+/*
+ * Launch accounting.  Every kernel launch of a handle is counted per kind and
+ * precision.  wfft_profile(h, 1) resets the totals and brackets each
+ * following launch with CUDA events on the handle's stream; wfft_profile(h, 0)
+ * stops.  wfft_profile_read returns, for one (precision, kind): launches
+ * counted, launches timed, their summed device time (ms), and their summed
+ * algorithmic DRAM bytes and flops (the compulsory traffic / arithmetic of the
+ * method, a model, not hardware counters).  Both synchronise the stream.
+ */
+WFFT_API int wfft_profile(wfft_handle* h, int enable);
+WFFT_API int wfft_profile_read(wfft_handle* h, int precision, int kind, long long* launches, long long* timed,
+                               double* ms, double* alg_bytes, double* alg_flops);
+/* Total kernel launches issued by the handle since creation. */
+WFFT_API int wfft_launch_count(const wfft_handle* h, long long* launches);
+
 /* Query helpers. */
 WFFT_API int wfft_get_sizes(const wfft_handle* h, int* ndim, int n[3], long long* nvox);
 WFFT_API int wfft_device_bytes(const wfft_handle* h, size_t* bytes);

@@ -14,8 +14,13 @@
 #include "finalize.cuh"
 #include "launch.cuh"
 #include "passes.cuh"
+#include "profiler.cuh"
 
 using namespace wfft;
+
+namespace wfft {
+thread_local Profiler* g_prof = nullptr;
+}
 
 struct wfft_handle {
   int ndim = 0, c = 0, s = 0;
@@ -35,7 +40,15 @@ struct wfft_handle {
   long long nstep = 0;
   bool has_mask = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  Profiler prof;
   std::string err;
+};
+
+// Makes the handle's profiler the current one for the launches of an API call.
+struct ProfScope {
+  Profiler* prev;
+  explicit ProfScope(wfft_handle* h) : prev(g_prof) { g_prof = h ? &h->prof : nullptr; }
+  ~ProfScope() { g_prof = prev; }
 };
 
 static std::string g_err;
@@ -465,6 +478,7 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   CKC(cudaEventCreate(&h->ev0));
   CKC(cudaEventCreate(&h->ev1));
   // lifting fields w_j = P A(E e_j) for the stopping-test reference norm
+  ProfScope ps_(h);
   if (h->has_mask) {
     double* tmp = reinterpret_cast<double*>(D.slot[SL_Z]);
     for (int j = 0; j < h->ndim; ++j) {
@@ -670,6 +684,7 @@ static void fill_info_base(wfft_step_info* info) {
 }
 
 extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info) {
+  ProfScope ps_(h);
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
   if (!U) return fail(h, WFFT_EINVAL, "U is NULL");
   fill_info_base(info);
@@ -719,6 +734,7 @@ __global__ static void k_keep_gamma(const Desc<double>* dd, double* x) {
 }
 
 extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol, int maxit, wfft_step_info* info) {
+  ProfScope ps_(h);
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
   if (!b || !x) return fail(h, WFFT_EINVAL, "b and x are required");
   fill_info_base(info);
@@ -735,13 +751,16 @@ extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol
   CKH(h, cudaMemcpyAsync(P.h.slot[SL_B], b, bytes, cudaMemcpyHostToDevice, h->st));
   // ref^2 = ||P(b - A x_Gamma)||^2: residual of x with its free DOFs zeroed
   CKH(h, cudaMemcpyAsync(P.h.slot[SL_X], x, bytes, cudaMemcpyHostToDevice, h->st));
-  k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]);
+  prof_launch(0, KK_NEWMARK, 16.0 * h->c * h->V, 0.0, h->st,
+              [&] { k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]); });
   launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
   launch_fin(h->sc64, P.h.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
   CKH(h, cudaMemcpyAsync(P.h.slot[SL_X], x, bytes, cudaMemcpyHostToDevice, h->st));
   int status = solve_core(h, info);
   h->opt.maxit = saved;
-  if (h->host_sc[0].zero_free) k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]);
+  if (h->host_sc[0].zero_free)
+    prof_launch(0, KK_NEWMARK, 16.0 * h->c * h->V, 0.0, h->st,
+                [&] { k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]); });
   CKH(h, cudaEventRecord(h->ev1, h->st));
   CKH(h, cudaMemcpyAsync(x, P.h.slot[SL_X], bytes, cudaMemcpyDeviceToHost, h->st));
   CKH(h, cudaStreamSynchronize(h->st));
@@ -757,6 +776,7 @@ extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol
 }
 
 extern "C" int wfft_apply(wfft_handle* h, int precision, const void* p_dev, void* q_dev, int masked) {
+  ProfScope ps_(h);
   if (!h || !p_dev || !q_dev) return fail(h, WFFT_EINVAL, "null argument");
   if (precision == WFFT_FP64) {
     launch_set_done(h->sc64, 0, h->st);
@@ -774,6 +794,7 @@ extern "C" int wfft_apply(wfft_handle* h, int precision, const void* p_dev, void
 }
 
 extern "C" int wfft_precond(wfft_handle* h, int precision, const void* r_dev, void* z_dev, int masked) {
+  ProfScope ps_(h);
   if (!h || !r_dev || !z_dev) return fail(h, WFFT_EINVAL, "null argument");
   if (precision == WFFT_FP64) {
     launch_set_done(h->sc64, 0, h->st);
@@ -808,6 +829,7 @@ static int rfft3_impl(wfft_handle* h, Plan<T>& P, Scalars* sc, int dir, int ncom
 }
 
 extern "C" int wfft_rfft3(wfft_handle* h, int precision, int dir, int ncomp, const void* in_dev, void* out_dev) {
+  ProfScope ps_(h);
   if (!h || !in_dev || !out_dev) return fail(h, WFFT_EINVAL, "null argument");
   if (ncomp < 1 || ncomp > h->s || (dir != -1 && dir != 1)) return fail(h, WFFT_EINVAL, "bad ncomp or dir");
   if (precision == WFFT_FP64) return rfft3_impl<double>(h, h->P64, h->sc64, dir, ncomp, in_dev, out_dev);
@@ -823,4 +845,41 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
     if (rc && !first) first = rc;
   }
   return first;
+}
+
+extern "C" int wfft_profile(wfft_handle* h, int enable) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  CKH(h, cudaStreamSynchronize(h->st));
+  h->prof.collect();
+  if (enable) {
+    h->prof.reset();
+    h->prof.on = true;
+  } else {
+    h->prof.on = false;
+  }
+  return WFFT_OK;
+}
+
+extern "C" int wfft_profile_read(wfft_handle* h, int precision, int kind, long long* launches, long long* timed,
+                                 double* ms, double* alg_bytes, double* alg_flops) {
+  if (!h || (precision != WFFT_FP64 && precision != WFFT_MIXED) || kind < 0 || kind >= KK_NKIND)
+    return fail(h, WFFT_EINVAL, "bad profile query");
+  CKH(h, cudaStreamSynchronize(h->st));
+  h->prof.collect();
+  const int p = precision == WFFT_FP64 ? 0 : 1;
+  if (launches) *launches = h->prof.launches[p][kind];
+  if (timed) *timed = h->prof.timed[p][kind];
+  if (ms) *ms = h->prof.ms[p][kind];
+  if (alg_bytes) *alg_bytes = h->prof.bytes[p][kind];
+  if (alg_flops) *alg_flops = h->prof.flops[p][kind];
+  return WFFT_OK;
+}
+
+extern "C" int wfft_launch_count(const wfft_handle* h, long long* launches) {
+  if (!h || !launches) return fail(nullptr, WFFT_EINVAL, "null argument");
+  long long n = 0;
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < KK_NKIND; ++k) n += h->prof.launches[p][k];
+  *launches = n;
+  return WFFT_OK;
 }

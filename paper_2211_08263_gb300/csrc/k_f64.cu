@@ -5,6 +5,7 @@
 
 #include "finalize.cuh"
 #include "passes_impl.cuh"
+#include "profiler.cuh"
 
 namespace wfft {
 
@@ -121,10 +122,17 @@ static int ew_blocks(const Plan<double>& P) {
   return (int)(nb < 1 ? 1 : nb);
 }
 
-void launch_predict(const Plan<double>& P, cudaStream_t st) { k_predict<<<ew_blocks(P), 256, 0, st>>>(P.d); }
-void launch_correct(const Plan<double>& P, cudaStream_t st) { k_correct<<<ew_blocks(P), 256, 0, st>>>(P.d); }
+void launch_predict(const Plan<double>& P, cudaStream_t st) {
+  const double cv = (double)P.h.c * P.h.V, mat = (P.h.phase ? 3.0 : 1.0) * P.h.V;
+  prof_launch(0, KK_NEWMARK, 8 * cv * (3 + P.h.ndim + 2) + mat, cv * (8 + 2 * P.h.ndim), st,
+              [&] { k_predict<<<ew_blocks(P), 256, 0, st>>>(P.d); });
+}
+void launch_correct(const Plan<double>& P, cudaStream_t st) {
+  const double cv = (double)P.h.c * P.h.V, mat = (P.h.phase ? 3.0 : 1.0) * P.h.V;
+  prof_launch(0, KK_NEWMARK, 8 * cv * 7 + mat, cv * 14, st, [&] { k_correct<<<ew_blocks(P), 256, 0, st>>>(P.d); });
+}
 void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st) {
-  k_fill_unit<<<ew_blocks(P), 256, 0, st>>>(P.d, j, dst);
+  prof_launch(0, KK_SCALAR, 8.0 * P.h.c * P.h.V, 0.0, st, [&] { k_fill_unit<<<ew_blocks(P), 256, 0, st>>>(P.d, j, dst); });
 }
 int ew_block_count(const Plan<double>& P) { return ew_blocks(P); }
 
@@ -267,11 +275,14 @@ __global__ void k_set_done(Scalars* sc, int done) {
 
 void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc, int mode,
                 Scalars* sc2, cudaStream_t st) {
-  k_fin<<<1, 256, 0, st>>>(sc, pa, na, pb, nb, pc, nc, mode, sc2);
+  prof_launch(0, KK_SCALAR, 8.0 * (na + nb + nc), (double)(na + nb + nc), st,
+              [&] { k_fin<<<1, 256, 0, st>>>(sc, pa, na, pb, nb, pc, nc, mode, sc2); });
 }
 void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st) {
-  k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit);
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit); });
 }
-void launch_set_done(Scalars* sc, int done, cudaStream_t st) { k_set_done<<<1, 32, 0, st>>>(sc, done); }
+void launch_set_done(Scalars* sc, int done, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_set_done<<<1, 32, 0, st>>>(sc, done); });
+}
 
 }  // namespace wfft

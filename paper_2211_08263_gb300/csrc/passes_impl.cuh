@@ -1,9 +1,11 @@
 // Launch sequences of the fused passes, instantiated per arithmetic type.
 #pragma once
 #include <algorithm>
+#include <cmath>
 
 #include "launch.cuh"
 #include "passes.cuh"
+#include "profiler.cuh"
 
 namespace wfft {
 
@@ -74,14 +76,54 @@ void plan_geometry(Plan<T>& P) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// algorithmic cost model of one launch (compulsory DRAM bytes: every input read
+// once and every output written once, spectra at their unpadded size; flops:
+// 5 N log2 N per complex FFT line, half that per real line, plus the pointwise work)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cost {
+  double V, Vh, st, lg1, lg2, lg3, c, s;
+  explicit Cost(const Desc<T>& D) {
+    V = (double)D.V;
+    Vh = (double)D.n3 * D.n2 * D.nh;
+    st = sizeof(T);
+    lg1 = std::log2((double)D.n1);
+    lg2 = std::log2((double)D.n2);
+    lg3 = std::log2((double)D.n3);
+    c = D.c;
+    s = D.s;
+  }
+  double spec(double ncomp) const { return ncomp * Vh * 2 * st; }
+  double real(double ncomp) const { return ncomp * V * st; }
+  double xfft(double ncomp) const { return 2.5 * V * lg1 * ncomp; }
+  double colfft(int axis, double ncomp) const { return 5.0 * Vh * (axis == 1 ? lg2 : lg3) * ncomp; }
+};
+static inline int prec_index(size_t st) { return st == 8 ? 0 : 1; }
+
 template <typename T>
 static void launch_xfwd(const Plan<T>& P, int pre, int in_slot, cudaStream_t st) {
   const PassGeo& g = P.g;
+  const Cost<T> k(P.h);
+  const int pi = prec_index(sizeof(T));
+  const double out = k.spec(k.c), fl = k.xfft(k.c);
   switch (pre) {
-    case PRE_PLAIN: k_xfwd<T, PRE_PLAIN><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); break;
-    case PRE_PUPD: k_xfwd<T, PRE_PUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); break;
-    case PRE_RUPD: k_xfwd<T, PRE_RUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); break;
-    default: k_xfwd<T, PRE_CONV><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); break;
+    case PRE_PLAIN:
+      prof_launch(pi, KK_XFWD_PLAIN, k.real(k.c) + out, fl, st,
+                  [&] { k_xfwd<T, PRE_PLAIN><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      break;
+    case PRE_PUPD:
+      prof_launch(pi, KK_XFWD_PUPD, 3 * k.real(k.c) + out, fl + 2 * k.c * k.V, st,
+                  [&] { k_xfwd<T, PRE_PUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      break;
+    case PRE_RUPD:
+      prof_launch(pi, KK_XFWD_RUPD, 16 * k.c * k.V + 4 * k.real(k.c) + out, fl + 6 * k.c * k.V, st,
+                  [&] { k_xfwd<T, PRE_RUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      break;
+    default:
+      prof_launch(pi, KK_XFWD_CONV, 8 * k.c * k.V + k.real(k.c) + out, fl + k.c * k.V, st,
+                  [&] { k_xfwd<T, PRE_CONV><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      break;
   }
 }
 
@@ -90,10 +132,15 @@ static void launch_colplain_bx(const Plan<T>& P, int op, int axis, int ncomp, cu
   const PassGeo& g = P.g;
   const dim3 grid(g.blk_col[axis][op], ncomp);
   const size_t sm = g.sm_col[axis][op];
+  const Cost<T> k(P.h);
+  const double by = 2 * k.spec(ncomp), fl = k.colfft(axis, ncomp);
+  const int pi = prec_index(sizeof(T));
   if (op == OP_FWD)
-    k_colplain<T, OP_FWD, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis);
+    prof_launch(pi, KK_COL_FWD, by, fl, st,
+                [&] { k_colplain<T, OP_FWD, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis); });
   else
-    k_colplain<T, OP_INV, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis);
+    prof_launch(pi, KK_COL_INV, by, fl, st,
+                [&] { k_colplain<T, OP_INV, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis); });
 }
 
 template <typename T, int OP, int BX>
@@ -101,13 +148,32 @@ static void launch_colop_bx(const Plan<T>& P, int axis, cudaStream_t st) {
   const PassGeo& g = P.g;
   const int nb = g.blk_col[axis][OP];
   const size_t sm = g.sm_col[axis][OP];
+  const Cost<T> k(P.h);
+  const bool d3 = P.h.ndim == 3;
+  double by, fl;
+  int kind;
+  if (OP == OP_GRAD) {
+    kind = KK_COL_GRAD;
+    by = k.spec(k.c) + k.spec(k.s);
+    fl = k.colfft(axis, k.c + k.s) + (d3 ? 42.0 : 20.0) * k.Vh;
+  } else if (OP == OP_DIV) {
+    kind = KK_COL_DIV;
+    by = k.spec(k.s) + k.spec(k.c);
+    fl = k.colfft(axis, k.c + k.s) + (d3 ? 36.0 : 16.0) * k.Vh;
+  } else {
+    kind = KK_COL_PREC;
+    by = 2 * k.spec(k.c);
+    fl = k.colfft(axis, 2 * k.c) + (d3 ? 100.0 : 40.0) * k.Vh;
+  }
   // slots: c (2 or 3) for the preconditioner, s (3 or 6) for gradient / divergence
   constexpr int kSmall = OP == OP_PREC ? 2 : 3;
   constexpr int kLarge = OP == OP_PREC ? 3 : 6;
-  if (P.h.ndim == 2)
-    k_colop<T, OP, BX, kSmall><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
-  else
-    k_colop<T, OP, BX, kLarge><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
+  prof_launch(prec_index(sizeof(T)), kind, by, fl, st, [&] {
+    if (!d3)
+      k_colop<T, OP, BX, kSmall><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
+    else
+      k_colop<T, OP, BX, kLarge><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
+  });
 }
 
 template <typename T, int OP>
@@ -139,15 +205,25 @@ template <typename T>
 static void launch_xinv(const Plan<T>& P, int post, int in_slot, int out_slot, int masked, int want_dot,
                         cudaStream_t st) {
   const PassGeo& g = P.g;
+  const Cost<T> k(P.h);
+  const int pi = prec_index(sizeof(T));
+  const double in = k.spec(k.c), fl = k.xfft(k.c);
+  const double mat = (P.h.phase ? 2.0 : 0.0) * k.V + k.V;  // phase ids + mask bytes
   switch (post) {
     case POST_APPLY:
-      k_xinv<T, POST_APPLY><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, want_dot);
+      prof_launch(pi, KK_XINV_APPLY, in + 2 * k.real(k.c) + mat, fl + 2 * k.c * k.V, st, [&] {
+        k_xinv<T, POST_APPLY><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, want_dot);
+      });
       break;
     case POST_RESID:
-      k_xinv<T, POST_RESID><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, want_dot);
+      prof_launch(pi, KK_XINV_RESID, in + 24 * k.c * k.V + mat, fl + 3 * k.c * k.V, st, [&] {
+        k_xinv<T, POST_RESID><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, want_dot);
+      });
       break;
     default:
-      k_xinv<T, POST_PREC><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, 0);
+      prof_launch(pi, KK_XINV_PREC, in + k.real(k.c) + k.V, fl, st, [&] {
+        k_xinv<T, POST_PREC><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, 0);
+      });
       break;
   }
 }
@@ -160,7 +236,13 @@ void launch_apply(const Plan<T>& P, int pre, int in_slot, int post, int out_slot
   if (D.midAxis) launch_col<T>(P, OP_FWD, D.midAxis, D.c, st);
   launch_col<T>(P, OP_GRAD, D.opAxis, D.c, st);
   if (D.midAxis) launch_col<T>(P, OP_INV, D.midAxis, D.s, st);
-  k_xmid<T><<<P.g.blk_xm, P.g.thr, P.g.sm_xm, st>>>(P.d, P.g.LXm);
+  {
+    const Cost<T> k(D);
+    const double by = 2 * k.spec(k.s) + (D.phase ? 2.0 : 0.0) * k.V;
+    const double fl = 2 * k.xfft(k.s) + (D.ndim == 3 ? 66.0 : 15.0) * k.V;
+    prof_launch(prec_index(sizeof(T)), KK_XMID, by, fl, st,
+                [&] { k_xmid<T><<<P.g.blk_xm, P.g.thr, P.g.sm_xm, st>>>(P.d, P.g.LXm); });
+  }
   if (D.midAxis) launch_col<T>(P, OP_FWD, D.midAxis, D.s, st);
   launch_col<T>(P, OP_DIV, D.opAxis, D.c, st);
   if (D.midAxis) launch_col<T>(P, OP_INV, D.midAxis, D.c, st);
@@ -225,13 +307,15 @@ void launch_rfft3(const Plan<T>& P, int dir, int ncomp, int real_slot, cudaStrea
   const size_t sm = (size_t)(D.n1 + (lx * ncomp / 2) * D.n1) * sizeof(cplx<T>);
   const int axes[2] = {1, 2};
   if (dir < 0) {
-    k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, -1, real_slot);
+    prof_launch(prec_index(sizeof(T)), KK_XFWD_PLAIN, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
+                Cost<T>(D).xfft(ncomp), st, [&] { k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, -1, real_slot); });
     for (int a : axes)
       if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T>(P, OP_FWD, a, ncomp, st);
   } else {
     for (int a : {2, 1})
       if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T>(P, OP_INV, a, ncomp, st);
-    k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, +1, real_slot);
+    prof_launch(prec_index(sizeof(T)), KK_XINV_PREC, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
+                Cost<T>(D).xfft(ncomp), st, [&] { k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, +1, real_slot); });
   }
 }
 

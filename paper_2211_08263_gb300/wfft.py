@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libwfft.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "wfft.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENUMERIC, ETIMEOUT, EUNSUPPORTED = range(8)
+KERNEL_KINDS = ["xfwd_plain", "xfwd_pupd", "xfwd_rupd", "xfwd_conv", "xinv_apply", "xinv_resid", "xinv_prec",
+                "xmid", "col_fwd", "col_inv", "col_grad", "col_div", "col_prec", "newmark", "scalar"]
 FP64, MIXED = 0, 1
 WARM_PREV, WARM_TAYLOR, WARM_LEARNED = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENUMERIC", 6: "ETIMEOUT",
@@ -90,6 +92,9 @@ def load(path: str = LIB_PATH):
     lib.wfft_batch_step.argtypes = [P(vp), i, P(d), P(StepInfo)]
     lib.wfft_get_sizes.argtypes = [vp, P(i), P(i), P(C.c_longlong)]
     lib.wfft_device_bytes.argtypes = [vp, P(C.c_size_t)]
+    lib.wfft_profile.argtypes = [vp, i]
+    lib.wfft_profile_read.argtypes = [vp, i, i, P(C.c_longlong), P(C.c_longlong), P(d), P(d), P(d)]
+    lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
     _lib = lib
     return lib
 
@@ -172,6 +177,12 @@ class Solver:
         self._check(self.lib.wfft_get_state(self.h, _ptr(u), _ptr(v), _ptr(a), C.byref(n)))
         return u, v, a, n.value
 
+    def download_u(self, out: np.ndarray) -> int:
+        """Copy u_n into `out` (host, [c][N3][N2][N1] float64, may be pinned); returns n."""
+        n = C.c_longlong()
+        self._check(self.lib.wfft_get_state(self.h, _ptr(out), None, None, C.byref(n)))
+        return n.value
+
     def set_state_dev(self, u, v, a, n: int = 0):
         self._check(self.lib.wfft_set_state_dev(self.h, _dptr(u), _dptr(v), _dptr(a), n))
 
@@ -208,6 +219,29 @@ class Solver:
 
     def rfft3(self, inp, out, precision: int = FP64, direction: int = -1, ncomp: int = 1):
         self._check(self.lib.wfft_rfft3(self.h, precision, direction, ncomp, _dptr(inp), _dptr(out)))
+
+    # ---- launch accounting
+    def profile(self, enable: bool):
+        self._check(self.lib.wfft_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        """{(precision, kind): {launches, timed, ms, bytes, flops}} for kinds with launches."""
+        out = {}
+        for prec in (FP64, MIXED):
+            for k, name in enumerate(KERNEL_KINDS):
+                n, t = C.c_longlong(), C.c_longlong()
+                ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+                self._check(self.lib.wfft_profile_read(self.h, prec, k, C.byref(n), C.byref(t), C.byref(ms),
+                                                       C.byref(by), C.byref(fl)))
+                if n.value:
+                    out[("fp64" if prec == FP64 else "fp32", name)] = {
+                        "launches": n.value, "timed": t.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
+        return out
+
+    def launch_count(self) -> int:
+        n = C.c_longlong()
+        self._check(self.lib.wfft_launch_count(self.h, C.byref(n)))
+        return n.value
 
     def spectral_pitch(self) -> int:
         p = C.c_int()
