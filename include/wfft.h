@@ -231,6 +231,34 @@ WFFT_API int wfft_profile_read(wfft_handle* h, int precision, int kind, long lon
 /* Total kernel launches issued by the handle since creation. */
 WFFT_API int wfft_launch_count(const wfft_handle* h, long long* launches);
 
+/*
+ * Preconditioner application z = M r (Eq. precond with Eq. acous, unmasked),
+ * FP64, for callers that cannot allocate device memory -- e.g. a framework
+ * that owns every device byte through its own arena once it has started, or
+ * code that must not change the device allocation state while other work is
+ * in flight.  It needs no handle and performs no cudaMalloc / cudaFree or any
+ * other allocating call: its scratch (kernel descriptor, scalars, twiddles,
+ * partial sums, spectral work buffer) is one fixed __device__ array of
+ * 16.25 MiB in the library, held by every GPU that loads the library until
+ * the process exits.  The paper has no counterpart of this call.
+ *   grid      : sizes as for wfft_create; c * N3 * N2 * pitch complex doubles must
+ *               fit 16 MiB (pitch = N1/2+1 rounded up to 8), e.g. up to 64^3 in 3-D;
+ *               larger grids return WFFT_EINVAL without touching the device.
+ *   cbar      : 21 Voigt values of the reference stiffness (the volume average
+ *               of C(x) for the paper's preconditioner); must be SPD.
+ *   rho_bar   : reference density (> 0); theta = beta dt^2 (> 0).
+ *   r_dev     : device FP64 [c][N3][N2][N1] input;  z_dev: device FP64 output.
+ *   stream    : cudaStream_t cast to void* (NULL = legacy default stream).
+ * Asynchronous on `stream`.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and sets the
+ * kernels' shared-memory attributes; make that first call before any stream
+ * capture.  All calls share the one scratch array and it keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Errors: wfft_last_error(NULL).
+ */
+WFFT_API int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21], double rho_bar, double theta,
+                                  const double* r_dev, double* z_dev, void* stream);
+
 /* Query helpers. */
 WFFT_API int wfft_get_sizes(const wfft_handle* h, int* ndim, int n[3], long long* nvox);
 WFFT_API int wfft_device_bytes(const wfft_handle* h, size_t* bytes);

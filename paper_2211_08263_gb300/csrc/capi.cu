@@ -15,6 +15,7 @@
 #include "launch.cuh"
 #include "passes.cuh"
 #include "profiler.cuh"
+#include "host_util.h"
 
 using namespace wfft;
 
@@ -53,6 +54,11 @@ struct ProfScope {
 
 static std::string g_err;
 
+namespace wfft {
+// Error text of calls that have no handle (wfft_last_error(NULL)).
+void set_global_error(const char* msg) { g_err = msg; }
+}  // namespace wfft
+
 static int fail(wfft_handle* h, int code, const std::string& msg) {
   if (h)
     h->err = msg;
@@ -76,103 +82,6 @@ static cudaError_t dalloc(wfft_handle* h, P** ptr, size_t bytes) {
   h->dev_allocs.push_back(p);
   *ptr = reinterpret_cast<P*>(p);
   return cudaSuccess;
-}
-
-// radix schedule: as many 8s as possible, the rest of the power of two as 4s / a 2
-// (4*4 rather than 8*2), then the odd radices 3, 5, 7
-static bool factorize(int n, AxisPlan& pl) {
-  pl.n = n;
-  for (int i = 0; i < 6; ++i) pl.cnt[i] = 0;
-  if (n < 1 || n > 512) return false;
-  int m = n, e2 = 0;
-  while (m % 2 == 0) {
-    m /= 2;
-    ++e2;
-  }
-  while (e2 >= 3 && e2 != 4) {
-    pl.cnt[0]++;
-    e2 -= 3;
-  }
-  if (e2 == 4) pl.cnt[1] += 2;
-  else if (e2 == 2) pl.cnt[1] += 1;
-  else if (e2 == 1) pl.cnt[2] += 1;
-  const int odd[3] = {3, 5, 7};
-  for (int q = 0; q < 3; ++q)
-    while (m % odd[q] == 0) {
-      pl.cnt[3 + q]++;
-      m /= odd[q];
-    }
-  return m == 1;
-}
-
-template <typename T>
-static std::vector<cplx<T>> twiddles(int n) {
-  std::vector<cplx<T>> w(n);
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int m = 0; m < n; ++m) {
-    const long double a = -2.0L * pi * (long double)m / (long double)n;
-    w[m].x = (T)cosl(a);
-    w[m].y = (T)sinl(a);
-  }
-  return w;
-}
-
-// Cholesky test of a symmetric matrix (row-major, size k)
-static bool spd(const double* m, int k) {
-  double L[36] = {0};
-  for (int i = 0; i < k; ++i) {
-    for (int j = 0; j <= i; ++j) {
-      double s = m[i * k + j];
-      for (int q = 0; q < j; ++q) s -= L[i * 6 + q] * L[j * 6 + q];
-      if (i == j) {
-        if (!(s > 0)) return false;
-        L[i * 6 + i] = std::sqrt(s);
-      } else {
-        L[i * 6 + j] = s / L[j * 6 + j];
-      }
-    }
-  }
-  return true;
-}
-
-static void voigt_full(const double* c21, double* m6) {
-  int k = 0;
-  for (int i = 0; i < 6; ++i)
-    for (int j = i; j < 6; ++j) {
-      m6[i * 6 + j] = m6[j * 6 + i] = c21[k];
-      ++k;
-    }
-}
-
-// Quadratic-form coefficients of theta*K(xi), K = B^T Cbar B (Eq. acous), B the
-// engineering strain-displacement map of xi.
-static void precond_coeffs(const double* cbar21, double theta, double kq[6][6]) {
-  double C[36];
-  voigt_full(cbar21, C);
-  double b[6][3][3] = {};
-  b[0][0][0] = 1;
-  b[1][1][1] = 1;
-  b[2][2][2] = 1;
-  b[3][1][2] = 1;
-  b[3][2][1] = 1;
-  b[4][0][2] = 1;
-  b[4][2][0] = 1;
-  b[5][0][1] = 1;
-  b[5][1][0] = 1;
-  const int pi_[6] = {0, 1, 2, 1, 0, 0}, pj_[6] = {0, 1, 2, 2, 2, 1};
-  const int mk[6] = {0, 1, 2, 1, 0, 0}, mm[6] = {0, 1, 2, 2, 2, 1};
-  for (int pr = 0; pr < 6; ++pr) {
-    const int i = pi_[pr], j = pj_[pr];
-    double G[3][3] = {};
-    for (int k = 0; k < 3; ++k)
-      for (int m = 0; m < 3; ++m)
-        for (int I = 0; I < 6; ++I)
-          for (int J = 0; J < 6; ++J) G[k][m] += b[I][i][k] * C[I * 6 + J] * b[J][j][m];
-    for (int mo = 0; mo < 6; ++mo) {
-      const int k = mk[mo], m = mm[mo];
-      kq[pr][mo] = theta * (k == m ? G[k][k] : G[k][m] + G[m][k]);
-    }
-  }
 }
 
 template <typename T>

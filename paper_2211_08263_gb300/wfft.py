@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.wfft_profile.argtypes = [vp, i]
     lib.wfft_profile_read.argtypes = [vp, i, i, P(C.c_longlong), P(C.c_longlong), P(d), P(d), P(d)]
     lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
+    lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -247,6 +248,17 @@ class Solver:
         p = C.c_int()
         self._check(self.lib.wfft_spectral_pitch(self.h, C.byref(p)))
         return p.value
+
+
+def precond_noalloc(ndim: int, n, h, cbar21, rho_bar: float, theta: float, r, z, stream: int = 0):
+    """z = M r (FP64, unmasked) through the allocation-free entry point; r, z are device arrays."""
+    lib = load()
+    g = Grid(ndim, (C.c_int * 3)(*[int(v) for v in n]), (C.c_double * 3)(*[float(v) for v in h]))
+    cb = (C.c_double * 21)(*[float(v) for v in cbar21])
+    rc = lib.wfft_precond_noalloc(C.byref(g), cb, float(rho_bar), float(theta), _dptr(r), _dptr(z),
+                                  C.c_void_p(stream))
+    if rc != OK:
+        raise WfftError(rc, lib.wfft_last_error(None).decode())
 
 
 def batch_step(solvers, U: np.ndarray):
