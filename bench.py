@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--modes", default="mixed,fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
     return ap.parse_args()
 
 
@@ -135,9 +136,11 @@ def load_peaks():
 FP64_PEAK_GFLOPS = 1195.2
 
 
-def run_mode(wfft, torch, prob, precision, W, K, world, e2e: bool):
+def run_mode(wfft, torch, prob, precision, W, K, world, e2e: bool, inner_tol=None):
     stream = torch.cuda.current_stream()
     opt = wfft.default_options(precision=precision, tol=1e-10, maxit=500, check_every=4)
+    if inner_tol:
+        opt.inner_tol = inner_tol
     s = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
     for n in range(W):
         s.step(prob.U[n])
@@ -294,7 +297,8 @@ def main():
         prec = wfft.MIXED if m == "mixed" else wfft.FP64
         if m == modes[0]:
             clocks.start()
-        results[m] = run_mode(wfft, torch, prob, prec, W, K, world, e2e=(m == modes[0] and not args.no_e2e))
+        results[m] = run_mode(wfft, torch, prob, prec, W, K, world, e2e=(m == modes[0] and not args.no_e2e),
+                              inner_tol=args.inner_tol)
         if m == modes[0]:
             clk = clocks.stop()
     head = results[modes[0]]

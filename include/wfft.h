@@ -94,7 +94,7 @@ typedef struct {
   double ms;           /* device time of the call (CUDA events) */
 } wfft_step_info;
 
-/* Fill *opt with defaults: FP64, tol 1e-10, maxit 1000, WARM_PREV, inner_tol 1e-4,
+/* Fill *opt with defaults: FP64, tol 1e-10, maxit 1000, WARM_PREV, inner_tol 1e-5,
    max_sweeps 20, check_every 4. */
 WFFT_API int wfft_default_options(wfft_options* opt);
 

@@ -42,6 +42,9 @@ struct wfft_handle {
   bool has_mask = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   Profiler prof;
+  bool au_valid = false;    // SL_AU holds A u for the current state u (mixed mode)
+  bool last_resid_on_x = false;
+  double U_prev[3] = {0, 0, 0};
   std::string err;
 };
 
@@ -190,7 +193,7 @@ extern "C" int wfft_default_options(wfft_options* o) {
   o->tol = 1e-10;
   o->maxit = 1000;
   o->warm_start = WFFT_WARM_PREV;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-5;
   o->max_sweeps = 20;
   o->check_every = 4;
   o->watchdog_iters = 0;
@@ -359,7 +362,14 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
     CKC(cudaMemset(p, 0, vec * sizeof(double)));
     D.slot[sl] = p;
   }
-  if (h->opt.precision == WFFT_FP64) D.slot[SL_R64] = D.slot[SL_R];
+  if (h->opt.precision == WFFT_FP64) {
+    D.slot[SL_R64] = D.slot[SL_R];
+  } else {
+    double* au;
+    CKC(dalloc(h, &au, vec * sizeof(double)));
+    CKC(cudaMemset(au, 0, vec * sizeof(double)));
+    D.slot[SL_AU] = au;
+  }
   double* w;
   CKC(dalloc(h, &w, vec * h->ndim * sizeof(double)));
   CKC(cudaMemset(w, 0, vec * h->ndim * sizeof(double)));
@@ -464,6 +474,7 @@ static int state_copy(wfft_handle* h, int to_dev, double* u, double* v, double* 
 extern "C" int wfft_set_state(wfft_handle* h, const double* u, const double* v, const double* a, long long n) {
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
   h->nstep = n;
+  h->au_valid = false;
   return state_copy(h, 1, (double*)u, (double*)v, (double*)a, cudaMemcpyHostToDevice);
 }
 extern "C" int wfft_get_state(const wfft_handle* hc, double* u, double* v, double* a, long long* n) {
@@ -475,6 +486,7 @@ extern "C" int wfft_get_state(const wfft_handle* hc, double* u, double* v, doubl
 extern "C" int wfft_set_state_dev(wfft_handle* h, const double* u, const double* v, const double* a, long long n) {
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
   h->nstep = n;
+  h->au_valid = false;
   return state_copy(h, 1, (double*)u, (double*)v, (double*)a, cudaMemcpyDeviceToDevice);
 }
 extern "C" int wfft_get_state_dev(const wfft_handle* hc, double* u, double* v, double* a) {
@@ -520,7 +532,7 @@ static int pcg_loop(wfft_handle* h, Plan<T>& P, Scalars* sc, int which, int budg
 }
 
 // Solve with B, X set and sc64->ref2 known; fills status / counts.
-static int solve_core(wfft_handle* h, wfft_step_info* info) {
+static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false) {
   Plan<double>& P = h->P64;
   const Desc<double>& D = P.h;
   const int op = D.opAxis;
@@ -540,10 +552,18 @@ static int solve_core(wfft_handle* h, wfft_step_info* info) {
   } else {
     Plan<float>& F = h->P32;
     const Desc<float>& DF = F.h;
+    bool stored = use_au;
     for (;;) {
-      launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
-      launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_OUTER, h->sc32, h->st);
-      ++outer;
+      if (stored) {
+        // initial residual already formed by the predictor from the stored A u
+        launch_fin(h->sc64, D.part[PT_B], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_OUTER, h->sc32, h->st);
+      } else {
+        launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
+        launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_OUTER, h->sc32, h->st);
+        ++outer;
+      }
+      h->last_resid_on_x = !stored;
+      stored = false;
       CKH(h, cudaGetLastError());
       int rc = read_scalars(h);
       if (rc) return rc;
@@ -600,13 +620,20 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
   if (h->opt.warm_start == WFFT_WARM_LEARNED) return fail(h, WFFT_EINVAL, "no warm-start model loaded");
   Plan<double>& P = h->P64;
   const double Uv[3] = {U[0], h->ndim > 1 ? U[1] : 0.0, h->ndim > 2 ? U[2] : 0.0};
+  const bool use_au = h->opt.precision == WFFT_MIXED && h->au_valid && h->opt.warm_start == WFFT_WARM_PREV;
+  const double dU[3] = {Uv[0] - h->U_prev[0], Uv[1] - h->U_prev[1], Uv[2] - h->U_prev[2]};
   CKH(h, cudaEventRecord(h->ev0, h->st));
-  launch_begin(h->sc64, Uv, h->opt.warm_start, h->opt.tol * h->opt.tol, h->opt.maxit, h->st);
+  launch_begin(h->sc64, Uv, h->opt.warm_start, h->opt.tol * h->opt.tol, h->opt.maxit, h->st, use_au ? 1 : 0, dU);
   launch_begin(h->sc32, Uv, h->opt.warm_start, h->opt.inner_tol * h->opt.inner_tol, h->opt.maxit, h->st);
   launch_predict(P, h->st);
   launch_fin(h->sc64, P.h.part[PT_A], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
-  int status = solve_core(h, info);
+  h->last_resid_on_x = false;
+  int status = solve_core(h, info, use_au);
+  // the stored A x is A u_n only if the last residual evaluation ran on the final x
+  h->au_valid = status == WFFT_OK && h->opt.precision == WFFT_MIXED && h->last_resid_on_x &&
+                !h->host_sc[0].zero_free;
   if (status == WFFT_OK) {
+    for (int k = 0; k < 3; ++k) h->U_prev[k] = Uv[k];
     launch_correct(P, h->st);
     const int nb = ew_block_count(P);
     launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
@@ -647,6 +674,7 @@ extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
   if (!b || !x) return fail(h, WFFT_EINVAL, "b and x are required");
   fill_info_base(info);
+  h->au_valid = false;  // the residual evaluations below overwrite the stored A u
   Plan<double>& P = h->P64;
   const size_t bytes = (size_t)h->c * h->V * sizeof(double);
   const double t = tol > 0 ? tol : h->opt.tol;

@@ -39,6 +39,7 @@ struct Scalars {
   double xcoef;     // x += xcoef * alpha * p  (1/scale in mixed, 1 in FP64)
   double react[3];
   double Ug[3];     // U(t_n) of the current step
+  double dU[3];     // U(t_n) - U(t_{n-1}) (stored-A u initial residual)
   int iter;         // operator applications inside the Krylov loop
   int maxit;
   int done;         // 1: every kernel of this solve returns immediately
@@ -47,6 +48,7 @@ struct Scalars {
   int zero_free;    // 1: ref == 0, the solution is x_Gamma
   int converged;
   int warm;         // WFFT_WARM_* of the current step
+  int use_au;       // 1: the predictor forms r0 = P(b - A u) from the stored A u
 };
 
 // Buffer slots of an instance.
@@ -55,6 +57,7 @@ enum Slot {
   SL_R, SL_Z, SL_P, SL_Q,                     // Krylov vectors in T
   SL_EXT_IN, SL_EXT_OUT,                      // caller-owned arrays (wfft_apply & co.)
   SL_W,                                       // lifting fields, ndim x c components (FP64)
+  SL_AU,                                      // A x of the latest FP64 residual evaluation (FP64)
   NSLOT
 };
 

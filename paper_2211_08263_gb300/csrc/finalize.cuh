@@ -13,7 +13,8 @@ constexpr int kEwBlocks = 1216;
 
 void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc, int mode,
                 Scalars* sc2, cudaStream_t st);
-void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st);
+void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st,
+                  int use_au = 0, const double* dU = nullptr);
 void launch_set_done(Scalars* sc, int done, cudaStream_t st);
 int ew_block_count(const Plan<double>& P);
 

@@ -29,7 +29,10 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
   double* x = reinterpret_cast<double*>(D.slot[SL_X]);
   const double U0 = sc->Ug[0], U1 = sc->Ug[1], U2 = sc->Ug[2];
   const int warm = sc->warm;
-  double acc = 0.0;
+  const bool use_au = sc->use_au != 0;
+  const double* au = reinterpret_cast<const double*>(D.slot[SL_AU]);
+  double* r64 = reinterpret_cast<double*>(D.slot[SL_R64]);
+  double acc = 0.0, accr = 0.0;
   const long long tot = (long long)c * V;
   for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
        gi += (long long)gridDim.x * blockDim.x) {
@@ -56,9 +59,24 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
       if (nd > 2) t -= U2 * w[2 * tot + gi];
       acc += t * t;
     }
+    if (use_au) {
+      // x0 = u_{n-1} + sum_j dU_j E e_j, so P(b - A x0) = P(b - A u_{n-1}) - sum_j dU_j w_j,
+      // with A u_{n-1} kept from the previous step's last FP64 residual evaluation
+      double rv = bv - au[gi];
+      rv -= sc->dU[0] * w[gi];
+      if (nd > 1) rv -= sc->dU[1] * w[tot + gi];
+      if (nd > 2) rv -= sc->dU[2] * w[2 * tot + gi];
+      if (isg) rv = 0.0;
+      r64[gi] = rv;
+      accr += rv * rv;
+    }
   }
   const double s = block_sum(acc);
   if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+  if (use_au) {
+    const double sr = block_sum(accr);
+    if (threadIdx.x == 0) D.part[PT_B][blockIdx.x] = sr;
+  }
 }
 
 // Corrector (Eq. Newmark): a_n = (u_n - u~)/(beta dt^2), v_n = v + dt((1-gamma) a + gamma a_n);
@@ -152,7 +170,7 @@ __global__ void k_fin(Scalars* sc, const double* pa, int na, const double* pb, i
   const double scc = pc ? fixed_order_sum(pc, nc) : 0.0;
   if (threadIdx.x != 0) return;
   // a finished solve is frozen: only the setup / bookkeeping modes still run
-  if (sc->done && mode != FIN_REF && mode != FIN_OUTER && mode != FIN_REACT) return;
+  if (sc->done && mode != FIN_REF && mode != FIN_REACT) return;
   switch (mode) {
     case FIN_REF:
       sc->ref2 = sa;
@@ -247,7 +265,8 @@ __global__ void k_fin(Scalars* sc, const double* pa, int na, const double* pb, i
   }
 }
 
-__global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, double tol2, int maxit) {
+__global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, double tol2, int maxit, int use_au,
+                        double d0, double d1, double d2) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   sc->Ug[0] = U0;
   sc->Ug[1] = U1;
@@ -267,6 +286,10 @@ __global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, 
   sc->rz = 0.0;
   sc->alpha = 0.0;
   sc->beta = 0.0;
+  sc->use_au = use_au;
+  sc->dU[0] = d0;
+  sc->dU[1] = d1;
+  sc->dU[2] = d2;
 }
 
 __global__ void k_set_done(Scalars* sc, int done) {
@@ -278,8 +301,11 @@ void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb,
   prof_launch(0, KK_SCALAR, 8.0 * (na + nb + nc), (double)(na + nb + nc), st,
               [&] { k_fin<<<1, 256, 0, st>>>(sc, pa, na, pb, nb, pc, nc, mode, sc2); });
 }
-void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st) {
-  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit); });
+void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st, int use_au,
+                  const double* dU) {
+  const double d0 = dU ? dU[0] : 0.0, d1 = dU ? dU[1] : 0.0, d2 = dU ? dU[2] : 0.0;
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st,
+              [&] { k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit, use_au, d0, d1, d2); });
 }
 void launch_set_done(Scalars* sc, int done, cudaStream_t st) {
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_set_done<<<1, 32, 0, st>>>(sc, done); });

@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, in
     } else if (POST == POST_RESID) {
       const T xv = reinterpret_cast<const T*>(D.slot[SL_X])[gi];
       const T bv = reinterpret_cast<const T*>(D.slot[SL_B])[gi];
-      T rv = bv - (t + rho_at<T>(D, vox) * xv);
+      const T ax = t + rho_at<T>(D, vox) * xv;
+      if (D.slot[SL_AU]) reinterpret_cast<T*>(D.slot[SL_AU])[gi] = ax;
+      T rv = bv - ax;
       if (isg) rv = 0;
       reinterpret_cast<T*>(D.slot[SL_R64])[gi] = rv;
       acc += (double)rv * (double)rv;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, in
 // its lines (line stride 1, element stride NS * BX).
 // ---------------------------------------------------------------------------
 constexpr int kColThreadsPlain = 256;  // plain transforms (one component per block)
-constexpr int kColThreadsOp = 512;     // fused gradient / divergence / preconditioner
+constexpr int kColThreadsOp = 256;     // fused gradient / divergence / preconditioner
 
 template <typename T>
 struct ColGeo {
@@ -350,7 +352,7 @@ __device__ __forceinline__ void col_xi(const Desc<T>& D, const ColGeo<T>& g, int
 
 // Plain transform of one component (blockIdx.y) along `axis`.
 template <typename T, int OP, int BX>
-__global__ void __launch_bounds__(kColThreadsPlain) k_colplain(const Desc<T>* __restrict__ dd, int axis) {
+__global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4) k_colplain(const Desc<T>* __restrict__ dd, int axis) {
   const Desc<T>& D = *dd;
   if (D.sc->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(kColThreadsPlain) k_colplain(const Desc<T>* __
 //   OP_PREC: c residuals r^ -> z^ = (1/V) (theta K(xi) + rho_bar I)^-1 r^, with the
 //            Parseval partial sum of (r, z) over the half spectrum
 template <typename T, int OP, int BX, int NS>
-__global__ void __launch_bounds__(kColThreadsOp) k_colop(const Desc<T>* __restrict__ dd, int axis) {
+__global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop(const Desc<T>* __restrict__ dd, int axis) {
   constexpr int ES = NS * BX;
   const Desc<T>& D = *dd;
   Scalars* sc = D.sc;
