@@ -114,6 +114,9 @@ static int build_plan(wfft_handle* h, Plan<T>& P, const std::vector<double>& cta
   D.kx1 = twopi / (h->n[0] * h->h[0]);
   D.kx2 = twopi / (h->n[1] * h->h[1]);
   D.kx3 = twopi / (h->n[2] * h->h[2]);
+  D.ks[0] = (T)D.kx1;
+  D.ks[1] = (T)D.kx2;
+  D.ks[2] = (T)D.kx3;
   D.invV = (T)(1.0 / (double)h->V);
   D.theta = (T)h->theta;
   D.mthetaInvV = (T)(-h->theta / (double)h->V);
@@ -378,6 +381,14 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   Desc<float>& F = h->P32.h;
   for (int sl : {(int)SL_U, (int)SL_V, (int)SL_A, (int)SL_B, (int)SL_X, (int)SL_W}) F.slot[sl] = D.slot[sl];
   F.slot[SL_R64] = h->opt.precision == WFFT_FP64 ? nullptr : D.slot[SL_R64];
+  if (h->opt.precision == WFFT_MIXED) {
+    // FP32 correction of the inner solve, folded into x by the FP64 residual pass
+    float* dcor;
+    CKC(dalloc(h, &dcor, vec * sizeof(float)));
+    CKC(cudaMemset(dcor, 0, vec * sizeof(float)));
+    F.slot[SL_D] = dcor;
+    D.slot[SL_D] = dcor;
+  }
   // partial sums and scalars
   h->nparts = std::max({h->P64.g.max_blocks, h->P32.g.max_blocks, kEwBlocks});
   for (int k = 0; k < NPART; ++k) {
@@ -390,6 +401,7 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   CKC(cudaMemset(h->sc32, 0, sizeof(Scalars)));
   D.sc = h->sc64;
   F.sc = h->sc32;
+  D.sc_inner = h->sc32;
   CKC(cudaMallocHost(&h->host_sc, 2 * sizeof(Scalars)));
   memset(h->host_sc, 0, 2 * sizeof(Scalars));
   CKC(upload_desc(h->P64));
@@ -558,7 +570,8 @@ static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false)
         // initial residual already formed by the predictor from the stored A u
         launch_fin(h->sc64, D.part[PT_B], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_OUTER, h->sc32, h->st);
       } else {
-        launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
+        // after an inner solve the residual pass first folds its FP32 correction into x
+        launch_apply<double>(P, sweeps > 0 ? PRE_XUPD : PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
         launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_OUTER, h->sc32, h->st);
         ++outer;
       }

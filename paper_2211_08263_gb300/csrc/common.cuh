@@ -58,6 +58,7 @@ enum Slot {
   SL_EXT_IN, SL_EXT_OUT,                      // caller-owned arrays (wfft_apply & co.)
   SL_W,                                       // lifting fields, ndim x c components (FP64)
   SL_AU,                                      // A x of the latest FP64 residual evaluation (FP64)
+  SL_D,                                       // mixed: FP32 correction of the inner solve
   NSLOT
 };
 
@@ -73,6 +74,7 @@ struct Desc {
   long long V;             // voxels
   long long Vh;            // complex elements per spectral component (n3*n2*pitch)
   double kx1, kx2, kx3;    // 2 pi / L_i
+  T ks[3];                 // 2 pi / L_i in T
   T invV;
   T theta;
   T mthetaInvV;            // -theta / V
@@ -89,6 +91,7 @@ struct Desc {
   cplx<T>* spec;           // spectral work buffer, s components x Vh
   double* part[NPART];     // partial sums
   Scalars* sc;
+  Scalars* sc_inner;       // FP64 descriptor of a mixed solve: the FP32 inner solve's scalars
   // Newmark constants (used by the FP64 descriptor)
   double dt, beta, gamma;
 };
@@ -119,13 +122,46 @@ __device__ __forceinline__ cplx<T> cmuli(cplx<T> a, int sgn) {
   return sgn > 0 ? cmake<T>(-a.y, a.x) : cmake<T>(a.y, -a.x);
 }
 
-// Discrete frequency of index k on an axis of n points (FFT order) times 2pi/L;
-// the unpaired Nyquist index k = n/2 of an even axis gets 0.
-__device__ __forceinline__ double xi_of(int k, int n, double twoPiOverL) {
-  if (2 * k == n) return 0.0;
-  int kk = (k <= (n - 1) / 2) ? k : k - n;
-  return (double)kk * twoPiOverL;
+// Discrete frequency of index k on an axis of n points (FFT order) times 2pi/L,
+// in the kernel's arithmetic type; the unpaired Nyquist index k = n/2 of an
+// even axis gets 0.
+template <typename T>
+__device__ __forceinline__ T xi_of(int k, int n, T twoPiOverL) {
+  if (2 * k == n) return (T)0;
+  const int kk = (2 * k < n) ? k : k - n;
+  return (T)kk * twoPiOverL;
 }
+
+// Dot-product accumulator: FP64 in FP64 kernels; in FP32 kernels a
+// double-float (hi, lo) pair updated with error-free transformations (TwoProd by
+// FMA, TwoSum), so FP32 x FP32 products are summed exactly to ~2^-48 without
+// touching the FP64 units (1/62 of the FP32 rate on GB300).
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a) {
+    const float s = hi + a;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (a - bb);  // TwoSum
+    hi = s;
+    lo += err;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);  // TwoProd
+    add(p);
+    lo += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 // Block-wide sum of one double per thread; result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {

@@ -134,37 +134,50 @@ struct Dft<T, 7> {
   }
 };
 
+// log2 of v if v is a power of two, else -1
+__device__ __forceinline__ int log2_if_pow2(int v) { return (v & (v - 1)) ? -1 : __ffs(v) - 1; }
+
 // One in-place Stockham stage over `nlines` lines of length N.
 // Row tiles (ES == 1): element e of line l at buf[l * lstride + e]; consecutive
-// threads take consecutive butterflies of a line.  Column tiles (ES > 1):
-// element e of line l at buf[l + e * ES]; consecutive threads take consecutive
-// lines.  Both keep shared-memory accesses conflict-free; a compile-time ES
-// keeps the address arithmetic to shifts.
-template <typename T, int R, int ES>
+// threads take consecutive butterflies of a line.  Column tiles (ES > 1, NL
+// lines, both compile-time): element e of line l at buf[l + e * ES];
+// consecutive threads take consecutive lines.  Both keep shared-memory
+// accesses conflict-free; compile-time strides and line counts and shifts for
+// power-of-two N and Ns keep the index arithmetic off the integer divider.
+template <typename T, int R, int ES, int NL>
 __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int lstride, int Ns, const cplx<T>* tw,
                                           int sgn) {
   constexpr int NB = NbOf<T, R>::v;
   constexpr bool LF = ES > 1;
   const int nb = N / R;
-  const int total = nb * nlines;
+  const int nl = LF ? NL : nlines;
+  const int total = nb * nl;
   const int nthr = blockDim.x;
   // read the thread index opaquely: keeps the compiler from hoisting every
   // stage's index arithmetic out of the callers' loops (register pressure)
   int tid;
   asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+  const int lgnb = log2_if_pow2(nb);
+  const int lgNs = log2_if_pow2(Ns);
   cplx<T> v[NB][R];
+  int jj[NB], ll[NB];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int id = tid + i * nthr;
+    int line = 0, j = 0;
+    if (LF) {
+      line = id % NL;
+      j = id / NL;
+    } else if (lgnb >= 0) {
+      j = id & (nb - 1);
+      line = id >> lgnb;
+    } else {
+      j = id % nb;
+      line = id / nb;
+    }
+    jj[i] = j;
+    ll[i] = line;
     if (id < total) {
-      int line, j;
-      if (LF) {
-        line = id % nlines;
-        j = id / nlines;
-      } else {
-        j = id % nb;
-        line = id / nb;
-      }
       const cplx<T>* src = LF ? buf + line : buf + (size_t)line * lstride;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[i][r] = src[(j + r * nb) * ES];
@@ -175,15 +188,15 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
   for (int i = 0; i < NB; ++i) {
     const int id = tid + i * nthr;
     if (id < total) {
-      int line, j;
-      if (LF) {
-        line = id % nlines;
-        j = id / nlines;
+      const int j = jj[i], line = ll[i];
+      int k, g;
+      if (lgNs >= 0) {
+        k = j & (Ns - 1);
+        g = j >> lgNs;
       } else {
-        j = id % nb;
-        line = id / nb;
+        k = j % Ns;
+        g = j / Ns;
       }
-      const int k = j % Ns;
       if (Ns > 1) {
         const int step = (N / (Ns * R)) * k;
 #pragma unroll
@@ -195,7 +208,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
       }
       Dft<T, R>::run(v[i], sgn, tw, N);
       cplx<T>* dst = LF ? buf + line : buf + (size_t)line * lstride;
-      const int base = (j / Ns) * Ns * R + k;
+      const int base = g * Ns * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ES] = v[i][r];
     }
@@ -207,19 +220,19 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
 // Stages are applied radix by radix (8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
 // formulation is valid for any order of the radices, and one loop per radix
 // keeps each stage's registers apart.  ES = 1: row tiles with line stride
-// `lstride`; ES > 1: column tiles (line stride 1, element stride ES).
-// Must be called by every thread of the block (contains barriers).
-template <typename T, int ES>
+// `lstride` (nlines at run time); ES > 1: column tiles (line stride 1, element
+// stride ES, NL lines).  Must be called by every thread of the block (barriers).
+template <typename T, int ES, int NL = 0>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int nlines, int lstride, const cplx<T>* tw,
                                           int sgn) {
   const int N = pl.n;
   int Ns = 1;
-  for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
-  for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
-  for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
-  for (int s = 0; s < pl.cnt[3]; ++s, Ns *= 3) fft_stage<T, 3, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
-  for (int s = 0; s < pl.cnt[4]; ++s, Ns *= 5) fft_stage<T, 5, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
-  for (int s = 0; s < pl.cnt[5]; ++s, Ns *= 7) fft_stage<T, 7, ES>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[3]; ++s, Ns *= 3) fft_stage<T, 3, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[4]; ++s, Ns *= 5) fft_stage<T, 5, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[5]; ++s, Ns *= 7) fft_stage<T, 7, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
 }
 
 }  // namespace wfft

@@ -122,6 +122,9 @@ extern "C" int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21]
   D.kx1 = twopi / (grid->n[0] * grid->h[0]);
   D.kx2 = twopi / (grid->n[1] * grid->h[1]);
   D.kx3 = twopi / (grid->n[2] * grid->h[2]);
+  D.ks[0] = D.kx1;
+  D.ks[1] = D.kx2;
+  D.ks[2] = D.kx3;
   D.invV = 1.0 / (double)D.V;
   D.theta = theta;
   D.mthetaInvV = -theta / (double)D.V;

@@ -22,7 +22,7 @@
 
 namespace wfft {
 
-enum { PRE_PLAIN = 0, PRE_PUPD = 1, PRE_RUPD = 2, PRE_CONV = 3 };
+enum { PRE_PLAIN = 0, PRE_PUPD = 1, PRE_RUPD = 2, PRE_CONV = 3, PRE_XUPD = 4 };
 enum { POST_APPLY = 0, POST_RESID = 1, POST_PREC = 2 };
 enum { OP_FWD = 0, OP_INV = 1, OP_GRAD = 2, OP_DIV = 3, OP_PREC = 4 };
 
@@ -37,50 +37,70 @@ __device__ __forceinline__ T& packed(cplx<T>* buf, int lstr, int q, int x) {
   return reinterpret_cast<T*>(buf + (size_t)(q >> 1) * lstr + x)[q & 1];
 }
 
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+__device__ __forceinline__ int num_warps() { return blockDim.x >> 5; }
+
 // Split the complex FFT of two packed real lines into their half spectra and
 // store them: A = (Z_k + conj Z_{N-k})/2, B = (Z_k - conj Z_{N-k})/(2i).
+// One warp per pair of lines, lanes along kx (no integer division per element).
 template <typename T>
 __device__ __forceinline__ void store_unpacked(const Desc<T>& D, const cplx<T>* buf, int lstr, int nlines_real,
                                                long long l0, int nc, long long nsp) {
   const int N = D.n1, nh = D.nh;
   const int npairs = nlines_real >> 1;
-  for (int e = threadIdx.x; e < npairs * nh; e += blockDim.x) {
-    const int kx = e % nh, p = e / nh;
-    const cplx<T> Z = buf[(size_t)p * lstr + kx];
-    const cplx<T> W = buf[(size_t)p * lstr + (kx == 0 ? 0 : N - kx)];
-    const T h = (T)0.5;
-    const cplx<T> A = cmake<T>((Z.x + W.x) * h, (Z.y - W.y) * h);
-    const cplx<T> B = cmake<T>((Z.y + W.y) * h, (W.x - Z.x) * h);
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int q = 2 * p + half;
-      const int l = q / nc, k = q % nc;
-      const long long line = l0 + l;
-      if (line < nsp) D.spec[(long long)k * D.Vh + line * D.pitch + kx] = half ? B : A;
+  for (int p = warp_id(); p < npairs; p += num_warps()) {
+    const int qa = 2 * p, qb = 2 * p + 1;
+    const long long la = l0 + qa / nc, lb = l0 + qb / nc;
+    cplx<T>* da = D.spec + (long long)(qa % nc) * D.Vh + la * D.pitch;
+    cplx<T>* db = D.spec + (long long)(qb % nc) * D.Vh + lb * D.pitch;
+    const cplx<T>* row = buf + (size_t)p * lstr;
+    for (int kx = lane_id(); kx < nh; kx += 32) {
+      const cplx<T> Z = row[kx];
+      const cplx<T> W = row[kx == 0 ? 0 : N - kx];
+      const T h = (T)0.5;
+      if (la < nsp) da[kx] = cmake<T>((Z.x + W.x) * h, (Z.y - W.y) * h);
+      if (lb < nsp) db[kx] = cmake<T>((Z.y + W.y) * h, (W.x - Z.x) * h);
     }
   }
 }
 
 // Load the half spectra of two real lines per complex line as Z = A + i B
 // over the full length (Hermitian extension); DC and Nyquist take real parts.
+// Load the half spectra of two real lines per complex line as Z = A + i B
+// over the full length (Hermitian extension); DC and Nyquist take real parts.
+// One warp per pair of lines; each lane keeps 4 kx loads of both lines in flight.
 template <typename T>
 __device__ __forceinline__ void load_packed(const Desc<T>& D, cplx<T>* buf, int lstr, int nlines_real, long long l0,
                                             int nc, long long nsp) {
+  constexpr int U = 4;
   const int N = D.n1, nh = D.nh;
   const int npairs = nlines_real >> 1;
-  for (int e = threadIdx.x; e < npairs * nh; e += blockDim.x) {
-    const int kx = e % nh, p = e / nh;
-    cplx<T> A = cmake<T>(0, 0), B = cmake<T>(0, 0);
+  for (int p = warp_id(); p < npairs; p += num_warps()) {
     const int qa = 2 * p, qb = 2 * p + 1;
     const long long la = l0 + qa / nc, lb = l0 + qb / nc;
-    if (la < nsp) A = D.spec[(long long)(qa % nc) * D.Vh + la * D.pitch + kx];
-    if (lb < nsp) B = D.spec[(long long)(qb % nc) * D.Vh + lb * D.pitch + kx];
+    const cplx<T>* sa = D.spec + (long long)(qa % nc) * D.Vh + la * D.pitch;
+    const cplx<T>* sb = D.spec + (long long)(qb % nc) * D.Vh + lb * D.pitch;
     cplx<T>* row = buf + (size_t)p * lstr;
-    if (kx == 0 || 2 * kx == N) {
-      row[kx] = cmake<T>(A.x, B.x);
-    } else {
-      row[kx] = cmake<T>(A.x - B.y, A.y + B.x);
-      row[N - kx] = cmake<T>(A.x + B.y, B.x - A.y);
+    for (int k0 = lane_id(); k0 < nh; k0 += 32 * U) {
+      cplx<T> A[U], B[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kx = k0 + 32 * u;
+        A[u] = (kx < nh && la < nsp) ? sa[kx] : cmake<T>(0, 0);
+        B[u] = (kx < nh && lb < nsp) ? sb[kx] : cmake<T>(0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kx = k0 + 32 * u;
+        if (kx >= nh) continue;
+        if (kx == 0 || 2 * kx == N) {
+          row[kx] = cmake<T>(A[u].x, B[u].x);
+        } else {
+          row[kx] = cmake<T>(A[u].x - B[u].y, A[u].y + B[u].x);
+          row[N - kx] = cmake<T>(A[u].x + B[u].y, B[u].x - A[u].y);
+        }
+      }
     }
   }
 }
@@ -92,6 +112,13 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const cplx<T>* src, i
 
 // ---------------------------------------------------------------------------
 // x forward pass: real c-component field -> half spectrum, with fused updates
+//   PRE_PLAIN  input slot in_slot
+//   PRE_PUPD   p = z + beta p (p = z on the first iteration)
+//   PRE_RUPD   r -= alpha q, ||r||^2, and the solution update: x += alpha p (FP64
+//              solve) or d += alpha p (FP32 correction of a mixed inner solve)
+//   PRE_CONV   r = scale * r64 in T, d = 0 (start of a mixed inner solve)
+//   PRE_XUPD   x += xcoef * d (FP64 descriptor of a mixed solve: folds the
+//              finished inner correction into the FP64 solution) and transform x
 // ---------------------------------------------------------------------------
 template <typename T, int PRE>
 __global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, int LX, int in_slot) {
@@ -109,54 +136,89 @@ __global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, in
   load_twiddles<T>(tw, D.tw[0], N);
   bool first = false;
   T beta = 0, alpha = 0;
-  double xa = 0.0, scale = 1.0;
+  double scale = 1.0, xc = 0.0;
   if (PRE == PRE_PUPD) {
     first = sc->first != 0;
     beta = (T)sc->beta;
   }
-  if (PRE == PRE_RUPD) {
-    alpha = (T)sc->alpha;
-    xa = sc->alpha * sc->xcoef;
-  }
+  if (PRE == PRE_RUPD) alpha = (T)sc->alpha;
   if (PRE == PRE_CONV) scale = sc->scale;
-  double acc = 0.0;
-  const int tot = LX * nc * N;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int x = e % N, q = e / N;
+  if (PRE == PRE_XUPD) xc = D.sc_inner->xcoef;
+  DotAcc<T> acc;
+  constexpr int U = 4;  // elements per lane kept in flight
+  const int nq = LX * nc;
+  for (int q = warp_id(); q < nq; q += num_warps()) {
     const int k = q % nc, l = q / nc;
     const long long line = l0 + l;
-    T val = 0;
-    if (line < nsp) {
-      const long long gi = (long long)k * V + line * N + x;
-      if (PRE == PRE_PLAIN) {
-        val = reinterpret_cast<const T*>(D.slot[in_slot])[gi];
-      } else if (PRE == PRE_PUPD) {
-        T* p = reinterpret_cast<T*>(D.slot[SL_P]);
-        const T zv = reinterpret_cast<const T*>(D.slot[SL_Z])[gi];
-        const T pv = first ? zv : zv + beta * p[gi];
-        p[gi] = pv;
-        val = pv;
-      } else if (PRE == PRE_RUPD) {
-        double* xs = reinterpret_cast<double*>(D.slot[SL_X]);
-        const T pv = reinterpret_cast<const T*>(D.slot[SL_P])[gi];
-        const T qv = reinterpret_cast<const T*>(D.slot[SL_Q])[gi];
-        T* r = reinterpret_cast<T*>(D.slot[SL_R]);
-        xs[gi] += xa * (double)pv;
-        const T rv = r[gi] - alpha * qv;
-        r[gi] = rv;
-        val = rv;
-        acc += (double)rv * (double)rv;
-      } else {  // PRE_CONV: r = scale * r64 in T
-        const double rv64 = reinterpret_cast<const double*>(D.slot[SL_R64])[gi];
-        const T rv = (T)(rv64 * scale);
-        reinterpret_cast<T*>(D.slot[SL_R])[gi] = rv;
-        val = rv;
+    const bool valid = line < nsp;
+    const long long g0 = (long long)k * V + line * N;
+    for (int x0 = lane_id(); x0 < N; x0 += 32 * U) {
+      T a[U], b[U], c[U], e[U];
+      double w[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int x = x0 + 32 * u;
+        const bool ok = valid && x < N;
+        const long long gi = g0 + x;
+        a[u] = b[u] = c[u] = e[u] = 0;
+        w[u] = 0.0;
+        if (ok) {
+          if (PRE == PRE_PLAIN) {
+            a[u] = reinterpret_cast<const T*>(D.slot[in_slot])[gi];
+          } else if (PRE == PRE_PUPD) {
+            a[u] = reinterpret_cast<const T*>(D.slot[SL_Z])[gi];
+            if (!first) b[u] = reinterpret_cast<const T*>(D.slot[SL_P])[gi];
+          } else if (PRE == PRE_RUPD) {
+            a[u] = reinterpret_cast<const T*>(D.slot[SL_P])[gi];
+            b[u] = reinterpret_cast<const T*>(D.slot[SL_Q])[gi];
+            c[u] = reinterpret_cast<const T*>(D.slot[SL_R])[gi];
+            e[u] = sizeof(T) == 8 ? reinterpret_cast<const T*>(D.slot[SL_X])[gi]
+                                  : reinterpret_cast<const T*>(D.slot[SL_D])[gi];
+          } else if (PRE == PRE_CONV) {
+            w[u] = reinterpret_cast<const double*>(D.slot[SL_R64])[gi];
+          } else {  // PRE_XUPD (T = double)
+            a[u] = reinterpret_cast<const T*>(D.slot[SL_X])[gi];
+            e[u] = (T)reinterpret_cast<const float*>(D.slot[SL_D])[gi];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int x = x0 + 32 * u;
+        if (x >= N) continue;
+        const bool ok = valid;
+        const long long gi = g0 + x;
+        T val = 0;
+        if (ok) {
+          if (PRE == PRE_PLAIN) {
+            val = a[u];
+          } else if (PRE == PRE_PUPD) {
+            val = first ? a[u] : a[u] + beta * b[u];
+            reinterpret_cast<T*>(D.slot[SL_P])[gi] = val;
+          } else if (PRE == PRE_RUPD) {
+            const T sol = e[u] + alpha * a[u];
+            if (sizeof(T) == 8)
+              reinterpret_cast<T*>(D.slot[SL_X])[gi] = sol;
+            else
+              reinterpret_cast<T*>(D.slot[SL_D])[gi] = sol;
+            val = c[u] - alpha * b[u];
+            reinterpret_cast<T*>(D.slot[SL_R])[gi] = val;
+            acc.add_prod(val, val);
+          } else if (PRE == PRE_CONV) {
+            val = (T)(w[u] * scale);
+            reinterpret_cast<T*>(D.slot[SL_R])[gi] = val;
+            reinterpret_cast<T*>(D.slot[SL_D])[gi] = (T)0;
+          } else {  // PRE_XUPD
+            val = a[u] + (T)(xc * (double)e[u]);
+            reinterpret_cast<T*>(D.slot[SL_X])[gi] = val;
+          }
+        }
+        packed<T>(buf, lstr, q, x) = val;
       }
     }
-    packed<T>(buf, lstr, q, x) = val;
   }
   if (PRE == PRE_RUPD) {
-    const double s = block_sum(acc);
+    const double s = block_sum(acc.value());
     if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
   }
   __syncthreads();
@@ -166,6 +228,9 @@ __global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, in
 
 // ---------------------------------------------------------------------------
 // x inverse pass: half spectrum -> real field with fused epilogue
+//   POST_APPLY  q = t + rho p (t = -theta div sigma), mask, (p, q)
+//   POST_RESID  A x = t + rho x (kept when the slot exists), r = P(b - A x), ||r||^2
+//   POST_PREC   z = P(t)
 // ---------------------------------------------------------------------------
 template <typename T, int POST>
 __global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, int LX, int in_slot, int out_slot,
@@ -185,38 +250,63 @@ __global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, in
   load_packed<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
   __syncthreads();
   fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, lstr, tw, +1);
-  double acc = 0.0;
-  const int tot = LX * nc * N;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int x = e % N, q = e / N;
+  DotAcc<T> acc;
+  constexpr int U = 4;  // elements per lane kept in flight
+  const int nq = LX * nc;
+  for (int q = warp_id(); q < nq; q += num_warps()) {
     const int k = q % nc, l = q / nc;
     const long long line = l0 + l;
     if (line >= nsp) continue;
-    const long long vox = line * N + x;
-    const long long gi = (long long)k * V + vox;
-    const T t = packed<T>(buf, lstr, q, x);
-    const bool isg = masked && ((D.mask[vox] >> k) & 1);
-    if (POST == POST_APPLY) {
-      const T pin = reinterpret_cast<const T*>(D.slot[in_slot])[gi];
-      T qv = t + rho_at<T>(D, vox) * pin;
-      if (isg) qv = 0;
-      reinterpret_cast<T*>(D.slot[out_slot])[gi] = qv;
-      acc += (double)pin * (double)qv;
-    } else if (POST == POST_RESID) {
-      const T xv = reinterpret_cast<const T*>(D.slot[SL_X])[gi];
-      const T bv = reinterpret_cast<const T*>(D.slot[SL_B])[gi];
-      const T ax = t + rho_at<T>(D, vox) * xv;
-      if (D.slot[SL_AU]) reinterpret_cast<T*>(D.slot[SL_AU])[gi] = ax;
-      T rv = bv - ax;
-      if (isg) rv = 0;
-      reinterpret_cast<T*>(D.slot[SL_R64])[gi] = rv;
-      acc += (double)rv * (double)rv;
-    } else {  // POST_PREC
-      reinterpret_cast<T*>(D.slot[out_slot])[gi] = isg ? (T)0 : t;
+    for (int x0 = lane_id(); x0 < N; x0 += 32 * U) {
+      T a[U], b[U], rho[U];
+      uint8_t m[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int x = x0 + 32 * u;
+        a[u] = b[u] = rho[u] = 0;
+        m[u] = 0;
+        if (x < N) {
+          const long long vox = line * N + x;
+          const long long gi = (long long)k * V + vox;
+          if (masked) m[u] = D.mask[vox];
+          if (POST == POST_APPLY) {
+            a[u] = reinterpret_cast<const T*>(D.slot[in_slot])[gi];
+            rho[u] = rho_at<T>(D, vox);
+          } else if (POST == POST_RESID) {
+            a[u] = reinterpret_cast<const T*>(D.slot[SL_X])[gi];
+            b[u] = reinterpret_cast<const T*>(D.slot[SL_B])[gi];
+            rho[u] = rho_at<T>(D, vox);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int x = x0 + 32 * u;
+        if (x >= N) continue;
+        const long long vox = line * N + x;
+        const long long gi = (long long)k * V + vox;
+        const T t = packed<T>(buf, lstr, q, x);
+        const bool isg = (m[u] >> k) & 1;
+        if (POST == POST_APPLY) {
+          T qv = t + rho[u] * a[u];
+          if (isg) qv = 0;
+          reinterpret_cast<T*>(D.slot[out_slot])[gi] = qv;
+          acc.add_prod(a[u], qv);
+        } else if (POST == POST_RESID) {
+          const T ax = t + rho[u] * a[u];
+          if (D.slot[SL_AU]) reinterpret_cast<T*>(D.slot[SL_AU])[gi] = ax;
+          T rv = b[u] - ax;
+          if (isg) rv = 0;
+          reinterpret_cast<T*>(D.slot[SL_R64])[gi] = rv;
+          acc.add_prod(rv, rv);
+        } else {  // POST_PREC
+          reinterpret_cast<T*>(D.slot[out_slot])[gi] = isg ? (T)0 : t;
+        }
+      }
     }
   }
   if (POST != POST_PREC && want_dot) {
-    const double s = block_sum(acc);
+    const double s = block_sum(acc.value());
     if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
   }
 }
@@ -258,20 +348,28 @@ __global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, in
   __syncthreads();
   fft_lines<T, 1>(buf, D.ax[0], LX * ns / 2, lstr, tw, +1);
   const int cstride = (ns == 6) ? kCtabStride3 : kCtabStride2;
-  for (int e = threadIdx.x; e < LX * N; e += blockDim.x) {
-    const int x = e % N, l = e / N;
+  for (int l = warp_id(); l < LX; l += num_warps()) {
     const long long line = l0 + l;
     if (line >= nsp) continue;
-    const long long vox = line * N + x;
-    const long long row = D.phase ? (long long)D.phase[vox] : vox;
-    const T* C = D.ctab + row * cstride;
-    T ev[6];
-    for (int k = 0; k < ns; ++k) ev[k] = packed<T>(buf, lstr, l * ns + k, x);
-    if (ns == 6)
-      hooke3<T>(C, ev);
-    else
-      hooke2<T>(C, ev);
-    for (int k = 0; k < ns; ++k) packed<T>(buf, lstr, l * ns + k, x) = ev[k];
+    for (int x = lane_id(); x < N; x += 32) {
+      const long long vox = line * N + x;
+      const long long row = D.phase ? (long long)D.phase[vox] : vox;
+      const T* C = D.ctab + row * cstride;
+      T ev[6];
+      if (ns == 6) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ev[k] = packed<T>(buf, lstr, l * 6 + k, x);
+        hooke3<T>(C, ev);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) packed<T>(buf, lstr, l * 6 + k, x) = ev[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ev[k] = packed<T>(buf, lstr, l * 3 + k, x);
+        hooke2<T>(C, ev);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) packed<T>(buf, lstr, l * 3 + k, x) = ev[k];
+      }
+    }
   }
   __syncthreads();
   fft_lines<T, 1>(buf, D.ax[0], LX * ns / 2, lstr, tw, -1);
@@ -317,12 +415,28 @@ __device__ __forceinline__ ColGeo<T> col_geo(const Desc<T>& D, int axis, int BX)
   return g;
 }
 
+// Tile loads keep kLoadBatch independent global loads in flight per thread.
+constexpr int kLoadBatch = 8;
+
 template <typename T, int BX, int ES>
 __device__ __forceinline__ void col_load(const Desc<T>& D, const ColGeo<T>& g, int comp, cplx<T>* tl, int slot) {
   const cplx<T>* src = D.spec + (long long)comp * D.Vh + g.base;
-  for (int e = threadIdx.x; e < g.N * BX; e += blockDim.x) {
-    const int y = e / BX, b = e % BX;
-    tl[y * ES + slot * BX + b] = (g.kx0 + b < D.nh) ? src[(long long)y * g.est + b] : cmake<T>(0, 0);
+  const int tot = g.N * BX;
+  const int nthr = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += nthr * kLoadBatch) {
+    cplx<T> v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * nthr;
+      const int y = e / BX, b = e % BX;
+      v[u] = (e < tot && g.kx0 + b < D.nh) ? src[(long long)y * g.est + b] : cmake<T>(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * nthr;
+      const int y = e / BX, b = e % BX;
+      if (e < tot) tl[y * ES + slot * BX + b] = v[u];
+    }
   }
 }
 
@@ -336,17 +450,17 @@ __device__ __forceinline__ void col_store(const Desc<T>& D, const ColGeo<T>& g, 
   }
 }
 
-// frequency vector of tile element (axis index y, column b)
+// frequency vector of tile element (axis index y, column b), in T
 template <typename T>
 __device__ __forceinline__ void col_xi(const Desc<T>& D, const ColGeo<T>& g, int axis, int y, int b, T& x1, T& x2,
                                        T& x3) {
-  x1 = (T)xi_of(g.kx0 + b, D.n1, D.kx1);
+  x1 = xi_of<T>(g.kx0 + b, D.n1, D.ks[0]);
   if (axis == 2) {
-    x2 = (T)xi_of(g.outer, D.n2, D.kx2);
-    x3 = (T)xi_of(y, D.n3, D.kx3);
+    x2 = xi_of<T>(g.outer, D.n2, D.ks[1]);
+    x3 = xi_of<T>(y, D.n3, D.ks[2]);
   } else {
-    x2 = (T)xi_of(y, D.n2, D.kx2);
-    x3 = (T)xi_of(g.outer, D.n3, D.kx3);
+    x2 = xi_of<T>(y, D.n2, D.ks[1]);
+    x3 = xi_of<T>(g.outer, D.n3, D.ks[2]);
   }
 }
 
@@ -364,7 +478,7 @@ __global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4) k_co
   const int comp = blockIdx.y;
   col_load<T, BX, BX>(D, g, comp, tl, 0);
   __syncthreads();
-  fft_lines<T, BX>(tl, pl, BX, 1, tw, OP == OP_FWD ? -1 : +1);
+  fft_lines<T, BX, BX>(tl, pl, BX, 1, tw, OP == OP_FWD ? -1 : +1);
   col_store<T, BX, BX>(D, g, comp, tl, 0);
 }
 
@@ -386,13 +500,16 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
   cplx<T>* tl = tw + N;
   load_twiddles<T>(tw, D.tw[axis], N);
   const AxisPlan pl = D.ax[axis];
-  const int c = D.c;
-  const int nin = (OP == OP_DIV) ? D.s : c;
-  const int nout = (OP == OP_GRAD) ? D.s : c;
-  for (int k = 0; k < nin; ++k) col_load<T, BX, ES>(D, g, k, tl, k);
+  // component counts, compile-time from the slot count: 3-D has NS = 6 (gradient,
+  // divergence) or 3 (preconditioner), 2-D has 3 or 2
+  constexpr int kC = (OP == OP_PREC) ? NS : (NS == 6 ? 3 : 2);
+  constexpr int kS = (OP == OP_PREC) ? 0 : NS;
+  constexpr int NIN = (OP == OP_DIV) ? kS : kC;
+  constexpr int NOUT = (OP == OP_GRAD) ? kS : kC;
+  for (int k = 0; k < NIN; ++k) col_load<T, BX, ES>(D, g, k, tl, k);
   __syncthreads();
-  fft_lines<T, ES>(tl, pl, nin * BX, 1, tw, -1);
-  double acc = 0.0;
+  fft_lines<T, ES, NIN * BX>(tl, pl, NIN * BX, 1, tw, -1);
+  DotAcc<T> acc;
   for (int e = threadIdx.x; e < N * BX; e += blockDim.x) {
     const int y = e / BX, b = e % BX;
     cplx<T>* el = tl + y * ES + b;  // slot t at el[t * BX]
@@ -400,7 +517,7 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
     col_xi<T>(D, g, axis, y, b, x1, x2, x3);
     if (OP == OP_GRAD) {
       const T iv = D.invV;
-      if (c == 3) {
+      if (kC == 3) {
         const cplx<T> u1 = el[0], u2 = el[BX], u3 = el[2 * BX];
         el[0] = cmuli<T>(cscale<T>(u1, x1 * iv), +1);
         el[BX] = cmuli<T>(cscale<T>(u2, x2 * iv), +1);
@@ -416,7 +533,7 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
       }
     } else if (OP == OP_DIV) {
       const T f = D.mthetaInvV;
-      if (c == 3) {
+      if (kC == 3) {
         const cplx<T> s11 = el[0], s22 = el[BX], s33 = el[2 * BX], s23 = el[3 * BX], s13 = el[4 * BX],
                       s12 = el[5 * BX];
         const cplx<T> t1 = cadd<T>(cadd<T>(cscale<T>(s11, x1), cscale<T>(s12, x2)), cscale<T>(s13, x3));
@@ -434,7 +551,7 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
       }
     } else {  // OP_PREC
       const int kx = g.kx0 + b;
-      const double wgt = (kx >= D.nh) ? 0.0 : ((kx == 0 || 2 * kx == D.n1) ? 1.0 : 2.0);
+      const T wgt = (kx >= D.nh) ? (T)0 : ((kx == 0 || 2 * kx == D.n1) ? (T)1 : (T)2);
       const T m0 = x1 * x1, m1 = x2 * x2, m2 = x3 * x3, m3 = x2 * x3, m4 = x1 * x3, m5 = x1 * x2;
       T Mv[6];
 #pragma unroll
@@ -445,7 +562,7 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
       Mv[1] += D.rhobar;
       Mv[2] += D.rhobar;
       const T iv = D.invV;
-      if (c == 3) {
+      if (kC == 3) {
         const T a = Mv[0], bb = Mv[1], cc = Mv[2], f = Mv[3], ee = Mv[4], d = Mv[5];
         const T A00 = bb * cc - f * f, A11 = a * cc - ee * ee, A22 = a * bb - d * d;
         const T A01 = ee * f - d * cc, A02 = d * f - bb * ee, A12 = d * ee - a * f;
@@ -455,8 +572,12 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
         const cplx<T> z1 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A00), cscale<T>(r2, A01)), cscale<T>(r3, A02)), id);
         const cplx<T> z2 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A01), cscale<T>(r2, A11)), cscale<T>(r3, A12)), id);
         const cplx<T> z3 = cscale<T>(cadd<T>(cadd<T>(cscale<T>(r1, A02), cscale<T>(r2, A12)), cscale<T>(r3, A22)), id);
-        acc += wgt * ((double)r1.x * z1.x + (double)r1.y * z1.y + (double)r2.x * z2.x + (double)r2.y * z2.y +
-                      (double)r3.x * z3.x + (double)r3.y * z3.y);
+        acc.add_prod(wgt * r1.x, z1.x);
+        acc.add_prod(wgt * r1.y, z1.y);
+        acc.add_prod(wgt * r2.x, z2.x);
+        acc.add_prod(wgt * r2.y, z2.y);
+        acc.add_prod(wgt * r3.x, z3.x);
+        acc.add_prod(wgt * r3.y, z3.y);
         el[0] = z1;
         el[BX] = z2;
         el[2 * BX] = z3;
@@ -466,19 +587,22 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
         const cplx<T> r1 = el[0], r2 = el[BX];
         const cplx<T> z1 = cscale<T>(csub<T>(cscale<T>(r1, bb), cscale<T>(r2, d)), id);
         const cplx<T> z2 = cscale<T>(csub<T>(cscale<T>(r2, a), cscale<T>(r1, d)), id);
-        acc += wgt * ((double)r1.x * z1.x + (double)r1.y * z1.y + (double)r2.x * z2.x + (double)r2.y * z2.y);
+        acc.add_prod(wgt * r1.x, z1.x);
+        acc.add_prod(wgt * r1.y, z1.y);
+        acc.add_prod(wgt * r2.x, z2.x);
+        acc.add_prod(wgt * r2.y, z2.y);
         el[0] = z1;
         el[BX] = z2;
       }
     }
   }
   if (OP == OP_PREC) {
-    const double s = block_sum(acc);  // contains barriers
+    const double s = block_sum(acc.value());  // contains barriers
     if (threadIdx.x == 0) D.part[PT_B][blockIdx.x] = s;
   }
   __syncthreads();
-  fft_lines<T, ES>(tl, pl, nout * BX, 1, tw, +1);
-  for (int k = 0; k < nout; ++k) col_store<T, BX, ES>(D, g, k, tl, k);
+  fft_lines<T, ES, NOUT * BX>(tl, pl, NOUT * BX, 1, tw, +1);
+  for (int k = 0; k < NOUT; ++k) col_store<T, BX, ES>(D, g, k, tl, k);
 }
 
 }  // namespace wfft

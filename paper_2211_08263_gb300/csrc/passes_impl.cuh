@@ -117,12 +117,16 @@ static void launch_xfwd(const Plan<T>& P, int pre, int in_slot, cudaStream_t st)
                   [&] { k_xfwd<T, PRE_PUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
       break;
     case PRE_RUPD:
-      prof_launch(pi, KK_XFWD_RUPD, 16 * k.c * k.V + 4 * k.real(k.c) + out, fl + 6 * k.c * k.V, st,
+      prof_launch(pi, KK_XFWD_RUPD, 6 * k.real(k.c) + out, fl + 6 * k.c * k.V, st,
                   [&] { k_xfwd<T, PRE_RUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
       break;
-    default:
-      prof_launch(pi, KK_XFWD_CONV, 8 * k.c * k.V + k.real(k.c) + out, fl + k.c * k.V, st,
+    case PRE_CONV:
+      prof_launch(pi, KK_XFWD_CONV, 8 * k.c * k.V + 2 * k.real(k.c) + out, fl + k.c * k.V, st,
                   [&] { k_xfwd<T, PRE_CONV><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      break;
+    default:  // PRE_XUPD: x += xcoef d (FP64 x, FP32 d), then transform x
+      prof_launch(pi, KK_XFWD_PLAIN, 2 * k.real(k.c) + 4 * k.c * k.V + out, fl + 2 * k.c * k.V, st,
+                  [&] { k_xfwd<T, PRE_XUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
       break;
   }
 }
@@ -332,6 +336,7 @@ cudaError_t init_kernel_attributes() {
   WFFT_SETATTR((k_xfwd<T, PRE_PUPD>));
   WFFT_SETATTR((k_xfwd<T, PRE_RUPD>));
   WFFT_SETATTR((k_xfwd<T, PRE_CONV>));
+  WFFT_SETATTR((k_xfwd<T, PRE_XUPD>));
   WFFT_SETATTR((k_xinv<T, POST_APPLY>));
   WFFT_SETATTR((k_xinv<T, POST_RESID>));
   WFFT_SETATTR((k_xinv<T, POST_PREC>));
