@@ -390,7 +390,10 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
     D.slot[SL_D] = dcor;
   }
   // partial sums and scalars
-  h->nparts = std::max({h->P64.g.max_blocks, h->P32.g.max_blocks, kEwBlocks});
+  // room for the block partial sums of any column-tile width (grouped launches may
+  // use a narrower tile than the instance's own plan)
+  const int colmax = (h->n[0] / 2 + 1) * std::max(h->n[1], h->n[2]);
+  h->nparts = std::max({h->P64.g.max_blocks, h->P32.g.max_blocks, kEwBlocks, colmax});
   for (int k = 0; k < NPART; ++k) {
     CKC(dalloc(h, &D.part[k], (size_t)h->nparts * sizeof(double)));
     CKC(dalloc(h, &F.part[k], (size_t)h->nparts * sizeof(double)));
@@ -787,12 +790,354 @@ extern "C" int wfft_rfft3(wfft_handle* h, int precision, int dir, int ncomp, con
   return fail(h, WFFT_EINVAL, "unknown precision");
 }
 
+// ---------------------------------------------------------------------------
+// grouped steps of several handles: every pass is one launch over all
+// instances that have not converged yet
+// ---------------------------------------------------------------------------
+namespace {
+
+enum FinSlot {
+  FJ_REF = 0, FJ_RES0, FJ_RZ0, FJ_ALPHA, FJ_BETA, FJ_OUTER_STORED, FJ_OUTER_RESID, FJ_REACT,
+  FJ_RZ0_32, FJ_ALPHA_32, FJ_BETA_32, FJ_N
+};
+
+struct BatchCtx {
+  std::vector<wfft_handle*> hs;
+  int precision = -1;
+  BatchLaunch<double> bl64;
+  BatchLaunch<float> bl32;
+  std::vector<void*> dev;  // device allocations of this context
+  FinJob* fin[FJ_N] = {};
+  BeginJob* begin64 = nullptr;
+  BeginJob* begin32 = nullptr;
+  Scalars* host = nullptr;  // pinned mirror: [i] = sc64 of instance i, [n + i] = sc32
+  Scalars* const* dsrc = nullptr;  // device: sc64 pointers then sc32 pointers
+  Scalars* dgather = nullptr;      // device: gathered copies
+  std::vector<BeginJob> hb64, hb32;
+  ~BatchCtx() {
+    for (void* p : dev) cudaFree(p);
+    if (host) cudaFreeHost(host);
+  }
+};
+BatchCtx* g_batch = nullptr;
+
+template <typename T>
+cudaError_t build_launch(BatchCtx& B, BatchLaunch<T>& bl, Plan<T> wfft_handle::*plan, std::vector<void*>& dev) {
+  const int n = (int)B.hs.size();
+  bl.n = n;
+  bl.plans.clear();
+  for (wfft_handle* h : B.hs) bl.plans.push_back(&(h->*plan));
+  // common column-tile width: the narrowest of the instances
+  for (int ax = 1; ax <= 2; ++ax)
+    for (int op = 0; op < 5; ++op) {
+      int bx = 8;
+      for (const Plan<T>* q : bl.plans) bx = std::min(bx, std::max(1, q->g.bx[ax][op]));
+      bl.bx[ax][op] = bx;
+    }
+  std::vector<int> starts((size_t)NGEO * (n + 1));
+  for (int cls = 0; cls < NGEO; ++cls) {
+    int acc = 0;
+    size_t sm = 0;
+    int bx = 1;
+    if (cls >= GEO_COL0 && cls < GEO_EW) bx = bl.bx[(cls - GEO_COL0) / 5 + 1][(cls - GEO_COL0) % 5];
+    for (int i = 0; i < n; ++i) {
+      starts[(size_t)cls * (n + 1) + i] = acc;
+      acc += geo_blocks<T>(*bl.plans[i], cls, bx);
+      sm = std::max(sm, geo_smem<T>(*bl.plans[i], cls, bx));
+    }
+    starts[(size_t)cls * (n + 1) + n] = acc;
+    bl.total[cls] = acc;
+    bl.sm[cls] = sm;
+  }
+  void *dstart = nullptr, *ddesc = nullptr;
+  cudaError_t e = cudaMalloc(&dstart, starts.size() * sizeof(int));
+  if (e != cudaSuccess) return e;
+  dev.push_back(dstart);
+  e = cudaMemcpy(dstart, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  for (int cls = 0; cls < NGEO; ++cls) bl.start[cls] = reinterpret_cast<int*>(dstart) + (size_t)cls * (n + 1);
+  std::vector<const Desc<T>*> descs;
+  for (const Plan<T>* q : bl.plans) descs.push_back(q->d);
+  e = cudaMalloc(&ddesc, descs.size() * sizeof(void*));
+  if (e != cudaSuccess) return e;
+  dev.push_back(ddesc);
+  e = cudaMemcpy(ddesc, descs.data(), descs.size() * sizeof(void*), cudaMemcpyHostToDevice);
+  bl.descs = reinterpret_cast<const Desc<T>* const*>(ddesc);
+  return e;
+}
+
+template <typename T>
+int blocks_of(const BatchLaunch<T>& bl, int i, int cls) {
+  int bx = 1;
+  if (cls >= GEO_COL0 && cls < GEO_EW) bx = bl.bx[(cls - GEO_COL0) / 5 + 1][(cls - GEO_COL0) % 5];
+  return geo_blocks<T>(*bl.plans[i], cls, bx);
+}
+
+int build_batch(std::vector<wfft_handle*>& hs, BatchCtx*& out, std::string& err) {
+  BatchCtx* B = new BatchCtx();
+  B->hs = hs;
+  B->precision = hs[0]->opt.precision;
+  const int n = (int)hs.size();
+  cudaError_t e = build_launch<double>(*B, B->bl64, &wfft_handle::P64, B->dev);
+  if (e == cudaSuccess) e = build_launch<float>(*B, B->bl32, &wfft_handle::P32, B->dev);
+  std::vector<FinJob> jobs((size_t)FJ_N * n);
+  for (int i = 0; i < n; ++i) {
+    wfft_handle* h = hs[i];
+    const Desc<double>& D = h->P64.h;
+    const Desc<float>& F = h->P32.h;
+    const int ew = blocks_of(B->bl64, i, GEO_EW), bx64 = blocks_of(B->bl64, i, GEO_X);
+    const int pr64 = blocks_of(B->bl64, i, geo_col(D.opAxis, OP_PREC));
+    const int bx32 = blocks_of(B->bl32, i, GEO_X), pr32 = blocks_of(B->bl32, i, geo_col(F.opAxis, OP_PREC));
+    auto J = [&](int slot) -> FinJob& { return jobs[(size_t)slot * n + i]; };
+    J(FJ_REF) = {h->sc64, D.part[PT_A], ew, nullptr, 0, nullptr, 0, nullptr};
+    J(FJ_RES0) = {h->sc64, D.part[PT_A], bx64, nullptr, 0, nullptr, 0, nullptr};
+    J(FJ_RZ0) = {h->sc64, nullptr, 0, D.part[PT_B], pr64, nullptr, 0, nullptr};
+    J(FJ_ALPHA) = {h->sc64, D.part[PT_A], bx64, nullptr, 0, nullptr, 0, nullptr};
+    J(FJ_BETA) = {h->sc64, D.part[PT_A], bx64, D.part[PT_B], pr64, nullptr, 0, nullptr};
+    J(FJ_OUTER_STORED) = {h->sc64, D.part[PT_B], ew, nullptr, 0, nullptr, 0, h->sc32};
+    J(FJ_OUTER_RESID) = {h->sc64, D.part[PT_A], bx64, nullptr, 0, nullptr, 0, h->sc32};
+    J(FJ_REACT) = {h->sc64, D.part[PT_A], ew, D.part[PT_B], ew, D.part[PT_C], ew, nullptr};
+    J(FJ_RZ0_32) = {h->sc32, nullptr, 0, F.part[PT_B], pr32, nullptr, 0, nullptr};
+    J(FJ_ALPHA_32) = {h->sc32, F.part[PT_A], bx32, nullptr, 0, nullptr, 0, nullptr};
+    J(FJ_BETA_32) = {h->sc32, F.part[PT_A], bx32, F.part[PT_B], pr32, nullptr, 0, nullptr};
+  }
+  if (e == cudaSuccess) {
+    std::vector<Scalars*> ptrs(2 * n);
+    for (int i = 0; i < n; ++i) {
+      ptrs[i] = hs[i]->sc64;
+      ptrs[n + i] = hs[i]->sc32;
+    }
+    void *dp = nullptr, *dg = nullptr;
+    e = cudaMalloc(&dp, ptrs.size() * sizeof(Scalars*));
+    if (e == cudaSuccess) {
+      B->dev.push_back(dp);
+      e = cudaMemcpy(dp, ptrs.data(), ptrs.size() * sizeof(Scalars*), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&dg, 2 * n * sizeof(Scalars));
+    if (e == cudaSuccess) {
+      B->dev.push_back(dg);
+      B->dsrc = reinterpret_cast<Scalars* const*>(dp);
+      B->dgather = reinterpret_cast<Scalars*>(dg);
+    }
+  }
+  void* dj = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&dj, jobs.size() * sizeof(FinJob) + 2 * n * sizeof(BeginJob));
+  if (e == cudaSuccess) {
+    B->dev.push_back(dj);
+    e = cudaMemcpy(dj, jobs.data(), jobs.size() * sizeof(FinJob), cudaMemcpyHostToDevice);
+    for (int k = 0; k < FJ_N; ++k) B->fin[k] = reinterpret_cast<FinJob*>(dj) + (size_t)k * n;
+    B->begin64 = reinterpret_cast<BeginJob*>(reinterpret_cast<FinJob*>(dj) + jobs.size());
+    B->begin32 = B->begin64 + n;
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&B->host, 2 * n * sizeof(Scalars));
+  if (e != cudaSuccess) {
+    err = std::string("batch context: ") + cudaGetErrorString(e);
+    delete B;
+    return WFFT_ECUDA;
+  }
+  B->hb64.resize(n);
+  B->hb32.resize(n);
+  out = B;
+  return WFFT_OK;
+}
+
+int batch_read(BatchCtx& B, cudaStream_t st) {
+  const int n = (int)B.hs.size();
+  launch_gather_scalars(B.dsrc, B.dgather, 2 * n, st);
+  cudaError_t e = cudaMemcpyAsync(B.host, B.dgather, 2 * n * sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? WFFT_OK : WFFT_ECUDA;
+}
+
+bool all_done(const BatchCtx& B, int which) {
+  const int n = (int)B.hs.size();
+  for (int i = 0; i < n; ++i)
+    if (!B.host[which * n + i].done) return false;
+  return true;
+}
+
+// Lockstep PCG iterations of plan type T over all instances until every one is done.
+template <typename T>
+int batch_pcg(BatchCtx& B, const BatchLaunch<T>& bl, const Plan<T>& P0, int which, int fa, int fb, int budget,
+              int check_every, cudaStream_t st) {
+  const int n = (int)B.hs.size();
+  int launched = 0;
+  for (;;) {
+    for (int i = 0; i < check_every; ++i) {
+      launch_apply<T>(P0, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, st, &bl);
+      launch_fin_batch(B.fin[fa], n, FIN_ALPHA, st);
+      launch_precond<T>(P0, PRE_RUPD, SL_R, SL_Z, 1, st, &bl);
+      launch_fin_batch(B.fin[fb], n, FIN_BETA, st);
+      ++launched;
+    }
+    if (cudaGetLastError() != cudaSuccess) return WFFT_ECUDA;
+    if (batch_read(B, st)) return WFFT_ECUDA;
+    if (all_done(B, which)) return WFFT_OK;
+    if (launched >= budget) return WFFT_ETIMEOUT;
+  }
+}
+
+}  // namespace
+
 extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step_info* infos) {
   if (!hs || n < 0 || (n > 0 && !U)) return fail(nullptr, WFFT_EINVAL, "bad batch arguments");
+  if (n == 0) return WFFT_OK;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]) return fail(nullptr, WFFT_EINVAL, "null handle in batch");
+  wfft_handle* h0 = hs[0];
+  // the grouped path needs one structure: same precision, dimensionality, pass
+  // sequence, stream and warm start; otherwise the handles step one by one
+  bool grouped = n > 1;
+  for (int i = 1; i < n && grouped; ++i) {
+    wfft_handle* h = hs[i];
+    grouped = h->opt.precision == h0->opt.precision && h->ndim == h0->ndim && h->st == h0->st &&
+              h->P64.h.midAxis == h0->P64.h.midAxis && h->P64.h.opAxis == h0->P64.h.opAxis &&
+              h->opt.warm_start == h0->opt.warm_start && h->opt.warm_start != WFFT_WARM_LEARNED;
+  }
+  if (!grouped) {
+    int first = WFFT_OK;
+    for (int i = 0; i < n; ++i) {
+      int rc = wfft_step(hs[i], U + 3 * i, infos ? &infos[i] : nullptr);
+      if (rc && !first) first = rc;
+    }
+    return first;
+  }
+  std::vector<wfft_handle*> v(hs, hs + n);
+  if (!g_batch || g_batch->hs != v || g_batch->precision != h0->opt.precision) {
+    delete g_batch;
+    g_batch = nullptr;
+    std::string err;
+    int rc = build_batch(v, g_batch, err);
+    if (rc) return fail(nullptr, rc, err);
+  }
+  BatchCtx& B = *g_batch;
+  cudaStream_t st = h0->st;
+  ProfScope ps_(h0);
+  const bool mixed = h0->opt.precision == WFFT_MIXED;
+  bool use_au = mixed && h0->opt.warm_start == WFFT_WARM_PREV;
+  for (int i = 0; i < n; ++i) use_au = use_au && hs[i]->au_valid;
+  for (int i = 0; i < n; ++i) {
+    wfft_handle* h = hs[i];
+    const double Uv[3] = {U[3 * i], h->ndim > 1 ? U[3 * i + 1] : 0.0, h->ndim > 2 ? U[3 * i + 2] : 0.0};
+    BeginJob& b = B.hb64[i];
+    b.sc = h->sc64;
+    for (int k = 0; k < 3; ++k) {
+      b.U[k] = Uv[k];
+      b.dU[k] = Uv[k] - h->U_prev[k];
+    }
+    b.warm = h->opt.warm_start;
+    b.tol2 = h->opt.tol * h->opt.tol;
+    b.maxit = h->opt.maxit;
+    b.use_au = use_au ? 1 : 0;
+    B.hb32[i] = b;
+    B.hb32[i].sc = h->sc32;
+    B.hb32[i].tol2 = h->opt.inner_tol * h->opt.inner_tol;
+    B.hb32[i].use_au = 0;
+  }
+  CKH(h0, cudaEventRecord(h0->ev0, st));
+  CKH(h0, cudaMemcpyAsync(B.begin64, B.hb64.data(), n * sizeof(BeginJob), cudaMemcpyHostToDevice, st));
+  CKH(h0, cudaMemcpyAsync(B.begin32, B.hb32.data(), n * sizeof(BeginJob), cudaMemcpyHostToDevice, st));
+  launch_begin_batch(B.begin64, n, st);
+  launch_begin_batch(B.begin32, n, st);
+  const Plan<double>& P0 = h0->P64;
+  const Plan<float>& F0 = h0->P32;
+  launch_predict(P0, st, &B.bl64);
+  launch_fin_batch(B.fin[FJ_REF], n, FIN_REF, st);
+  const int watchdog = h0->opt.watchdog_iters > 0 ? h0->opt.watchdog_iters : 4 * h0->opt.maxit;
+  std::vector<int> iters(n, 0), outer(n, 0), sweeps(n, 0);
+  int status_all = WFFT_OK;
+  bool last_resid_on_x = false;
+  if (!mixed) {
+    launch_apply<double>(P0, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, st, &B.bl64);
+    launch_fin_batch(B.fin[FJ_RES0], n, FIN_RES0, st);
+    launch_precond<double>(P0, PRE_PLAIN, SL_R, SL_Z, 1, st, &B.bl64);
+    launch_fin_batch(B.fin[FJ_RZ0], n, FIN_RZ0, st);
+    int rc = batch_pcg<double>(B, B.bl64, P0, 0, FJ_ALPHA, FJ_BETA, watchdog, h0->opt.check_every, st);
+    if (rc == WFFT_ETIMEOUT) status_all = WFFT_ETIMEOUT;
+    else if (rc) return fail(h0, rc, "batch solve failed");
+    for (int i = 0; i < n; ++i) {
+      iters[i] = B.host[i].iter;
+      outer[i] = 1;
+    }
+  } else {
+    bool stored = use_au;
+    int sweep = 0, total_inner = 0;
+    std::vector<char> active(n, 1);
+    for (;;) {
+      if (stored) {
+        launch_fin_batch(B.fin[FJ_OUTER_STORED], n, FIN_OUTER, st);
+      } else {
+        launch_apply<double>(P0, sweep > 0 ? PRE_XUPD : PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, st, &B.bl64);
+        launch_fin_batch(B.fin[FJ_OUTER_RESID], n, FIN_OUTER, st);
+        for (int i = 0; i < n; ++i) outer[i] += active[i];
+      }
+      last_resid_on_x = !stored;
+      stored = false;
+      if (cudaGetLastError() != cudaSuccess || batch_read(B, st)) return fail(h0, WFFT_ECUDA, "batch solve failed");
+      for (int i = 0; i < n; ++i) active[i] = !B.host[i].done;
+      if (all_done(B, 0)) break;
+      if (sweep >= h0->opt.max_sweeps) {
+        status_all = WFFT_ENOTCONV;
+        break;
+      }
+      if (total_inner >= watchdog) {
+        status_all = WFFT_ETIMEOUT;
+        break;
+      }
+      ++sweep;
+      for (int i = 0; i < n; ++i) sweeps[i] += active[i];
+      launch_precond<float>(F0, PRE_CONV, SL_R, SL_Z, 1, st, &B.bl32);
+      launch_fin_batch(B.fin[FJ_RZ0_32], n, FIN_RZ0, st);
+      int rc = batch_pcg<float>(B, B.bl32, F0, 1, FJ_ALPHA_32, FJ_BETA_32, std::max(1, watchdog - total_inner),
+                                h0->opt.check_every, st);
+      int mx = 0;
+      for (int i = 0; i < n; ++i)
+        if (active[i]) {
+          iters[i] += B.host[n + i].iter;
+          mx = std::max(mx, B.host[n + i].iter);
+        }
+      total_inner += mx;
+      if (rc == WFFT_ETIMEOUT) {
+        status_all = WFFT_ETIMEOUT;
+        break;
+      }
+      if (rc) return fail(h0, rc, "batch solve failed");
+    }
+  }
+  // instances that did not finish fail (not committed); the corrector skips them
+  std::vector<char> closed(n, 0);
+  for (int i = 0; i < n; ++i) closed[i] = !B.host[i].done;
+  launch_fin_batch(B.fin[FJ_REF], n, FIN_CLOSE, st);
+  launch_correct(P0, st, &B.bl64);
+  launch_fin_batch(B.fin[FJ_REACT], n, FIN_REACT, st);
+  CKH(h0, cudaEventRecord(h0->ev1, st));
+  if (batch_read(B, st)) return fail(h0, WFFT_ECUDA, "batch solve failed");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h0->ev0, h0->ev1);
   int first = WFFT_OK;
   for (int i = 0; i < n; ++i) {
-    int rc = wfft_step(hs[i], U + 3 * i, infos ? &infos[i] : nullptr);
-    if (rc && !first) first = rc;
+    wfft_handle* h = hs[i];
+    const Scalars& s64 = B.host[i];
+    int st_i = s64.status;
+    if (closed[i] && status_all != WFFT_OK) st_i = status_all;
+    if (st_i == WFFT_OK) {
+      ++h->nstep;
+      for (int k = 0; k < 3; ++k) h->U_prev[k] = B.hb64[i].U[k];
+    }
+    h->au_valid = st_i == WFFT_OK && mixed && last_resid_on_x && !s64.zero_free;
+    if (infos) {
+      wfft_step_info& in = infos[i];
+      memset(&in, 0, sizeof(in));
+      in.status = st_i;
+      in.iters = iters[i];
+      in.outer_applies = outer[i];
+      in.sweeps = sweeps[i];
+      in.ref = std::sqrt(s64.ref2);
+      in.rel_res = s64.ref2 > 0 ? std::sqrt(s64.rr / s64.ref2) : 0.0;
+      for (int k = 0; k < 3; ++k) in.reaction[k] = st_i == WFFT_OK ? s64.react[k] : 0.0;
+      in.ms = ms;
+    }
+    if (st_i != WFFT_OK && !first) first = st_i;
   }
   return first;
 }

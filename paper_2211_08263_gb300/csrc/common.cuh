@@ -69,6 +69,7 @@ template <typename T>
 struct Desc {
   int ndim, c, s;          // dimensions, displacement and strain components
   int n1, n2, n3, nh, pitch;
+  int lx, lxm;             // spatial x lines per block of the c- / s-component x passes
   int opAxis;              // 1 or 2: column axis hosting the spectral multiply
   int midAxis;             // 0 (none) or 1: column axis transformed plainly before/after
   long long V;             // voxels
@@ -162,6 +163,30 @@ struct DotAcc<float> {
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+
+// Grouped (batched) launch: blocks [start[i], start[i+1]) of the grid work on
+// instance i (descriptor descs[i]); n = 0 means a single-instance launch.
+template <typename T>
+struct BatchArgs {
+  const Desc<T>* const* descs;
+  const int* start;
+  int n;
+};
+
+// Descriptor and instance-local block index of this block.
+template <typename T, int BATCH>
+__device__ __forceinline__ const Desc<T>* pick_ptr(const Desc<T>* dd, const BatchArgs<T>& ba, int& blk) {
+  blk = blockIdx.x;
+  if (!BATCH || ba.n == 0) return dd;
+  int lo = 0, hi = ba.n - 1;  // largest i with start[i] <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(ba.start + mid) <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  blk = blockIdx.x - __ldg(ba.start + lo);
+  return ba.descs[lo];
+}
 
 // Block-wide sum of one double per thread; result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {

@@ -5,11 +5,36 @@
 
 namespace wfft {
 
-enum FinMode { FIN_REF = 0, FIN_RES0, FIN_RZ0, FIN_ALPHA, FIN_BETA, FIN_OUTER, FIN_REACT };
+enum FinMode { FIN_REF = 0, FIN_RES0, FIN_RZ0, FIN_ALPHA, FIN_BETA, FIN_OUTER, FIN_REACT, FIN_CLOSE };
 
 // Grid size cap of the elementwise FP64 kernels (and so a lower bound on the
 // length of every partial-sum array).
 constexpr int kEwBlocks = 1216;
+
+// Per-instance arguments of the grouped finalize / begin kernels.
+struct FinJob {
+  Scalars* sc;
+  const double* pa;
+  int na;
+  const double* pb;
+  int nb;
+  const double* pc;
+  int nc;
+  Scalars* sc2;
+};
+struct BeginJob {
+  Scalars* sc;
+  double U[3];
+  double dU[3];
+  int warm;
+  double tol2;
+  int maxit;
+  int use_au;
+};
+void launch_fin_batch(const FinJob* jobs, int n, int mode, cudaStream_t st);
+// Copy the scalars of n solves (src[i]) into one contiguous array (for one read-back).
+void launch_gather_scalars(Scalars* const* src, Scalars* dst, int n, cudaStream_t st);
+void launch_begin_batch(const BeginJob* jobs, int n, cudaStream_t st);
 
 void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc, int mode,
                 Scalars* sc2, cudaStream_t st);

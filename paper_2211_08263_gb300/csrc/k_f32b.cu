@@ -1,0 +1,7 @@
+// FP32 grouped-launch instantiation of the pass kernels (several instances of
+// uneven sizes per launch).
+#include "passes_impl.cuh"
+
+namespace wfft {
+WFFT_INSTANTIATE_BATCH(float)
+}  // namespace wfft

@@ -15,8 +15,19 @@ WFFT_INSTANTIATE(double)
 //   u~ = u + dt v + dt^2 (1/2 - beta) a,  b = rho u~,
 //   x0 = warm start with x0 = U(t_n) on the prescribed DOFs,
 //   partial sums of || P b - sum_j U_j w_j ||^2 (w_j = P A(E e_j)).
-__global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict__ dd) {
-  const Desc<double>& D = *dd;
+// Blocks of an instance for its elementwise kernels (same rule as geo_blocks).
+__device__ __forceinline__ int ew_blocks_dev(const Desc<double>& D) {
+  const long long tot = (long long)D.c * D.V;
+  long long nb = (tot + 255) / 256;
+  if (nb > kEwBlocks) nb = kEwBlocks;
+  return (int)(nb < 1 ? 1 : nb);
+}
+
+__global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict__ dd, BatchArgs<double> ba) {
+  int blk;
+  const Desc<double>* __restrict__ Dp = pick_ptr<double, 1>(dd, ba, blk);
+  const Desc<double>& D = *Dp;
+  const int nblk = ew_blocks_dev(D);
   const Scalars* sc = D.sc;
   const long long V = D.V;
   const int c = D.c, nd = D.ndim;
@@ -34,8 +45,7 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
   double* r64 = reinterpret_cast<double*>(D.slot[SL_R64]);
   double acc = 0.0, accr = 0.0;
   const long long tot = (long long)c * V;
-  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
-       gi += (long long)gridDim.x * blockDim.x) {
+  for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
     const int k = (int)(gi / V);
     const long long vox = gi - (long long)k * V;
     const double uu = u[gi], vv = v[gi], aa = a[gi];
@@ -72,17 +82,20 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
     }
   }
   const double s = block_sum(acc);
-  if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+  if (threadIdx.x == 0) D.part[PT_A][blk] = s;
   if (use_au) {
     const double sr = block_sum(accr);
-    if (threadIdx.x == 0) D.part[PT_B][blockIdx.x] = sr;
+    if (threadIdx.x == 0) D.part[PT_B][blk] = sr;
   }
 }
 
 // Corrector (Eq. Newmark): a_n = (u_n - u~)/(beta dt^2), v_n = v + dt((1-gamma) a + gamma a_n);
 // partial sums of rho a_n per component (total force on the prescribed region).
-__global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict__ dd) {
-  const Desc<double>& D = *dd;
+__global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict__ dd, BatchArgs<double> ba) {
+  int blk;
+  const Desc<double>* __restrict__ Dp = pick_ptr<double, 1>(dd, ba, blk);
+  const Desc<double>& D = *Dp;
+  const int nblk = ew_blocks_dev(D);
   const Scalars* sc = D.sc;
   if (sc->status != 0) return;
   const long long V = D.V;
@@ -96,8 +109,7 @@ __global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict_
   const bool zf = sc->zero_free != 0;
   double acc[3] = {0.0, 0.0, 0.0};
   const long long tot = (long long)c * V;
-  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
-       gi += (long long)gridDim.x * blockDim.x) {
+  for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
     const int k = (int)(gi / V);
     const long long vox = gi - (long long)k * V;
     const double uu = u[gi], vv = v[gi], aa = a[gi];
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict_
   }
   for (int k = 0; k < 3; ++k) {
     const double s = block_sum(acc[k]);
-    if (threadIdx.x == 0) D.part[k][blockIdx.x] = s;
+    if (threadIdx.x == 0) D.part[k][blk] = s;
   }
 }
 
@@ -140,14 +152,32 @@ static int ew_blocks(const Plan<double>& P) {
   return (int)(nb < 1 ? 1 : nb);
 }
 
-void launch_predict(const Plan<double>& P, cudaStream_t st) {
-  const double cv = (double)P.h.c * P.h.V, mat = (P.h.phase ? 3.0 : 1.0) * P.h.V;
-  prof_launch(0, KK_NEWMARK, 8 * cv * (3 + P.h.ndim + 2) + mat, cv * (8 + 2 * P.h.ndim), st,
-              [&] { k_predict<<<ew_blocks(P), 256, 0, st>>>(P.d); });
+static BatchArgs<double> ew_args(const BatchLaunch<double>* bl) {
+  BatchArgs<double> a;
+  a.descs = bl ? bl->descs : nullptr;
+  a.start = bl ? bl->start[GEO_EW] : nullptr;
+  a.n = bl ? bl->n : 0;
+  return a;
 }
-void launch_correct(const Plan<double>& P, cudaStream_t st) {
-  const double cv = (double)P.h.c * P.h.V, mat = (P.h.phase ? 3.0 : 1.0) * P.h.V;
-  prof_launch(0, KK_NEWMARK, 8 * cv * 7 + mat, cv * 14, st, [&] { k_correct<<<ew_blocks(P), 256, 0, st>>>(P.d); });
+static double ew_cv(const Plan<double>& P, const BatchLaunch<double>* bl) {
+  if (!bl) return (double)P.h.c * P.h.V;
+  double s = 0;
+  for (const Plan<double>* q : bl->plans) s += (double)q->h.c * q->h.V;
+  return s;
+}
+
+void launch_predict(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl) {
+  const double cv = ew_cv(P, bl), mat = 3.0 * cv / P.h.c;
+  const int nb = bl ? bl->total[GEO_EW] : ew_blocks(P);
+  const BatchArgs<double> ba = ew_args(bl);
+  prof_launch(0, KK_NEWMARK, 8 * cv * (3 + P.h.ndim + 2) + mat, cv * (8 + 2 * P.h.ndim), st,
+              [&] { k_predict<<<nb, 256, 0, st>>>(P.d, ba); });
+}
+void launch_correct(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl) {
+  const double cv = ew_cv(P, bl), mat = 3.0 * cv / P.h.c;
+  const int nb = bl ? bl->total[GEO_EW] : ew_blocks(P);
+  const BatchArgs<double> ba = ew_args(bl);
+  prof_launch(0, KK_NEWMARK, 8 * cv * 7 + mat, cv * 14, st, [&] { k_correct<<<nb, 256, 0, st>>>(P.d, ba); });
 }
 void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st) {
   prof_launch(0, KK_SCALAR, 8.0 * P.h.c * P.h.V, 0.0, st, [&] { k_fill_unit<<<ew_blocks(P), 256, 0, st>>>(P.d, j, dst); });
@@ -163,12 +193,19 @@ __device__ double fixed_order_sum(const double* p, int n) {
   return block_sum(s);
 }
 
-__global__ void k_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc,
-                      int mode, Scalars* sc2) {
+__device__ void fin_body(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc,
+                         int mode, Scalars* sc2) {
   const double sa = pa ? fixed_order_sum(pa, na) : 0.0;
   const double sb = pb ? fixed_order_sum(pb, nb) : 0.0;
   const double scc = pc ? fixed_order_sum(pc, nc) : 0.0;
   if (threadIdx.x != 0) return;
+  if (mode == FIN_CLOSE) {  // a grouped solve ended on a host limit: unfinished instances fail
+    if (!sc->done) {
+      sc->status = 4;
+      sc->done = 1;
+    }
+    return;
+  }
   // a finished solve is frozen: only the setup / bookkeeping modes still run
   if (sc->done && mode != FIN_REF && mode != FIN_REACT) return;
   switch (mode) {
@@ -265,6 +302,17 @@ __global__ void k_fin(Scalars* sc, const double* pa, int na, const double* pb, i
   }
 }
 
+__global__ void k_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc,
+                      int mode, Scalars* sc2) {
+  fin_body(sc, pa, na, pb, nb, pc, nc, mode, sc2);
+}
+
+// One block per instance of a grouped solve.
+__global__ void k_fin_batch(const FinJob* jobs, int mode) {
+  const FinJob& j = jobs[blockIdx.x];
+  fin_body(j.sc, j.pa, j.na, j.pb, j.nb, j.pc, j.nc, mode, j.sc2);
+}
+
 __global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, double tol2, int maxit, int use_au,
                         double d0, double d1, double d2) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -292,6 +340,33 @@ __global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, 
   sc->dU[2] = d2;
 }
 
+__global__ void k_begin_batch(const BeginJob* jobs, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const BeginJob& j = jobs[i];
+  Scalars* sc = j.sc;
+  for (int k = 0; k < 3; ++k) {
+    sc->Ug[k] = j.U[k];
+    sc->dU[k] = j.dU[k];
+  }
+  sc->warm = j.warm;
+  sc->tol2 = j.tol2;
+  sc->maxit = j.maxit;
+  sc->done = 0;
+  sc->status = 0;
+  sc->iter = 0;
+  sc->first = 1;
+  sc->zero_free = 0;
+  sc->converged = 0;
+  sc->scale = 1.0;
+  sc->xcoef = 1.0;
+  sc->rr = 0.0;
+  sc->rz = 0.0;
+  sc->alpha = 0.0;
+  sc->beta = 0.0;
+  sc->use_au = j.use_au;
+}
+
 __global__ void k_set_done(Scalars* sc, int done) {
   if (threadIdx.x == 0 && blockIdx.x == 0) sc->done = done;
 }
@@ -307,6 +382,24 @@ void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int max
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st,
               [&] { k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit, use_au, d0, d1, d2); });
 }
+void launch_fin_batch(const FinJob* jobs, int n, int mode, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_fin_batch<<<n, 256, 0, st>>>(jobs, mode); });
+}
+void launch_begin_batch(const BeginJob* jobs, int n, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_begin_batch<<<(n + 63) / 64, 64, 0, st>>>(jobs, n); });
+}
+
+__global__ void k_gather_scalars(Scalars* const* src, Scalars* dst, int n) {
+  const int words = (int)(sizeof(Scalars) / sizeof(int));
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * words; t += gridDim.x * blockDim.x) {
+    const int i = t / words, w = t - i * words;
+    reinterpret_cast<int*>(dst + i)[w] = reinterpret_cast<const int*>(src[i])[w];
+  }
+}
+void launch_gather_scalars(Scalars* const* src, Scalars* dst, int n, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_gather_scalars<<<8, 256, 0, st>>>(src, dst, n); });
+}
+
 void launch_set_done(Scalars* sc, int done, cudaStream_t st) {
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_set_done<<<1, 32, 0, st>>>(sc, done); });
 }

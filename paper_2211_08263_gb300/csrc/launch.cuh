@@ -27,19 +27,61 @@ struct Plan {
   PassGeo g;
 };
 
+// Geometry classes of the passes (one block count per instance each).
+enum GeoClass { GEO_X = 0, GEO_XM = 1, GEO_COL0 = 2, GEO_EW = GEO_COL0 + 10, NGEO };
+inline int geo_col(int axis, int op) { return GEO_COL0 + (axis - 1) * 5 + op; }
+
+// A grouped launch over several instances of the same structure (ndim, pass
+// sequence): device array of descriptors, per-class block prefix sums, the
+// common column-tile width and the largest shared memory per class.
+template <typename T>
+struct BatchLaunch {
+  int n = 0;
+  const Desc<T>* const* descs = nullptr;  // device
+  const int* start[NGEO] = {};            // device, n + 1 entries each
+  int total[NGEO] = {};
+  size_t sm[NGEO] = {};
+  int bx[3][5] = {};
+  std::vector<const Plan<T>*> plans;
+};
+
 // Compute tile geometry from h's sizes (elements budget per block).
 template <typename T>
 void plan_geometry(Plan<T>& P);
 
 // q(out_slot) = [P] A in, where `pre` selects the fused x-pass prologue
 // (PRE_PLAIN reads in_slot) and `post` the epilogue (POST_APPLY / POST_RESID).
+// B = 1: grouped launch over the instances of `bl` (P is any one of them).
+template <typename T, int B>
+void launch_apply_impl(const Plan<T>& P, int pre, int in_slot, int post, int out_slot, int masked, int want_dot,
+                       cudaStream_t st, const BatchLaunch<T>* bl);
 template <typename T>
-void launch_apply(const Plan<T>& P, int pre, int in_slot, int post, int out_slot, int masked, int want_dot,
-                  cudaStream_t st);
+inline void launch_apply(const Plan<T>& P, int pre, int in_slot, int post, int out_slot, int masked, int want_dot,
+                         cudaStream_t st, const BatchLaunch<T>* bl = nullptr) {
+  if (bl)
+    launch_apply_impl<T, 1>(P, pre, in_slot, post, out_slot, masked, want_dot, st, bl);
+  else
+    launch_apply_impl<T, 0>(P, pre, in_slot, post, out_slot, masked, want_dot, st, nullptr);
+}
 
 // z(out_slot) = [P] M r, prologue `pre` (PRE_PLAIN reads in_slot, PRE_RUPD, PRE_CONV).
+template <typename T, int B>
+void launch_precond_impl(const Plan<T>& P, int pre, int in_slot, int out_slot, int masked, cudaStream_t st,
+                         const BatchLaunch<T>* bl);
 template <typename T>
-void launch_precond(const Plan<T>& P, int pre, int in_slot, int out_slot, int masked, cudaStream_t st);
+inline void launch_precond(const Plan<T>& P, int pre, int in_slot, int out_slot, int masked, cudaStream_t st,
+                           const BatchLaunch<T>* bl = nullptr) {
+  if (bl)
+    launch_precond_impl<T, 1>(P, pre, in_slot, out_slot, masked, st, bl);
+  else
+    launch_precond_impl<T, 0>(P, pre, in_slot, out_slot, masked, st, nullptr);
+}
+
+// Block count of an instance for a geometry class at a given column-tile width.
+template <typename T>
+int geo_blocks(const Plan<T>& P, int cls, int bx);
+template <typename T>
+size_t geo_smem(const Plan<T>& P, int cls, int bx);
 
 // Plain forward (dir -1) or inverse (dir +1) 3-D real FFT of ncomp components between
 // a real slot and the spectral buffer (testing entry point).
@@ -47,12 +89,18 @@ template <typename T>
 void launch_rfft3(const Plan<T>& P, int dir, int ncomp, int real_slot, cudaStream_t st);
 
 // Set the max dynamic shared memory attribute of every kernel (once per process).
+template <typename T, int B>
+cudaError_t init_kernel_attributes_impl();
 template <typename T>
-cudaError_t init_kernel_attributes();
+inline cudaError_t init_kernel_attributes() {
+  cudaError_t e = init_kernel_attributes_impl<T, 0>();
+  if (e == cudaSuccess) e = init_kernel_attributes_impl<T, 1>();
+  return e;
+}
 
 // FP64 elementwise kernels of the Newmark step (k_f64.cu).
-void launch_predict(const Plan<double>& P, cudaStream_t st);
-void launch_correct(const Plan<double>& P, cudaStream_t st);
+void launch_predict(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl = nullptr);
+void launch_correct(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl = nullptr);
 void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st);
 
 }  // namespace wfft

@@ -120,9 +120,12 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const cplx<T>* src, i
 //   PRE_XUPD   x += xcoef * d (FP64 descriptor of a mixed solve: folds the
 //              finished inner correction into the FP64 solution) and transform x
 // ---------------------------------------------------------------------------
-template <typename T, int PRE>
-__global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, int LX, int in_slot) {
-  const Desc<T>& D = *dd;
+template <typename T, int PRE, int BATCH>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int in_slot) {
+  int blk;
+  const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
+  const Desc<T>& D = *Dp;
+  const int LX = D.lx;
   Scalars* sc = D.sc;
   if (sc->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, in
   cplx<T>* buf = tw + N;
   const int lstr = N;
   const long long nsp = (long long)D.n2 * D.n3;
-  const long long l0 = (long long)blockIdx.x * LX;
+  const long long l0 = (long long)blk * LX;
   const long long V = D.V;
   load_twiddles<T>(tw, D.tw[0], N);
   bool first = false;
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, in
   }
   if (PRE == PRE_RUPD) {
     const double s = block_sum(acc.value());
-    if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+    if (threadIdx.x == 0) D.part[PT_A][blk] = s;
   }
   __syncthreads();
   fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, lstr, tw, -1);
@@ -232,10 +235,13 @@ __global__ void __launch_bounds__(256) k_xfwd(const Desc<T>* __restrict__ dd, in
 //   POST_RESID  A x = t + rho x (kept when the slot exists), r = P(b - A x), ||r||^2
 //   POST_PREC   z = P(t)
 // ---------------------------------------------------------------------------
-template <typename T, int POST>
-__global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, int LX, int in_slot, int out_slot,
-                                              int masked, int want_dot) {
-  const Desc<T>& D = *dd;
+template <typename T, int POST, int BATCH>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int in_slot,
+                                              int out_slot, int masked, int want_dot) {
+  int blk;
+  const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
+  const Desc<T>& D = *Dp;
+  const int LX = D.lx;
   Scalars* sc = D.sc;
   if (sc->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, in
   cplx<T>* buf = tw + N;
   const int lstr = N;
   const long long nsp = (long long)D.n2 * D.n3;
-  const long long l0 = (long long)blockIdx.x * LX;
+  const long long l0 = (long long)blk * LX;
   const long long V = D.V;
   load_twiddles<T>(tw, D.tw[0], N);
   load_packed<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(256) k_xinv(const Desc<T>* __restrict__ dd, in
   }
   if (POST != POST_PREC && want_dot) {
     const double s = block_sum(acc.value());
-    if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+    if (threadIdx.x == 0) D.part[PT_A][blk] = s;
   }
 }
 
@@ -332,9 +338,30 @@ __device__ __forceinline__ void hooke2(const T* __restrict__ C, T* e) {
   e[2] = C[2] * e0 + C[4] * e1 + C[5] * e2;
 }
 
+// One padded stiffness row (24 or 8 values, 16-byte aligned) with vector loads.
 template <typename T>
-__global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, int LX) {
-  const Desc<T>& D = *dd;
+__device__ __forceinline__ void load_row(const T* __restrict__ src, T* dst, int n) {
+  if (sizeof(T) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      if (4 * i < n) d4[i] = __ldg(s4 + i);
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+      if (2 * i < n) d2[i] = __ldg(s2 + i);
+  }
+}
+
+template <typename T, int BATCH>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc<T>* __restrict__ dd, BatchArgs<T> ba) {
+  int blk;
+  const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
+  const Desc<T>& D = *Dp;
+  const int LX = D.lxm;
   if (D.sc->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = D.n1, ns = D.s;
@@ -342,7 +369,7 @@ __global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, in
   cplx<T>* buf = tw + N;
   const int lstr = N;
   const long long nsp = (long long)D.n2 * D.n3;
-  const long long l0 = (long long)blockIdx.x * LX;
+  const long long l0 = (long long)blk * LX;
   load_twiddles<T>(tw, D.tw[0], N);
   load_packed<T>(D, buf, lstr, LX * ns, l0, ns, nsp);
   __syncthreads();
@@ -354,7 +381,8 @@ __global__ void __launch_bounds__(256) k_xmid(const Desc<T>* __restrict__ dd, in
     for (int x = lane_id(); x < N; x += 32) {
       const long long vox = line * N + x;
       const long long row = D.phase ? (long long)D.phase[vox] : vox;
-      const T* C = D.ctab + row * cstride;
+      T C[24];
+      load_row<T>(D.ctab + row * cstride, C, ns == 6 ? 24 : 8);
       T ev[6];
       if (ns == 6) {
 #pragma unroll
@@ -396,11 +424,11 @@ struct ColGeo {
 };
 
 template <typename T>
-__device__ __forceinline__ ColGeo<T> col_geo(const Desc<T>& D, int axis, int BX) {
+__device__ __forceinline__ ColGeo<T> col_geo(const Desc<T>& D, int axis, int BX, int blk) {
   ColGeo<T> g;
   const int ntx = (D.nh + BX - 1) / BX;
-  const int tile = blockIdx.x % ntx;
-  const int o = blockIdx.x / ntx;
+  const int tile = blk % ntx;
+  const int o = blk / ntx;
   g.kx0 = tile * BX;
   g.outer = o;
   if (axis == 1) {
@@ -440,6 +468,32 @@ __device__ __forceinline__ void col_load(const Desc<T>& D, const ColGeo<T>& g, i
   }
 }
 
+// Components 0..NC-1 into slots 0..NC-1 in one batched loop (more loads in flight).
+template <typename T, int BX, int ES, int NC>
+__device__ __forceinline__ void col_load_all(const Desc<T>& D, const ColGeo<T>& g, cplx<T>* tl) {
+  const int per = g.N * BX;
+  const int tot = NC * per;
+  const int nthr = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += nthr * kLoadBatch) {
+    cplx<T> v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * nthr;
+      const int comp = e / per, r = e - comp * per;
+      const int y = r / BX, b = r % BX;
+      v[u] = (e < tot && g.kx0 + b < D.nh) ? D.spec[(long long)comp * D.Vh + g.base + (long long)y * g.est + b]
+                                            : cmake<T>(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = e0 + u * nthr;
+      const int comp = e / per, r = e - comp * per;
+      const int y = r / BX, b = r % BX;
+      if (e < tot) tl[y * ES + comp * BX + b] = v[u];
+    }
+  }
+}
+
 template <typename T, int BX, int ES>
 __device__ __forceinline__ void col_store(const Desc<T>& D, const ColGeo<T>& g, int comp, const cplx<T>* tl,
                                           int slot) {
@@ -465,12 +519,15 @@ __device__ __forceinline__ void col_xi(const Desc<T>& D, const ColGeo<T>& g, int
 }
 
 // Plain transform of one component (blockIdx.y) along `axis`.
-template <typename T, int OP, int BX>
-__global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4) k_colplain(const Desc<T>* __restrict__ dd, int axis) {
-  const Desc<T>& D = *dd;
+template <typename T, int OP, int BX, int BATCH>
+__global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4)
+    k_colplain(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int axis) {
+  int blk;
+  const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
+  const Desc<T>& D = *Dp;
   if (D.sc->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const ColGeo<T> g = col_geo<T>(D, axis, BX);
+  const ColGeo<T> g = col_geo<T>(D, axis, BX, blk);
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* tl = tw + g.N;
   load_twiddles<T>(tw, D.tw[axis], g.N);
@@ -487,14 +544,17 @@ __global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4) k_co
 //   OP_DIV : s stresses sig^ -> c tractions t^ = (-theta/V) i B(xi)^T sig^
 //   OP_PREC: c residuals r^ -> z^ = (1/V) (theta K(xi) + rho_bar I)^-1 r^, with the
 //            Parseval partial sum of (r, z) over the half spectrum
-template <typename T, int OP, int BX, int NS>
-__global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop(const Desc<T>* __restrict__ dd, int axis) {
+template <typename T, int OP, int BX, int NS, int BATCH>
+__global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3)
+    k_colop(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int axis) {
   constexpr int ES = NS * BX;
-  const Desc<T>& D = *dd;
+  int blk;
+  const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
+  const Desc<T>& D = *Dp;
   Scalars* sc = D.sc;
   if (sc->done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const ColGeo<T> g = col_geo<T>(D, axis, BX);
+  const ColGeo<T> g = col_geo<T>(D, axis, BX, blk);
   const int N = g.N;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* tl = tw + N;
@@ -506,7 +566,7 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
   constexpr int kS = (OP == OP_PREC) ? 0 : NS;
   constexpr int NIN = (OP == OP_DIV) ? kS : kC;
   constexpr int NOUT = (OP == OP_GRAD) ? kS : kC;
-  for (int k = 0; k < NIN; ++k) col_load<T, BX, ES>(D, g, k, tl, k);
+  col_load_all<T, BX, ES, NIN>(D, g, tl);
   __syncthreads();
   fft_lines<T, ES, NIN * BX>(tl, pl, NIN * BX, 1, tw, -1);
   DotAcc<T> acc;
@@ -598,7 +658,7 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3) k_colop
   }
   if (OP == OP_PREC) {
     const double s = block_sum(acc.value());  // contains barriers
-    if (threadIdx.x == 0) D.part[PT_B][blockIdx.x] = s;
+    if (threadIdx.x == 0) D.part[PT_B][blk] = s;
   }
   __syncthreads();
   fft_lines<T, ES, NOUT * BX>(tl, pl, NOUT * BX, 1, tw, +1);

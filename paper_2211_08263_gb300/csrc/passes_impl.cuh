@@ -27,7 +27,7 @@ static int max_tile_elems(const AxisPlan& pl, int thr) {
 
 template <typename T>
 void plan_geometry(Plan<T>& P) {
-  const Desc<T>& D = P.h;
+  Desc<T>& D = P.h;
   PassGeo& g = P.g;
   g.thr = 256;
   const int budget = 2048;  // target complex elements per block tile
@@ -43,6 +43,8 @@ void plan_geometry(Plan<T>& P) {
   };
   g.LX = pick_lx(D.c);
   g.LXm = pick_lx(D.s);
+  P.h.lx = g.LX;
+  P.h.lxm = g.LXm;
   g.blk_x = (int)((nsp + g.LX - 1) / g.LX);
   g.blk_xm = (int)((nsp + g.LXm - 1) / g.LXm);
   const size_t cs = sizeof(cplx<T>);
@@ -101,167 +103,293 @@ struct Cost {
 };
 static inline int prec_index(size_t st) { return st == 8 ? 0 : 1; }
 
+// ---------------------------------------------------------------------------
+// launch helpers: one code path for single-instance and grouped launches
+// ---------------------------------------------------------------------------
 template <typename T>
-static void launch_xfwd(const Plan<T>& P, int pre, int in_slot, cudaStream_t st) {
-  const PassGeo& g = P.g;
-  const Cost<T> k(P.h);
+int geo_blocks(const Plan<T>& P, int cls, int bx) {
+  const Desc<T>& D = P.h;
+  if (cls == GEO_X) return P.g.blk_x;
+  if (cls == GEO_XM) return P.g.blk_xm;
+  if (cls == GEO_EW) {
+    const long long tot = (long long)D.c * D.V;
+    return (int)std::min<long long>(std::max<long long>((tot + 255) / 256, 1), 1216);
+  }
+  const int axis = (cls - GEO_COL0) / 5 + 1;
+  const int nouter = axis == 1 ? D.n3 : D.n2;
+  return ((D.nh + bx - 1) / bx) * nouter;
+}
+
+template <typename T>
+size_t geo_smem(const Plan<T>& P, int cls, int bx) {
+  const Desc<T>& D = P.h;
+  const size_t cs = sizeof(cplx<T>);
+  if (cls == GEO_X) return P.g.sm_x;
+  if (cls == GEO_XM) return P.g.sm_xm;
+  if (cls == GEO_EW) return 0;
+  const int axis = (cls - GEO_COL0) / 5 + 1, op = (cls - GEO_COL0) % 5;
+  const int N = axis == 1 ? D.n2 : D.n3;
+  const bool plain = op == OP_FWD || op == OP_INV;
+  const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
+  return (size_t)(N + ns * bx * N) * cs;
+}
+
+template <typename T, int B>
+struct Launch {
+  const Plan<T>& P;
+  const BatchLaunch<T>* bl;
+  int grid(int cls) const {
+    if (bl) return bl->total[cls];
+    if (cls == GEO_X) return P.g.blk_x;
+    if (cls == GEO_XM) return P.g.blk_xm;
+    const int axis = (cls - GEO_COL0) / 5 + 1, op = (cls - GEO_COL0) % 5;
+    return P.g.blk_col[axis][op];
+  }
+  size_t smem(int cls) const {
+    if (bl) return bl->sm[cls];
+    if (cls == GEO_X) return P.g.sm_x;
+    if (cls == GEO_XM) return P.g.sm_xm;
+    const int axis = (cls - GEO_COL0) / 5 + 1, op = (cls - GEO_COL0) % 5;
+    return P.g.sm_col[axis][op];
+  }
+  int bx(int axis, int op) const { return bl ? bl->bx[axis][op] : P.g.bx[axis][op]; }
+  BatchArgs<T> args(int cls) const {
+    BatchArgs<T> a;
+    a.descs = bl ? bl->descs : nullptr;
+    a.start = bl ? bl->start[cls] : nullptr;
+    a.n = bl ? bl->n : 0;
+    return a;
+  }
+  // summed cost model over the instances of the launch
+  template <typename F>
+  void cost(F&& f, double& bytes, double& flops) const {
+    bytes = flops = 0.0;
+    if (!bl) {
+      f(P, bytes, flops);
+      return;
+    }
+    for (const Plan<T>* q : bl->plans) {
+      double b = 0, fl = 0;
+      f(*q, b, fl);
+      bytes += b;
+      flops += fl;
+    }
+  }
+};
+
+template <typename T, int B>
+static void launch_xfwd(const Launch<T, B>& L, int pre, int in_slot, cudaStream_t st) {
   const int pi = prec_index(sizeof(T));
-  const double out = k.spec(k.c), fl = k.xfft(k.c);
+  const int nb = L.grid(GEO_X);
+  const size_t sm = L.smem(GEO_X);
+  const BatchArgs<T> ba = L.args(GEO_X);
+  const Desc<T>* d = L.P.d;
+  double by, fl;
+  L.cost(
+      [&](const Plan<T>& Q, double& b, double& f) {
+        const Cost<T> k(Q.h);
+        const double out = k.spec(k.c);
+        f = k.xfft(k.c);
+        switch (pre) {
+          case PRE_PLAIN: b = k.real(k.c) + out; break;
+          case PRE_PUPD: b = 3 * k.real(k.c) + out; f += 2 * k.c * k.V; break;
+          case PRE_RUPD: b = 6 * k.real(k.c) + out; f += 6 * k.c * k.V; break;
+          case PRE_CONV: b = 8 * k.c * k.V + 2 * k.real(k.c) + out; f += k.c * k.V; break;
+          default: b = 2 * k.real(k.c) + 4 * k.c * k.V + out; f += 2 * k.c * k.V; break;
+        }
+      },
+      by, fl);
   switch (pre) {
     case PRE_PLAIN:
-      prof_launch(pi, KK_XFWD_PLAIN, k.real(k.c) + out, fl, st,
-                  [&] { k_xfwd<T, PRE_PLAIN><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      prof_launch(pi, KK_XFWD_PLAIN, by, fl, st, [&] { k_xfwd<T, PRE_PLAIN, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
     case PRE_PUPD:
-      prof_launch(pi, KK_XFWD_PUPD, 3 * k.real(k.c) + out, fl + 2 * k.c * k.V, st,
-                  [&] { k_xfwd<T, PRE_PUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      prof_launch(pi, KK_XFWD_PUPD, by, fl, st, [&] { k_xfwd<T, PRE_PUPD, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
     case PRE_RUPD:
-      prof_launch(pi, KK_XFWD_RUPD, 6 * k.real(k.c) + out, fl + 6 * k.c * k.V, st,
-                  [&] { k_xfwd<T, PRE_RUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      prof_launch(pi, KK_XFWD_RUPD, by, fl, st, [&] { k_xfwd<T, PRE_RUPD, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
     case PRE_CONV:
-      prof_launch(pi, KK_XFWD_CONV, 8 * k.c * k.V + 2 * k.real(k.c) + out, fl + k.c * k.V, st,
-                  [&] { k_xfwd<T, PRE_CONV><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      prof_launch(pi, KK_XFWD_CONV, by, fl, st, [&] { k_xfwd<T, PRE_CONV, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
     default:  // PRE_XUPD: x += xcoef d (FP64 x, FP32 d), then transform x
-      prof_launch(pi, KK_XFWD_PLAIN, 2 * k.real(k.c) + 4 * k.c * k.V + out, fl + 2 * k.c * k.V, st,
-                  [&] { k_xfwd<T, PRE_XUPD><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot); });
+      prof_launch(pi, KK_XFWD_PLAIN, by, fl, st, [&] { k_xfwd<T, PRE_XUPD, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
   }
 }
 
-template <typename T, int BX>
-static void launch_colplain_bx(const Plan<T>& P, int op, int axis, int ncomp, cudaStream_t st) {
-  const PassGeo& g = P.g;
-  const dim3 grid(g.blk_col[axis][op], ncomp);
-  const size_t sm = g.sm_col[axis][op];
-  const Cost<T> k(P.h);
-  const double by = 2 * k.spec(ncomp), fl = k.colfft(axis, ncomp);
+template <typename T, int BX, int B>
+static void launch_colplain_bx(const Launch<T, B>& L, int op, int axis, int ncomp, cudaStream_t st) {
+  const int cls = geo_col(axis, op);
+  const dim3 grid(L.grid(cls), ncomp);
+  const size_t sm = L.smem(cls);
+  const BatchArgs<T> ba = L.args(cls);
+  const Desc<T>* d = L.P.d;
+  double by, fl;
+  L.cost(
+      [&](const Plan<T>& Q, double& b, double& f) {
+        const Cost<T> k(Q.h);
+        b = 2 * k.spec(ncomp);
+        f = k.colfft(axis, ncomp);
+      },
+      by, fl);
   const int pi = prec_index(sizeof(T));
   if (op == OP_FWD)
     prof_launch(pi, KK_COL_FWD, by, fl, st,
-                [&] { k_colplain<T, OP_FWD, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis); });
+                [&] { k_colplain<T, OP_FWD, BX, B><<<grid, kColThreadsPlain, sm, st>>>(d, ba, axis); });
   else
     prof_launch(pi, KK_COL_INV, by, fl, st,
-                [&] { k_colplain<T, OP_INV, BX><<<grid, kColThreadsPlain, sm, st>>>(P.d, axis); });
+                [&] { k_colplain<T, OP_INV, BX, B><<<grid, kColThreadsPlain, sm, st>>>(d, ba, axis); });
 }
 
-template <typename T, int OP, int BX>
-static void launch_colop_bx(const Plan<T>& P, int axis, cudaStream_t st) {
-  const PassGeo& g = P.g;
-  const int nb = g.blk_col[axis][OP];
-  const size_t sm = g.sm_col[axis][OP];
-  const Cost<T> k(P.h);
-  const bool d3 = P.h.ndim == 3;
+template <typename T, int OP, int BX, int B>
+static void launch_colop_bx(const Launch<T, B>& L, int axis, cudaStream_t st) {
+  const int cls = geo_col(axis, OP);
+  const int nb = L.grid(cls);
+  const size_t sm = L.smem(cls);
+  const BatchArgs<T> ba = L.args(cls);
+  const Desc<T>* d = L.P.d;
+  const bool d3 = L.P.h.ndim == 3;
   double by, fl;
-  int kind;
-  if (OP == OP_GRAD) {
-    kind = KK_COL_GRAD;
-    by = k.spec(k.c) + k.spec(k.s);
-    fl = k.colfft(axis, k.c + k.s) + (d3 ? 42.0 : 20.0) * k.Vh;
-  } else if (OP == OP_DIV) {
-    kind = KK_COL_DIV;
-    by = k.spec(k.s) + k.spec(k.c);
-    fl = k.colfft(axis, k.c + k.s) + (d3 ? 36.0 : 16.0) * k.Vh;
-  } else {
-    kind = KK_COL_PREC;
-    by = 2 * k.spec(k.c);
-    fl = k.colfft(axis, 2 * k.c) + (d3 ? 100.0 : 40.0) * k.Vh;
-  }
+  L.cost(
+      [&](const Plan<T>& Q, double& b, double& f) {
+        const Cost<T> k(Q.h);
+        if (OP == OP_GRAD) {
+          b = k.spec(k.c) + k.spec(k.s);
+          f = k.colfft(axis, k.c + k.s) + (d3 ? 42.0 : 20.0) * k.Vh;
+        } else if (OP == OP_DIV) {
+          b = k.spec(k.s) + k.spec(k.c);
+          f = k.colfft(axis, k.c + k.s) + (d3 ? 36.0 : 16.0) * k.Vh;
+        } else {
+          b = 2 * k.spec(k.c);
+          f = k.colfft(axis, 2 * k.c) + (d3 ? 100.0 : 40.0) * k.Vh;
+        }
+      },
+      by, fl);
+  const int kind = OP == OP_GRAD ? KK_COL_GRAD : (OP == OP_DIV ? KK_COL_DIV : KK_COL_PREC);
   // slots: c (2 or 3) for the preconditioner, s (3 or 6) for gradient / divergence
   constexpr int kSmall = OP == OP_PREC ? 2 : 3;
   constexpr int kLarge = OP == OP_PREC ? 3 : 6;
   prof_launch(prec_index(sizeof(T)), kind, by, fl, st, [&] {
     if (!d3)
-      k_colop<T, OP, BX, kSmall><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
+      k_colop<T, OP, BX, kSmall, B><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);
     else
-      k_colop<T, OP, BX, kLarge><<<nb, kColThreadsOp, sm, st>>>(P.d, axis);
+      k_colop<T, OP, BX, kLarge, B><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);
   });
 }
 
-template <typename T, int OP>
-static void launch_colop(const Plan<T>& P, int axis, cudaStream_t st) {
-  switch (P.g.bx[axis][OP]) {
-    case 4: launch_colop_bx<T, OP, 4>(P, axis, st); break;
-    case 2: launch_colop_bx<T, OP, 2>(P, axis, st); break;
-    default: launch_colop_bx<T, OP, 1>(P, axis, st); break;
+template <typename T, int OP, int B>
+static void launch_colop(const Launch<T, B>& L, int axis, cudaStream_t st) {
+  switch (L.bx(axis, OP)) {
+    case 4: launch_colop_bx<T, OP, 4, B>(L, axis, st); break;
+    case 2: launch_colop_bx<T, OP, 2, B>(L, axis, st); break;
+    default: launch_colop_bx<T, OP, 1, B>(L, axis, st); break;
   }
 }
 
-template <typename T>
-static void launch_col(const Plan<T>& P, int op, int axis, int ncomp, cudaStream_t st) {
+template <typename T, int B>
+static void launch_col(const Launch<T, B>& L, int op, int axis, int ncomp, cudaStream_t st) {
   if (op == OP_FWD || op == OP_INV) {
-    switch (P.g.bx[axis][op]) {
-      case 8: launch_colplain_bx<T, 8>(P, op, axis, ncomp, st); break;
-      case 4: launch_colplain_bx<T, 4>(P, op, axis, ncomp, st); break;
-      case 2: launch_colplain_bx<T, 2>(P, op, axis, ncomp, st); break;
-      default: launch_colplain_bx<T, 1>(P, op, axis, ncomp, st); break;
+    switch (L.bx(axis, op)) {
+      case 8: launch_colplain_bx<T, 8, B>(L, op, axis, ncomp, st); break;
+      case 4: launch_colplain_bx<T, 4, B>(L, op, axis, ncomp, st); break;
+      case 2: launch_colplain_bx<T, 2, B>(L, op, axis, ncomp, st); break;
+      default: launch_colplain_bx<T, 1, B>(L, op, axis, ncomp, st); break;
     }
     return;
   }
-  if (op == OP_GRAD) launch_colop<T, OP_GRAD>(P, axis, st);
-  else if (op == OP_DIV) launch_colop<T, OP_DIV>(P, axis, st);
-  else launch_colop<T, OP_PREC>(P, axis, st);
+  if (op == OP_GRAD) launch_colop<T, OP_GRAD, B>(L, axis, st);
+  else if (op == OP_DIV) launch_colop<T, OP_DIV, B>(L, axis, st);
+  else launch_colop<T, OP_PREC, B>(L, axis, st);
 }
 
-template <typename T>
-static void launch_xinv(const Plan<T>& P, int post, int in_slot, int out_slot, int masked, int want_dot,
+template <typename T, int B>
+static void launch_xinv(const Launch<T, B>& L, int post, int in_slot, int out_slot, int masked, int want_dot,
                         cudaStream_t st) {
-  const PassGeo& g = P.g;
-  const Cost<T> k(P.h);
   const int pi = prec_index(sizeof(T));
-  const double in = k.spec(k.c), fl = k.xfft(k.c);
-  const double mat = (P.h.phase ? 2.0 : 0.0) * k.V + k.V;  // phase ids + mask bytes
+  const int nb = L.grid(GEO_X);
+  const size_t sm = L.smem(GEO_X);
+  const BatchArgs<T> ba = L.args(GEO_X);
+  const Desc<T>* d = L.P.d;
+  double by, fl;
+  L.cost(
+      [&](const Plan<T>& Q, double& b, double& f) {
+        const Cost<T> k(Q.h);
+        const double in = k.spec(k.c), mat = (Q.h.phase ? 2.0 : 0.0) * k.V + k.V;
+        f = k.xfft(k.c);
+        if (post == POST_APPLY) {
+          b = in + 2 * k.real(k.c) + mat;
+          f += 2 * k.c * k.V;
+        } else if (post == POST_RESID) {
+          b = in + 24 * k.c * k.V + mat;
+          f += 3 * k.c * k.V;
+        } else {
+          b = in + k.real(k.c) + k.V;
+        }
+      },
+      by, fl);
   switch (post) {
     case POST_APPLY:
-      prof_launch(pi, KK_XINV_APPLY, in + 2 * k.real(k.c) + mat, fl + 2 * k.c * k.V, st, [&] {
-        k_xinv<T, POST_APPLY><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, want_dot);
+      prof_launch(pi, KK_XINV_APPLY, by, fl, st, [&] {
+        k_xinv<T, POST_APPLY, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, want_dot);
       });
       break;
     case POST_RESID:
-      prof_launch(pi, KK_XINV_RESID, in + 24 * k.c * k.V + mat, fl + 3 * k.c * k.V, st, [&] {
-        k_xinv<T, POST_RESID><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, want_dot);
+      prof_launch(pi, KK_XINV_RESID, by, fl, st, [&] {
+        k_xinv<T, POST_RESID, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, want_dot);
       });
       break;
     default:
-      prof_launch(pi, KK_XINV_PREC, in + k.real(k.c) + k.V, fl, st, [&] {
-        k_xinv<T, POST_PREC><<<g.blk_x, g.thr, g.sm_x, st>>>(P.d, g.LX, in_slot, out_slot, masked, 0);
-      });
+      prof_launch(pi, KK_XINV_PREC, by, fl, st,
+                  [&] { k_xinv<T, POST_PREC, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, 0); });
       break;
   }
 }
 
-template <typename T>
-void launch_apply(const Plan<T>& P, int pre, int in_slot, int post, int out_slot, int masked, int want_dot,
-                  cudaStream_t st) {
-  const Desc<T>& D = P.h;
-  launch_xfwd<T>(P, pre, in_slot, st);
-  if (D.midAxis) launch_col<T>(P, OP_FWD, D.midAxis, D.c, st);
-  launch_col<T>(P, OP_GRAD, D.opAxis, D.c, st);
-  if (D.midAxis) launch_col<T>(P, OP_INV, D.midAxis, D.s, st);
-  {
-    const Cost<T> k(D);
-    const double by = 2 * k.spec(k.s) + (D.phase ? 2.0 : 0.0) * k.V;
-    const double fl = 2 * k.xfft(k.s) + (D.ndim == 3 ? 66.0 : 15.0) * k.V;
-    prof_launch(prec_index(sizeof(T)), KK_XMID, by, fl, st,
-                [&] { k_xmid<T><<<P.g.blk_xm, P.g.thr, P.g.sm_xm, st>>>(P.d, P.g.LXm); });
-  }
-  if (D.midAxis) launch_col<T>(P, OP_FWD, D.midAxis, D.s, st);
-  launch_col<T>(P, OP_DIV, D.opAxis, D.c, st);
-  if (D.midAxis) launch_col<T>(P, OP_INV, D.midAxis, D.c, st);
-  // PRE_PUPD writes p; the epilogue reads the operator's input from in_slot
-  launch_xinv<T>(P, post, pre == PRE_PUPD ? (int)SL_P : in_slot, out_slot, masked, want_dot, st);
+template <typename T, int B>
+static void launch_xmid(const Launch<T, B>& L, cudaStream_t st) {
+  const int nb = L.grid(GEO_XM);
+  const size_t sm = L.smem(GEO_XM);
+  const BatchArgs<T> ba = L.args(GEO_XM);
+  const Desc<T>* d = L.P.d;
+  double by, fl;
+  L.cost(
+      [&](const Plan<T>& Q, double& b, double& f) {
+        const Cost<T> k(Q.h);
+        b = 2 * k.spec(k.s) + (Q.h.phase ? 2.0 : 0.0) * k.V;
+        f = 2 * k.xfft(k.s) + (Q.h.ndim == 3 ? 66.0 : 15.0) * k.V;
+      },
+      by, fl);
+  prof_launch(prec_index(sizeof(T)), KK_XMID, by, fl, st, [&] { k_xmid<T, B><<<nb, 256, sm, st>>>(d, ba); });
 }
 
-template <typename T>
-void launch_precond(const Plan<T>& P, int pre, int in_slot, int out_slot, int masked, cudaStream_t st) {
+template <typename T, int B>
+void launch_apply_impl(const Plan<T>& P, int pre, int in_slot, int post, int out_slot, int masked, int want_dot,
+                       cudaStream_t st, const BatchLaunch<T>* bl) {
   const Desc<T>& D = P.h;
-  launch_xfwd<T>(P, pre, in_slot, st);
-  if (D.midAxis) launch_col<T>(P, OP_FWD, D.midAxis, D.c, st);
-  launch_col<T>(P, OP_PREC, D.opAxis, D.c, st);
-  if (D.midAxis) launch_col<T>(P, OP_INV, D.midAxis, D.c, st);
-  launch_xinv<T>(P, POST_PREC, in_slot, out_slot, masked, 0, st);
+  const Launch<T, B> L{P, bl};
+  launch_xfwd<T, B>(L, pre, in_slot, st);
+  if (D.midAxis) launch_col<T, B>(L, OP_FWD, D.midAxis, D.c, st);
+  launch_col<T, B>(L, OP_GRAD, D.opAxis, D.c, st);
+  if (D.midAxis) launch_col<T, B>(L, OP_INV, D.midAxis, D.s, st);
+  launch_xmid<T, B>(L, st);
+  if (D.midAxis) launch_col<T, B>(L, OP_FWD, D.midAxis, D.s, st);
+  launch_col<T, B>(L, OP_DIV, D.opAxis, D.c, st);
+  if (D.midAxis) launch_col<T, B>(L, OP_INV, D.midAxis, D.c, st);
+  // PRE_PUPD writes p; the epilogue reads the operator's input from in_slot
+  launch_xinv<T, B>(L, post, pre == PRE_PUPD ? (int)SL_P : in_slot, out_slot, masked, want_dot, st);
+}
+
+template <typename T, int B>
+void launch_precond_impl(const Plan<T>& P, int pre, int in_slot, int out_slot, int masked, cudaStream_t st,
+                         const BatchLaunch<T>* bl) {
+  const Desc<T>& D = P.h;
+  const Launch<T, B> L{P, bl};
+  launch_xfwd<T, B>(L, pre, in_slot, st);
+  if (D.midAxis) launch_col<T, B>(L, OP_FWD, D.midAxis, D.c, st);
+  launch_col<T, B>(L, OP_PREC, D.opAxis, D.c, st);
+  if (D.midAxis) launch_col<T, B>(L, OP_INV, D.midAxis, D.c, st);
+  launch_xinv<T, B>(L, POST_PREC, in_slot, out_slot, masked, 0, st);
 }
 
 // Plain 3-D transforms for testing: the x pass with c replaced by ncomp.
@@ -310,21 +438,22 @@ void launch_rfft3(const Plan<T>& P, int dir, int ncomp, int real_slot, cudaStrea
   const int nb = (int)((nsp + lx - 1) / lx);
   const size_t sm = (size_t)(D.n1 + (lx * ncomp / 2) * D.n1) * sizeof(cplx<T>);
   const int axes[2] = {1, 2};
+  const Launch<T, 0> L{P, nullptr};
   if (dir < 0) {
     prof_launch(prec_index(sizeof(T)), KK_XFWD_PLAIN, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
                 Cost<T>(D).xfft(ncomp), st, [&] { k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, -1, real_slot); });
     for (int a : axes)
-      if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T>(P, OP_FWD, a, ncomp, st);
+      if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T, 0>(L, OP_FWD, a, ncomp, st);
   } else {
     for (int a : {2, 1})
-      if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T>(P, OP_INV, a, ncomp, st);
+      if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T, 0>(L, OP_INV, a, ncomp, st);
     prof_launch(prec_index(sizeof(T)), KK_XINV_PREC, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
                 Cost<T>(D).xfft(ncomp), st, [&] { k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, +1, real_slot); });
   }
 }
 
-template <typename T>
-cudaError_t init_kernel_attributes() {
+template <typename T, int B>
+cudaError_t init_kernel_attributes_impl() {
   const int maxsm = 200 * 1024;  // opt-in limit minus the static shared memory of the reductions
   cudaError_t e = cudaSuccess;
 #define WFFT_SETATTR(k)                                                                    \
@@ -332,44 +461,57 @@ cudaError_t init_kernel_attributes() {
     cudaError_t ee = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm); \
     if (ee != cudaSuccess) e = ee;                                                         \
   } while (0)
-  WFFT_SETATTR((k_xfwd<T, PRE_PLAIN>));
-  WFFT_SETATTR((k_xfwd<T, PRE_PUPD>));
-  WFFT_SETATTR((k_xfwd<T, PRE_RUPD>));
-  WFFT_SETATTR((k_xfwd<T, PRE_CONV>));
-  WFFT_SETATTR((k_xfwd<T, PRE_XUPD>));
-  WFFT_SETATTR((k_xinv<T, POST_APPLY>));
-  WFFT_SETATTR((k_xinv<T, POST_RESID>));
-  WFFT_SETATTR((k_xinv<T, POST_PREC>));
-  WFFT_SETATTR((k_xmid<T>));
-  WFFT_SETATTR((k_xplain<T>));
+  WFFT_SETATTR((k_xfwd<T, PRE_PLAIN, B>));
+  WFFT_SETATTR((k_xfwd<T, PRE_PUPD, B>));
+  WFFT_SETATTR((k_xfwd<T, PRE_RUPD, B>));
+  WFFT_SETATTR((k_xfwd<T, PRE_CONV, B>));
+  WFFT_SETATTR((k_xfwd<T, PRE_XUPD, B>));
+  WFFT_SETATTR((k_xinv<T, POST_APPLY, B>));
+  WFFT_SETATTR((k_xinv<T, POST_RESID, B>));
+  WFFT_SETATTR((k_xinv<T, POST_PREC, B>));
+  WFFT_SETATTR((k_xmid<T, B>));
+  if (!B) WFFT_SETATTR((k_xplain<T>));
 #define WFFT_SETATTR_BX(BXV)                  \
-  WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 3>));  \
-  WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 6>));  \
-  WFFT_SETATTR((k_colop<T, OP_DIV, BXV, 3>));   \
-  WFFT_SETATTR((k_colop<T, OP_DIV, BXV, 6>));   \
-  WFFT_SETATTR((k_colop<T, OP_PREC, BXV, 2>));  \
-  WFFT_SETATTR((k_colop<T, OP_PREC, BXV, 3>));
+  WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 3, B>));  \
+  WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 6, B>));  \
+  WFFT_SETATTR((k_colop<T, OP_DIV, BXV, 3, B>));   \
+  WFFT_SETATTR((k_colop<T, OP_DIV, BXV, 6, B>));   \
+  WFFT_SETATTR((k_colop<T, OP_PREC, BXV, 2, B>));  \
+  WFFT_SETATTR((k_colop<T, OP_PREC, BXV, 3, B>));
   WFFT_SETATTR_BX(1)
   WFFT_SETATTR_BX(2)
   WFFT_SETATTR_BX(4)
-  WFFT_SETATTR((k_colplain<T, OP_FWD, 1>));
-  WFFT_SETATTR((k_colplain<T, OP_INV, 1>));
-  WFFT_SETATTR((k_colplain<T, OP_FWD, 2>));
-  WFFT_SETATTR((k_colplain<T, OP_INV, 2>));
-  WFFT_SETATTR((k_colplain<T, OP_FWD, 4>));
-  WFFT_SETATTR((k_colplain<T, OP_INV, 4>));
-  WFFT_SETATTR((k_colplain<T, OP_FWD, 8>));
-  WFFT_SETATTR((k_colplain<T, OP_INV, 8>));
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 1, B>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 1, B>));
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 2, B>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 2, B>));
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 4, B>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 4, B>));
+  WFFT_SETATTR((k_colplain<T, OP_FWD, 8, B>));
+  WFFT_SETATTR((k_colplain<T, OP_INV, 8, B>));
 #undef WFFT_SETATTR_BX
 #undef WFFT_SETATTR
   return e;
 }
 
+// Single-instance kernels and the shared host helpers.
 #define WFFT_INSTANTIATE(T)                                                                                  \
   template void plan_geometry<T>(Plan<T>&);                                                                  \
-  template void launch_apply<T>(const Plan<T>&, int, int, int, int, int, int, cudaStream_t);                \
-  template void launch_precond<T>(const Plan<T>&, int, int, int, int, cudaStream_t);                        \
+  template void launch_apply_impl<T, 0>(const Plan<T>&, int, int, int, int, int, int, cudaStream_t,          \
+                                        const BatchLaunch<T>*);                                              \
+  template void launch_precond_impl<T, 0>(const Plan<T>&, int, int, int, int, cudaStream_t,                  \
+                                          const BatchLaunch<T>*);                                            \
+  template int geo_blocks<T>(const Plan<T>&, int, int);                                                     \
+  template size_t geo_smem<T>(const Plan<T>&, int, int);                                                    \
   template void launch_rfft3<T>(const Plan<T>&, int, int, int, cudaStream_t);                               \
-  template cudaError_t init_kernel_attributes<T>();
+  template cudaError_t init_kernel_attributes_impl<T, 0>();
+
+// Grouped (batched) kernels.
+#define WFFT_INSTANTIATE_BATCH(T)                                                                            \
+  template void launch_apply_impl<T, 1>(const Plan<T>&, int, int, int, int, int, int, cudaStream_t,          \
+                                        const BatchLaunch<T>*);                                              \
+  template void launch_precond_impl<T, 1>(const Plan<T>&, int, int, int, int, cudaStream_t,                  \
+                                          const BatchLaunch<T>*);                                            \
+  template cudaError_t init_kernel_attributes_impl<T, 1>();
 
 }  // namespace wfft

@@ -1,0 +1,78 @@
+"""Grouped steps of uneven grids (wfft_batch_step): one launch per pass over
+all unconverged instances must give the same states as stepping each handle on
+its own (and as the FP64 oracle), in FP64 and mixed precision; an instance that
+fails does not commit while the others do."""
+import numpy as np
+import pytest
+
+from paper_2211_08263_gb300 import inputs
+from tests.gpu_util import oracle_field, rel, solver_lib, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(16, 16, 16), (24, 20, 12), (20, 16, 24), (32, 24, 16)]
+
+
+def _problems(seed, nsteps=4, sizes=SIZES):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for n in sizes:
+        p = inputs.random_problem(rng, 3, n, nphase=3, mask_width=2, nsteps=nsteps, contrast=3.0, dt=4e-7)
+        p.U[:, 0] = 1e-6 * np.sin(np.linspace(0.2, 1.0, nsteps)) * (1.0 + rng.random())
+        probs.append(p)
+    return probs
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-12, 1e-10), (1, 1e-10, 1e-6)])
+def test_batched_steps_match_single_steps_and_oracle(precision, tol, bar):
+    from oracle import newmark
+    torch_cuda()
+    wfft = solver_lib()
+    probs = _problems(5)
+    opt = lambda: wfft.default_options(precision=precision, tol=tol)
+    grouped = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
+    single = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
+    for k in range(probs[0].nsteps):
+        U = np.stack([p.U[k] for p in probs])
+        rc, infos = wfft.batch_step(grouped, U)
+        assert rc == wfft.OK, infos
+        for s, p in zip(single, probs):
+            s.step(p.U[k])
+        for inf in infos:
+            assert inf["status"] == wfft.OK and inf["rel_res"] <= tol * 1.0001
+    for g, s, p in zip(grouped, single, probs):
+        ug, vg, ag, ng = g.get_state()
+        us, vs, as_, ns = s.get_state()
+        assert ng == ns == p.nsteps
+        assert rel(ug, us) < (1e-10 if precision == 0 else 1e-6)
+        so, _ = newmark.oracle_from_problem(p, tol=1e-13).run(p.U)
+        assert rel(oracle_field(p, ug), so.u) < bar
+
+
+def test_batched_instance_failure_does_not_commit_and_others_do():
+    torch_cuda()
+    wfft = solver_lib()
+    probs = _problems(9, nsteps=1)
+    solvers = [wfft.Solver.from_problem(p, options=wfft.default_options(tol=1e-12, maxit=(2 if i == 1 else 500)))
+               for i, p in enumerate(probs)]
+    before = solvers[1].get_state()
+    U = np.stack([p.U[0] for p in probs])
+    rc, infos = wfft.batch_step(solvers, U)
+    assert rc == wfft.ENOTCONV
+    assert infos[1]["status"] == wfft.ENOTCONV
+    assert all(infos[i]["status"] == wfft.OK for i in (0, 2, 3))
+    after = solvers[1].get_state()
+    assert all(np.array_equal(x, y) for x, y in zip(before[:3], after[:3])) and after[3] == 0
+    assert all(solvers[i].get_state()[3] == 1 for i in (0, 2, 3))
+
+
+def test_mixed_structure_falls_back_to_one_by_one():
+    torch_cuda()
+    wfft = solver_lib()
+    rng = np.random.default_rng(3)
+    p2 = inputs.random_problem(rng, 2, (32, 24, 1), nphase=2, mask_width=2, nsteps=1)
+    p3 = inputs.random_problem(rng, 3, (16, 12, 8), nphase=2, mask_width=2, nsteps=1)
+    s = [wfft.Solver.from_problem(p) for p in (p2, p3)]
+    U = np.stack([p2.U[0], p3.U[0]])
+    rc, infos = wfft.batch_step(s, U)
+    assert rc == wfft.OK and all(i["status"] == wfft.OK for i in infos)
