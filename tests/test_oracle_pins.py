@@ -340,3 +340,57 @@ def test_3d_plane_wave_speeds_match_table_4():
         n1, n2 = int(0.25 * N1 * h / c / dt), nsteps
         speed = (cents[n2] - cents[n1]) / ((n2 - n1) * dt)
         assert abs(speed - c) / c < 1e-2, (comp, speed, c)
+
+
+# --------------------------------------------------------------------------
+# warm-start network reference (not in the paper): gradients by finite differences
+# --------------------------------------------------------------------------
+
+def test_conv_oracle_matches_direct_sum_and_finite_differences():
+    from oracle import conv
+    rng = np.random.default_rng(61)
+    x = rng.standard_normal((5, 4, 6, 3))
+    W = rng.standard_normal((27, 2, 3))
+    b = rng.standard_normal(2)
+    y = conv.conv_forward(x, W, b)
+    # brute force at a few voxels, periodic indices written out
+    for (z, yy, xx) in [(0, 0, 0), (4, 3, 5), (2, 1, 3)]:
+        ref = b.copy()
+        for o, (dz, dy, dx) in enumerate(conv.OFFSETS):
+            ref += W[o] @ x[(z + dz) % 5, (yy + dy) % 4, (xx + dx) % 6]
+        assert np.allclose(y[z, yy, xx], ref, rtol=1e-13, atol=1e-13)
+    # a 2-layer net: backward against central finite differences
+    params = [(0.3 * rng.standard_normal((27, 4, 3)), 0.1 * rng.standard_normal(4)),
+              (0.3 * rng.standard_normal((27, 2, 4)), 0.1 * rng.standard_normal(2))]
+    target = rng.standard_normal((5, 4, 6, 2))
+
+    def loss(ps, xin):
+        out, _ = conv.net_forward(xin, ps)
+        return conv.masked_mse(out, target, 1)[0]
+
+    out, cache = conv.net_forward(x, params)
+    L, dout = conv.masked_mse(out, target, 1)
+    grads, gx = conv.net_backward(params, cache, dout)
+    eps = 1e-6
+    for li in range(2):
+        for idx in [(0, 0, 0), (13, 1, 2), (26, 0, 1)]:
+            if idx[1] >= params[li][0].shape[1] or idx[2] >= params[li][0].shape[2]:
+                continue
+            pp = [(W_.copy(), b_.copy()) for W_, b_ in params]
+            pm = [(W_.copy(), b_.copy()) for W_, b_ in params]
+            pp[li][0][idx] += eps
+            pm[li][0][idx] -= eps
+            fd = (loss(pp, x) - loss(pm, x)) / (2 * eps)
+            assert abs(fd - grads[li][0][idx]) <= 1e-6 * max(1.0, abs(fd))
+        pp = [(W_.copy(), b_.copy()) for W_, b_ in params]
+        pm = [(W_.copy(), b_.copy()) for W_, b_ in params]
+        pp[li][1][0] += eps
+        pm[li][1][0] -= eps
+        fd = (loss(pp, x) - loss(pm, x)) / (2 * eps)
+        assert abs(fd - grads[li][1][0]) <= 1e-6 * max(1.0, abs(fd))
+    for idx in [(0, 0, 0, 0), (3, 2, 5, 1)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += eps
+        xm[idx] -= eps
+        fd = (loss(params, xp) - loss(params, xm)) / (2 * eps)
+        assert abs(fd - gx[idx]) <= 1e-6 * max(1.0, abs(fd))
