@@ -7,9 +7,12 @@ x-face slab), one GB300.
 A step is one Newmark step of the whole hot path: predictor, the masked
 preconditioned Krylov solve to 1e-10 (FFT operator + reference-medium
 preconditioner) and the corrector.  The headline `value` is voxel *
-Krylov-iterations / s of the mixed solve (FP32 inner PCG, FP64 dots, FP64
-true-residual refinement, FP64 state); the plain FP64 solve is measured beside
-it.  Timed with CUDA events on the solver's stream after `--warmup` untimed
+Krylov-iterations / s of the mixed+learned solve (FP32 inner PCG, FP64 dots,
+FP64 true-residual refinement, FP64 state; warm start = Taylor extrapolation
+plus the BF16 network's correction, trained on the GPU beforehand -- untimed --
+on 2000 step pairs of new-seed polycrystal runs at 48^3); the plain FP64
+solve, the mixed solve from u_{n-1} and the mixed solve from the Taylor
+extrapolation alone are measured beside it.  Timed with CUDA events on the solver's stream after `--warmup` untimed
 steps; every field is >= 64 MB, so the working set of each pass exceeds L2.
 
 `--impl reference` times the FP64 CPU oracle (the reference implementation
@@ -47,7 +50,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid edge (the workload is 256)")
-    ap.add_argument("--modes", default="mixed,fp64")
+    ap.add_argument("--modes", default="learned,mixed,taylor,fp64",
+                    help="learned = mixed + learned warm start, taylor = mixed + Taylor warm start, "
+                         "mixed = mixed from u_{n-1}, fp64 = plain FP64 from u_{n-1}")
+    ap.add_argument("--hidden", type=int, default=32, help="warm-start network width (16 or 32)")
+    ap.add_argument("--train-pairs", type=int, default=2000)
+    ap.add_argument("--train-n", type=int, default=48)
+    ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
@@ -130,18 +139,81 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed inside a long step: the
+    sustained cuBLAS figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("bf16_tflops_sustained", d.get("bf16_tflops", 1700.0)), "measured (sustained)"
+    return 1700.0, "fallback (sustained)"
+
+
+def net_roofline(prof):
+    """The warm-start convolutions (BF16 tensor-core contraction) against the BF16 peak."""
+    d = prof.get(("fp32", "net_conv"))
+    if not d or not d["timed"]:
+        return None
+    peak, src = bf16_peak()
+    per = d["ms"] / d["timed"]
+    ach = d["flops"] / d["timed"] / (per * 1e-3) / 1e12
+    return {"kernel": "net_conv (bf16 mma.sync, f32 accumulate)", "bound": "tensor", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src, "ms_per_launch": per,
+            "launches": d["timed"], "ms_total": d["ms"]}
+
+
 # FP64 FMA throughput of a GB300, measured with an FMA-chain microbenchmark
 # (152 SMs x 2 FP64 FMA/clk/SM x 2 flop x ~1.97 GHz); the FP64 kernels are
 # bound by it rather than by HBM.
 FP64_PEAK_GFLOPS = 1195.2
 
 
-def run_mode(wfft, torch, prob, precision, W, K, world, e2e: bool, inner_tol=None):
+MODES = {"learned": ("mixed+learned", "MIXED", "WARM_LEARNED"), "taylor": ("mixed+taylor", "MIXED", "WARM_TAYLOR"),
+         "mixed": ("mixed", "MIXED", "WARM_PREV"), "fp64": ("fp64", "FP64", "WARM_PREV")}
+
+
+def train_warm_start(wfft, args, stream):
+    """GPU training of the warm-start network (untimed): step pairs collected from
+    runs of the same kind of workload with new seeds -- polycrystals at
+    train_n^3 with 6..21 grains, Gaussian pulses of widths 10..50 dt."""
+    from paper_2211_08263_gb300 import inputs
+    nruns = 16
+    steps = max(1, -(-args.train_pairs // nruns))
+    t0 = time.perf_counter()
+    tr = wfft.Trainer(wfft.model_init(args.hidden, seed=0), stream=stream.cuda_stream)
+    opt = wfft.default_options(precision=wfft.MIXED, tol=1e-10, maxit=500, check_every=4)
+    for r in range(nruns):
+        width = 10.0 + 40.0 * r / (nruns - 1)
+        p = inputs.config_c3(nsteps=steps, n=args.train_n, ngrains=6 + r, seed=1000 + r, width_steps=width)
+        s = wfft.Solver.from_problem(p, options=opt, stream=stream.cuda_stream)
+        tr.collect(s, p.U)
+        s.close()
+    t1 = time.perf_counter()
+    loss0 = tr.fit(1, batch=8, lr=1e-3, seed=1)
+    loss = tr.fit(max(0, args.epochs - 1), batch=8, lr=1e-3, seed=2) if args.epochs > 1 else loss0
+    blob = tr.model()
+    info = {"hidden": args.hidden, "pairs": tr.samples, "grid": args.train_n, "runs": nruns,
+            "epochs": args.epochs, "batch": 8, "lr": 1e-3, "loss_first_epoch": loss0, "loss_last_epoch": loss,
+            "collect_s": round(t1 - t0, 2), "fit_s": round(time.perf_counter() - t1, 2)}
+    tr.close()
+    return blob, info
+
+
+def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None):
     stream = torch.cuda.current_stream()
-    opt = wfft.default_options(precision=precision, tol=1e-10, maxit=500, check_every=4)
+    _, prec, warm = MODES[mode]
+    opt = wfft.default_options(precision=getattr(wfft, prec), tol=1e-10, maxit=500, check_every=4,
+                               warm_start=getattr(wfft, warm))
     if inner_tol:
         opt.inner_tol = inner_tol
-    s = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
+
+    def make():
+        sv = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
+        if mode == "learned":
+            sv.set_model(blob)
+        return sv
+
+    s = make()
     for n in range(W):
         s.step(prob.U[n])
     torch.cuda.synchronize()
@@ -171,7 +243,7 @@ def run_mode(wfft, torch, prob, precision, W, K, world, e2e: bool, inner_tol=Non
         # end to end through the C ABI: U(t_n) from host memory in, the displacement
         # field u_n copied back to pinned host memory after every step
         host_u = torch.empty(s.shape, dtype=torch.float64, pin_memory=True).numpy()
-        s2 = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
+        s2 = make()
         for n in range(W):
             s2.step(prob.U[n])
         torch.cuda.synchronize()
@@ -291,13 +363,18 @@ def main():
     hbm_peak, peak_kind = load_peaks()
     V = prob.nvox
     modes = [m.strip() for m in args.modes.split(",") if m.strip()]
+    for m in modes:
+        if m not in MODES:
+            raise SystemExit(f"unknown mode {m!r}; choose from {sorted(MODES)}")
+    blob, learned = None, None
+    if "learned" in modes:
+        blob, learned = train_warm_start(wfft, args, torch.cuda.current_stream())
     clocks = ClockSampler(local)
     results = {}
     for m in modes:
-        prec = wfft.MIXED if m == "mixed" else wfft.FP64
         if m == modes[0]:
             clocks.start()
-        results[m] = run_mode(wfft, torch, prob, prec, W, K, world, e2e=(m == modes[0] and not args.no_e2e),
+        results[m] = run_mode(wfft, torch, prob, m, blob, W, K, world, e2e=(m == modes[0] and not args.no_e2e),
                               inner_tol=args.inner_tol)
         if m == modes[0]:
             clk = clocks.stop()
@@ -315,7 +392,7 @@ def main():
     value = V * iters / (ms * 1e-3)
     modes_out = {}
     for m, r in results.items():
-        modes_out[m] = {"ms_per_step": r["ms_total"] / K, "s_per_step": r["ms_total"] / K / 1e3,
+        modes_out[MODES[m][0]] = {"ms_per_step": r["ms_total"] / K, "s_per_step": r["ms_total"] / K / 1e3,
                         "voxel_iters_per_s": V * r["iters"] / (r["ms_total"] * 1e-3),
                         "krylov_iters_per_step": r["iters"] / K, "fp64_applies_per_step": r["outer_applies"] / K,
                         "sweeps_per_step": r["sweeps"] / K, "max_rel_res": r["rel_res_max"],
@@ -328,15 +405,25 @@ def main():
             rl["traffic"] = tf["kernels"][rl["kernel"]]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (inner PCG) + f64 (dots, residual refinement, state)" if modes[0] == "mixed" else "f64",
+            "dtype": {"fp64": "f64",
+                      "mixed": "f32 (inner PCG) + f64 (dots, residual refinement, state)",
+                      "taylor": "f32 (inner PCG) + f64 (dots, residual refinement, state)",
+                      "learned": "f32 (inner PCG) + f64 (dots, residual refinement, state) + bf16 (warm-start "
+                                 "network, f32 accumulate)"}[modes[0]],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [prob.n[0], prob.n[1], prob.n[2]], "mode": modes[0],
+            "config": {"workload": WORKLOAD, "grid": [prob.n[0], prob.n[1], prob.n[2]],
+                       "mode": MODES[modes[0]][0],
                        "timed_steps": [W + 1, W + K], "tol": 1e-10,
                        "l2": "inputs larger than L2 (every field >= 64 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "modes": modes_out, "roofline": rl,
             "kernels": kernel_table(head["profile"], hbm_peak, head["ms_total"]),
             "gpu_launches": head["launches"], "clocks": clk}
+    if learned:
+        line["learned"] = learned
+        nr = net_roofline(results["learned"]["profile"])
+        if nr:
+            line["roofline_net"] = nr
     if "e2e_s" in head:
         line["e2e"] = {"value": V * head["e2e_iters"] * world / head["e2e_s"], "unit": UNIT,
                        "h2d_bytes_per_step": 24, "d2h_bytes_per_step": head["d2h_bytes"],

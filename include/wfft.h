@@ -62,7 +62,7 @@ extern "C" {
 /* warm start of the solve of each step */
 #define WFFT_WARM_PREV 0     /* x0 = u_{n-1} (the paper's choice) */
 #define WFFT_WARM_TAYLOR 1   /* x0 = u + dt v + dt^2/2 a */
-#define WFFT_WARM_LEARNED 2  /* x0 = u_{n-1} + network prediction (wfft_set_model) */
+#define WFFT_WARM_LEARNED 2  /* x0 = u + dt v + dt^2/2 a + s y, y = network prediction (wfft_set_model) */
 
 typedef struct wfft_handle wfft_handle;
 
@@ -198,6 +198,76 @@ WFFT_API int wfft_spectral_pitch(const wfft_handle* h, int* pitch);
  */
 WFFT_API int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step_info* infos);
 
+/*
+ * Learned warm start.  Not part of the paper's method: the paper starts each
+ * step's Krylov solve from u_{n-1}.  A small network predicts the part of the
+ * next displacement that the Taylor extrapolation misses, and the prediction
+ * only changes the initial guess: the same stopping test (see wfft_step) still
+ * decides when a step has converged.
+ *
+ * Network: four periodic 3x3x3 convolutions 16 -> H -> H -> H -> 3 with ReLU
+ * after the first three, H = 16 or 32; BF16 weights and activations, FP32
+ * accumulation and biases.  Inputs per voxel (channels-last, 16): dt v / s (3),
+ * (dt^2/2) a / s (3), U(t_n) - (u + dt v + dt^2/2 a) on the prescribed DOFs / s
+ * (3), prescribed indicator, rho / rho_bar - 1, C_11 / C_bar_11 - 1,
+ * C_22 / C_bar_22 - 1, C_33 / C_bar_33 - 1, (C_44 + C_55 + C_66) / mean - 1,
+ * (C_12 + C_13 + C_23) / mean - 1 (2-D: the in-plane entries, absent ones 0),
+ * with s = sqrt(mean over DOFs of (dt v)^2 + (dt^2/2 a)^2, plus the prescribed
+ * increments squared / (c V)).  Output y (3 channels): the warm start is
+ * x0 = u + dt v + dt^2/2 a + s y on the free DOFs and U(t_n) on Gamma; the
+ * training target is (u_n - u - dt v - dt^2/2 a) / s = beta dt^2 (a_n - a_{n-1}) / s.
+ *
+ * Model blob (host memory, native byte order): 8 int32 {magic 0x314E4657,
+ * version 1, layers 4, cin 16, hidden H, cout 3, cout_pad 16, 0}, then per layer
+ * l = 1..4 the FP32 weights W[27][cout_l][cin_l] (offset o = 9 (dz+1) +
+ * 3 (dy+1) + (dx+1), output voxel x reads input voxel x + (dx, dy, dz) mod N)
+ * followed by the FP32 biases b[cout_l]; cout_4 = 16 (only the first 3 are used).
+ */
+/* Bytes of a model blob of hidden width H (0 unless H is 16 or 32). */
+WFFT_API size_t wfft_model_bytes(int hidden);
+/* Seeded initial model: He-normal weights for layers 1-3, zero last layer (so the
+   untrained network reproduces the Taylor warm start exactly).  bytes must equal
+   wfft_model_bytes(hidden). */
+WFFT_API int wfft_model_init(int hidden, unsigned long long seed, void* blob, size_t bytes);
+/* Load a model into a handle (copied; the blob may be freed afterwards) for
+   warm_start = WFFT_WARM_LEARNED.  blob = NULL with bytes = 0 unloads.  Allocates
+   (16 + 2 H) * 2 bytes per voxel of work buffers.  EINVAL on a malformed blob. */
+WFFT_API int wfft_set_model(wfft_handle* h, const void* blob, size_t bytes);
+
+/* GPU training of the warm-start network on trajectories of the method itself. */
+typedef struct wfft_trainer wfft_trainer;
+/* Trainer on the current device starting from a model blob, issuing its work on
+   cuda_stream (NULL = default stream).  Keeps FP32 master parameters and Adam moments. */
+WFFT_API int wfft_trainer_create(const void* blob, size_t bytes, void* cuda_stream, wfft_trainer** out);
+/* Advance handle h by nsteps steps (U: nsteps x 3, as wfft_step) and keep one
+   training pair per step (features of the state before the step, target after it),
+   (16 * 2 + 4 * 4) bytes per voxel per step on the device.  infos (nsteps entries,
+   optional) receives each step's wfft_step_info.  A failing step stops the
+   collection with its status; the pairs of the earlier steps are kept. */
+WFFT_API int wfft_trainer_collect(wfft_trainer* t, wfft_handle* h, const double* U, int nsteps,
+                                  wfft_step_info* infos);
+/* Number of training pairs collected so far. */
+WFFT_API long long wfft_trainer_samples(const wfft_trainer* t);
+/* epochs passes over the pairs in seeded random order; Adam (beta1 0.9, beta2 0.999,
+   eps 1e-8, step lr) on the mean of batch per-pair losses.  Loss of a pair: mean
+   over its free DOFs of (y - target)^2.  *loss (optional): mean loss of the last epoch. */
+WFFT_API int wfft_trainer_fit(wfft_trainer* t, int epochs, int batch, double lr, unsigned long long seed,
+                              double* loss);
+/* Current parameters as a model blob (bytes = wfft_model_bytes(hidden)). */
+WFFT_API int wfft_trainer_get_model(const wfft_trainer* t, void* blob, size_t bytes);
+WFFT_API const char* wfft_trainer_error(const wfft_trainer* t);
+WFFT_API void wfft_trainer_destroy(wfft_trainer* t);
+
+/* One evaluation of the network on a periodic grid n = {N1, N2, N3}: x is
+   [V][16] FP32 host features (rounded to BF16 on the device), y receives
+   [V][3] FP32 outputs. */
+WFFT_API int wfft_net_forward(const void* blob, size_t bytes, const int n[3], const float* x, float* y);
+/* Loss of one pair (mean over free DOFs of (y - target)^2, target [V][3], mask
+   uint8 [V] with bit k set = component k prescribed, or NULL; c components) and its gradient
+   w.r.t. the parameters (grad: FP32 in the blob's parameter layout). */
+WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], int c, const float* x,
+                                const float* target, const unsigned char* mask, float* grad, double* loss);
+
 /* Kernel kinds of the launch accounting (wfft_profile_read). */
 #define WFFT_K_XFWD_PLAIN 0   /* x-axis real->half-spectrum pass */
 #define WFFT_K_XFWD_PUPD 1    /* ... fused with p = z + beta p */
@@ -214,7 +284,9 @@ WFFT_API int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step
 #define WFFT_K_COL_PREC 12    /* column pass fused with (theta K(xi) + rho_bar I)^-1 and Parseval (r,z) */
 #define WFFT_K_NEWMARK 13     /* predictor / corrector */
 #define WFFT_K_SCALAR 14      /* single-block finalize and bookkeeping kernels */
-#define WFFT_K_COUNT 15
+#define WFFT_K_NET_CONV 15    /* warm-start network convolutions (BF16 MMA, FP32 accumulate; counted as precision 1) */
+#define WFFT_K_NET_AUX 16     /* warm-start scale, features, Taylor increment, training bookkeeping (precision 1) */
+#define WFFT_K_COUNT 17
 
 /*
  * Launch accounting.  Every kernel launch of a handle is counted per kind and

@@ -68,12 +68,9 @@ def net_backward(params, cache, dout: np.ndarray):
     return grads, g
 
 
-def masked_mse(pred: np.ndarray, target: np.ndarray, margin: int):
-    """Mean squared error over the voxels at least `margin` away from the crop
-    border (outside the receptive field of the wrapped periodic border), and its
-    gradient w.r.t. pred."""
-    m = np.zeros(pred.shape[:3], dtype=bool)
-    m[margin:pred.shape[0] - margin, margin:pred.shape[1] - margin, margin:pred.shape[2] - margin] = True
-    diff = (pred - target) * m[..., None]
-    n = m.sum() * pred.shape[3]
+def masked_mse(pred: np.ndarray, target: np.ndarray, free: np.ndarray):
+    """Mean squared error over the entries where `free` (bool, shape of pred) is
+    set -- the free DOFs of a training pair -- and its gradient w.r.t. pred."""
+    diff = (pred - target) * free
+    n = max(int(free.sum()), 1)
     return float((diff ** 2).sum() / n), 2.0 * diff / n

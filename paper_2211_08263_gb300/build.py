@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwfft.so")
-SOURCES = ["capi.cu", "k_f64.cu", "k_f32.cu", "k_f64b.cu", "k_f32b.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "k_f64.cu", "k_f32.cu", "k_f64b.cu", "k_f32b.cu", "noalloc.cu", "k_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fvisibility=hidden"]

@@ -16,6 +16,7 @@
 #include "passes.cuh"
 #include "profiler.cuh"
 #include "host_util.h"
+#include "net.cuh"
 
 using namespace wfft;
 
@@ -45,6 +46,11 @@ struct wfft_handle {
   bool au_valid = false;    // SL_AU holds A u for the current state u (mixed mode)
   bool last_resid_on_x = false;
   double U_prev[3] = {0, 0, 0};
+  double cbar[21] = {0};
+  double rhobar = 0;
+  NetDev* net = nullptr;    // learned warm start (wfft_set_model)
+  NetWork nw;
+  float* delta = nullptr;   // FP64 handles: FP32 warm-start increment
   std::string err;
 };
 
@@ -309,6 +315,8 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   }
   for (int k = 0; k < 21; ++k) cbar[k] /= (double)V;
   rhobar /= (double)V;
+  for (int k = 0; k < 21; ++k) h->cbar[k] = cbar[k];
+  h->rhobar = rhobar;
   // per-voxel component mask bits
   std::vector<uint8_t> mbits((size_t)V, 0);
   long long nfixed = 0;
@@ -434,6 +442,8 @@ extern "C" void wfft_destroy(wfft_handle* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   for (void* p : h->dev_allocs) cudaFree(p);
+  net_free(h->net);
+  net_work_free(&h->nw);
   if (h->P64.d) cudaFree(h->P64.d);
   if (h->P32.d) cudaFree(h->P32.d);
   if (h->host_sc) cudaFreeHost(h->host_sc);
@@ -547,7 +557,7 @@ static int pcg_loop(wfft_handle* h, Plan<T>& P, Scalars* sc, int which, int budg
 }
 
 // Solve with B, X set and sc64->ref2 known; fills status / counts.
-static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false) {
+static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false, bool inner_guess = false) {
   Plan<double>& P = h->P64;
   const Desc<double>& D = P.h;
   const int op = D.opAxis;
@@ -570,7 +580,9 @@ static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false)
     bool stored = use_au;
     for (;;) {
       if (stored) {
-        // initial residual already formed by the predictor from the stored A u
+        // initial residual already formed by the predictor from the stored A u; with an
+        // increment warm start d, q = P A d (FP32) for the first inner solve's residual
+        if (inner_guess) launch_apply<float>(F, PRE_PLAIN, SL_D, POST_APPLY, SL_Q, 1, 0, h->st);
         launch_fin(h->sc64, D.part[PT_B], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_OUTER, h->sc32, h->st);
       } else {
         // after an inner solve the residual pass first folds its FP32 correction into x
@@ -596,7 +608,7 @@ static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false)
         break;
       }
       ++sweeps;
-      launch_precond<float>(F, PRE_CONV, SL_R, SL_Z, 1, h->st);
+      launch_precond<float>(F, inner_guess && sweeps == 1 ? PRE_CONVD : PRE_CONV, SL_R, SL_Z, 1, h->st);
       launch_fin(h->sc32, nullptr, 0, DF.part[PT_B], F.g.blk_col[DF.opAxis][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, h->st);
       int it = 0;
       rc = pcg_loop<float>(h, F, h->sc32, 1, std::max(1, watchdog - iters), &it);
@@ -628,26 +640,55 @@ static void fill_info_base(wfft_step_info* info) {
   memset(info, 0, sizeof(*info));
 }
 
+__global__ static void k_add_delta(const Desc<double>* dd, const float* delta) {
+  const Desc<double>& D = *dd;
+  double* x = reinterpret_cast<double*>(D.slot[SL_X]);
+  const long long tot = (long long)D.c * D.V;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x)
+    x[gi] += (double)delta[gi];  // delta is 0 on the prescribed DOFs
+}
+
 extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info) {
   ProfScope ps_(h);
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
   if (!U) return fail(h, WFFT_EINVAL, "U is NULL");
   fill_info_base(info);
-  if (h->opt.warm_start == WFFT_WARM_LEARNED) return fail(h, WFFT_EINVAL, "no warm-start model loaded");
+  const int warm = h->opt.warm_start;
+  if (warm == WFFT_WARM_LEARNED && !h->net) return fail(h, WFFT_EINVAL, "no warm-start model loaded");
   Plan<double>& P = h->P64;
+  const bool mixed = h->opt.precision == WFFT_MIXED;
   const double Uv[3] = {U[0], h->ndim > 1 ? U[1] : 0.0, h->ndim > 2 ? U[2] : 0.0};
-  const bool use_au = h->opt.precision == WFFT_MIXED && h->au_valid && h->opt.warm_start == WFFT_WARM_PREV;
+  // increment warm starts: x0 = u_{n-1} + delta (delta FP32, zero on Gamma); in a
+  // mixed solve with the stored A u_{n-1} the increment is the initial guess of the
+  // first FP32 inner solve, so the initial residual still needs no FP64 apply
+  const bool delta_mode = warm == WFFT_WARM_LEARNED || (mixed && warm == WFFT_WARM_TAYLOR);
+  const bool use_au = mixed && h->au_valid && (warm == WFFT_WARM_PREV || delta_mode);
   const double dU[3] = {Uv[0] - h->U_prev[0], Uv[1] - h->U_prev[1], Uv[2] - h->U_prev[2]};
   CKH(h, cudaEventRecord(h->ev0, h->st));
-  launch_begin(h->sc64, Uv, h->opt.warm_start, h->opt.tol * h->opt.tol, h->opt.maxit, h->st, use_au ? 1 : 0, dU);
-  launch_begin(h->sc32, Uv, h->opt.warm_start, h->opt.inner_tol * h->opt.inner_tol, h->opt.maxit, h->st);
+  launch_begin(h->sc64, Uv, delta_mode ? WFFT_WARM_PREV : warm, h->opt.tol * h->opt.tol, h->opt.maxit, h->st,
+               use_au ? 1 : 0, dU);
+  launch_begin(h->sc32, Uv, delta_mode ? WFFT_WARM_PREV : warm, h->opt.inner_tol * h->opt.inner_tol,
+               h->opt.maxit, h->st);
   launch_predict(P, h->st);
   launch_fin(h->sc64, P.h.part[PT_A], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
+  bool inner_guess = false;
+  if (delta_mode) {
+    WarmArgs wa;
+    handle_warm_args(h, Uv, &wa, nullptr, nullptr);
+    float* delta = mixed ? reinterpret_cast<float*>(h->P32.h.slot[SL_D]) : h->delta;
+    net_warm(warm == WFFT_WARM_LEARNED ? h->net : nullptr, &h->nw, wa, delta, h->st);
+    if (use_au) {
+      inner_guess = true;
+    } else {
+      prof_launch(0, KK_NEWMARK, 20.0 * h->c * h->V, (double)h->c * h->V, h->st,
+                  [&] { k_add_delta<<<ew_block_count(P), 256, 0, h->st>>>(P.d, delta); });
+    }
+  }
   h->last_resid_on_x = false;
-  int status = solve_core(h, info, use_au);
+  int status = solve_core(h, info, use_au, inner_guess);
   // the stored A x is A u_n only if the last residual evaluation ran on the final x
-  h->au_valid = status == WFFT_OK && h->opt.precision == WFFT_MIXED && h->last_resid_on_x &&
-                !h->host_sc[0].zero_free;
+  h->au_valid = status == WFFT_OK && mixed && h->last_resid_on_x && !h->host_sc[0].zero_free;
   if (status == WFFT_OK) {
     for (int k = 0; k < 3; ++k) h->U_prev[k] = Uv[k];
     launch_correct(P, h->st);
@@ -671,6 +712,88 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
     snprintf(buf, sizeof buf, "step not committed (status %d)", status);
     return fail(h, status, buf);
   }
+  return WFFT_OK;
+}
+
+namespace wfft {
+// Device fields of a handle for the warm-start kernels (k_net.cu).
+int handle_warm_args(wfft_handle* h, const double U[3], WarmArgs* a, cudaStream_t* st, int* device) {
+  if (!h || !a) return WFFT_EINVAL;
+  const Desc<double>& D = h->P64.h;
+  const Desc<float>& F = h->P32.h;
+  WarmArgs w{};
+  w.n1 = h->n[0];
+  w.n2 = h->n[1];
+  w.n3 = h->n[2];
+  w.c = h->c;
+  w.V = h->V;
+  w.u = reinterpret_cast<const double*>(D.slot[SL_U]);
+  w.v = reinterpret_cast<const double*>(D.slot[SL_V]);
+  w.a = reinterpret_cast<const double*>(D.slot[SL_A]);
+  w.mask = h->has_mask ? D.mask : nullptr;
+  w.phase = D.phase;
+  w.ctab = F.ctab;
+  w.cstride = h->ndim == 3 ? kCtabStride3 : kCtabStride2;
+  w.rhotab = F.rhotab;
+  // entries of the material row and of the 21-value mean stiffness for the features:
+  // normal diagonal, shear diagonal (summed), normal off-diagonal (summed)
+  const int nd3[3] = {0, 6, 11}, sh3[3] = {15, 18, 20}, of3[3] = {1, 2, 7};
+  const int nd2[3] = {0, 3, -1}, sh2[3] = {5, -1, -1}, of2[3] = {1, -1, -1};
+  const int nd2c[3] = {0, 6, -1}, sh2c[3] = {20, -1, -1}, of2c[3] = {1, -1, -1};
+  const bool three = h->ndim == 3;
+  double ssh = 0, sof = 0;
+  for (int k = 0; k < 3; ++k) {
+    w.nd_idx[k] = three ? nd3[k] : nd2[k];
+    w.sh_idx[k] = three ? sh3[k] : sh2[k];
+    w.of_idx[k] = three ? of3[k] : of2[k];
+    const int ndc = three ? nd3[k] : nd2c[k], shc = three ? sh3[k] : sh2c[k], ofc = three ? of3[k] : of2c[k];
+    w.inv_nd[k] = ndc >= 0 && h->cbar[ndc] > 0 ? (float)(1.0 / h->cbar[ndc]) : 0.f;
+    if (shc >= 0) ssh += h->cbar[shc];
+    if (ofc >= 0) sof += h->cbar[ofc];
+  }
+  w.inv_sh = ssh > 0 ? (float)(1.0 / ssh) : 0.f;
+  w.inv_of = std::fabs(sof) > 1e-12 * std::fabs(h->cbar[0]) ? (float)(1.0 / sof) : 0.f;
+  w.inv_rhobar = (float)(1.0 / h->rhobar);
+  w.dt = h->dt;
+  w.theta = h->theta;
+  for (int k = 0; k < 3; ++k) w.Ug[k] = k < h->c ? U[k] : 0.0;
+  *a = w;
+  if (st) *st = h->st;
+  if (device) {
+    cudaPointerAttributes pa;
+    *device = cudaPointerGetAttributes(&pa, D.slot[SL_U]) == cudaSuccess ? pa.device : -1;
+  }
+  return WFFT_OK;
+}
+}  // namespace wfft
+
+extern "C" int wfft_set_model(wfft_handle* h, const void* blob, size_t bytes) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (!blob && bytes == 0) {
+    CKH(h, cudaStreamSynchronize(h->st));
+    net_free(h->net);
+    h->net = nullptr;
+    return WFFT_OK;
+  }
+  CKH(h, cudaStreamSynchronize(h->st));
+  NetDev* n = nullptr;
+  std::string err;
+  int rc = net_upload(blob, bytes, false, &n, &err);
+  if (rc) return fail(h, rc, err);
+  rc = net_work_alloc(&h->nw, h->V, n->d.hidden);
+  if (rc) {
+    net_free(n);
+    return fail(h, rc, "warm-start work buffers");
+  }
+  if (h->opt.precision == WFFT_FP64 && !h->delta) {
+    cudaError_t e = dalloc(h, &h->delta, (size_t)h->c * h->V * sizeof(float));
+    if (e != cudaSuccess) {
+      net_free(n);
+      return fail(h, WFFT_ENOMEM, "warm-start increment buffer");
+    }
+  }
+  net_free(h->net);
+  h->net = n;
   return WFFT_OK;
 }
 

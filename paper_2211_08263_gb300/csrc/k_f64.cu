@@ -54,10 +54,8 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
     double x0;
     if (warm == 1)
       x0 = uu + dt * vv + 0.5 * dt * dt * aa;
-    else if (warm == 2)
-      x0 = x[gi];  // prepared by the warm-start network
     else
-      x0 = uu;
+      x0 = uu;  // increment warm starts add their FP32 increment after this pass
     const bool isg = (D.mask[vox] >> k) & 1;
     const double Uk = k == 0 ? U0 : (k == 1 ? U1 : U2);
     if (isg) x0 = Uk;

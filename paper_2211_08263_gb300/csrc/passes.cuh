@@ -22,7 +22,7 @@
 
 namespace wfft {
 
-enum { PRE_PLAIN = 0, PRE_PUPD = 1, PRE_RUPD = 2, PRE_CONV = 3, PRE_XUPD = 4 };
+enum { PRE_PLAIN = 0, PRE_PUPD = 1, PRE_RUPD = 2, PRE_CONV = 3, PRE_XUPD = 4, PRE_CONVD = 5 };
 enum { POST_APPLY = 0, POST_RESID = 1, POST_PREC = 2 };
 enum { OP_FWD = 0, OP_INV = 1, OP_GRAD = 2, OP_DIV = 3, OP_PREC = 4 };
 
@@ -117,6 +117,8 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const cplx<T>* src, i
 //   PRE_RUPD   r -= alpha q, ||r||^2, and the solution update: x += alpha p (FP64
 //              solve) or d += alpha p (FP32 correction of a mixed inner solve)
 //   PRE_CONV   r = scale * r64 in T, d = 0 (start of a mixed inner solve)
+//   PRE_CONVD  r = scale * (r64 - q), d = scale * d (start of a mixed inner solve
+//              from the initial guess d with q = P A d already formed)
 //   PRE_XUPD   x += xcoef * d (FP64 descriptor of a mixed solve: folds the
 //              finished inner correction into the FP64 solution) and transform x
 // ---------------------------------------------------------------------------
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc
     beta = (T)sc->beta;
   }
   if (PRE == PRE_RUPD) alpha = (T)sc->alpha;
-  if (PRE == PRE_CONV) scale = sc->scale;
+  if (PRE == PRE_CONV || PRE == PRE_CONVD) scale = sc->scale;
   if (PRE == PRE_XUPD) xc = D.sc_inner->xcoef;
   DotAcc<T> acc;
   constexpr int U = 4;  // elements per lane kept in flight
@@ -179,6 +181,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc
                                   : reinterpret_cast<const T*>(D.slot[SL_D])[gi];
           } else if (PRE == PRE_CONV) {
             w[u] = reinterpret_cast<const double*>(D.slot[SL_R64])[gi];
+          } else if (PRE == PRE_CONVD) {
+            w[u] = reinterpret_cast<const double*>(D.slot[SL_R64])[gi];
+            b[u] = reinterpret_cast<const T*>(D.slot[SL_Q])[gi];
+            e[u] = reinterpret_cast<const T*>(D.slot[SL_D])[gi];
           } else {  // PRE_XUPD (T = double)
             a[u] = reinterpret_cast<const T*>(D.slot[SL_X])[gi];
             e[u] = (T)reinterpret_cast<const float*>(D.slot[SL_D])[gi];
@@ -211,6 +217,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc
             val = (T)(w[u] * scale);
             reinterpret_cast<T*>(D.slot[SL_R])[gi] = val;
             reinterpret_cast<T*>(D.slot[SL_D])[gi] = (T)0;
+          } else if (PRE == PRE_CONVD) {
+            val = (T)((w[u] - (double)b[u]) * scale);
+            reinterpret_cast<T*>(D.slot[SL_R])[gi] = val;
+            reinterpret_cast<T*>(D.slot[SL_D])[gi] = (T)((double)e[u] * scale);
           } else {  // PRE_XUPD
             val = a[u] + (T)(xc * (double)e[u]);
             reinterpret_cast<T*>(D.slot[SL_X])[gi] = val;

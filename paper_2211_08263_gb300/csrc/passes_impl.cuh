@@ -195,6 +195,7 @@ static void launch_xfwd(const Launch<T, B>& L, int pre, int in_slot, cudaStream_
           case PRE_PUPD: b = 3 * k.real(k.c) + out; f += 2 * k.c * k.V; break;
           case PRE_RUPD: b = 6 * k.real(k.c) + out; f += 6 * k.c * k.V; break;
           case PRE_CONV: b = 8 * k.c * k.V + 2 * k.real(k.c) + out; f += k.c * k.V; break;
+          case PRE_CONVD: b = 8 * k.c * k.V + 4 * k.real(k.c) + out; f += 3 * k.c * k.V; break;
           default: b = 2 * k.real(k.c) + 4 * k.c * k.V + out; f += 2 * k.c * k.V; break;
         }
       },
@@ -211,6 +212,10 @@ static void launch_xfwd(const Launch<T, B>& L, int pre, int in_slot, cudaStream_
       break;
     case PRE_CONV:
       prof_launch(pi, KK_XFWD_CONV, by, fl, st, [&] { k_xfwd<T, PRE_CONV, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
+      break;
+    case PRE_CONVD:
+      if constexpr (B == 0 && sizeof(T) == 4)
+        prof_launch(pi, KK_XFWD_CONV, by, fl, st, [&] { k_xfwd<T, PRE_CONVD, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
     default:  // PRE_XUPD: x += xcoef d (FP64 x, FP32 d), then transform x
       prof_launch(pi, KK_XFWD_PLAIN, by, fl, st, [&] { k_xfwd<T, PRE_XUPD, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
@@ -466,6 +471,7 @@ cudaError_t init_kernel_attributes_impl() {
   WFFT_SETATTR((k_xfwd<T, PRE_RUPD, B>));
   WFFT_SETATTR((k_xfwd<T, PRE_CONV, B>));
   WFFT_SETATTR((k_xfwd<T, PRE_XUPD, B>));
+  if constexpr (B == 0 && sizeof(T) == 4) WFFT_SETATTR((k_xfwd<T, PRE_CONVD, B>));
   WFFT_SETATTR((k_xinv<T, POST_APPLY, B>));
   WFFT_SETATTR((k_xinv<T, POST_RESID, B>));
   WFFT_SETATTR((k_xinv<T, POST_PREC, B>));

@@ -20,7 +20,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "wfft.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENUMERIC, ETIMEOUT, EUNSUPPORTED = range(8)
 KERNEL_KINDS = ["xfwd_plain", "xfwd_pupd", "xfwd_rupd", "xfwd_conv", "xinv_apply", "xinv_resid", "xinv_prec",
-                "xmid", "col_fwd", "col_inv", "col_grad", "col_div", "col_prec", "newmark", "scalar"]
+                "xmid", "col_fwd", "col_inv", "col_grad", "col_div", "col_prec", "newmark", "scalar", "net_conv",
+                "net_aux"]
 FP64, MIXED = 0, 1
 WARM_PREV, WARM_TAYLOR, WARM_LEARNED = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENUMERIC", 6: "ETIMEOUT",
@@ -96,6 +97,22 @@ def load(path: str = LIB_PATH):
     lib.wfft_profile_read.argtypes = [vp, i, i, P(C.c_longlong), P(C.c_longlong), P(d), P(d), P(d)]
     lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
+    lib.wfft_model_bytes.argtypes = [i]
+    lib.wfft_model_bytes.restype = C.c_size_t
+    lib.wfft_model_init.argtypes = [i, C.c_ulonglong, vp, C.c_size_t]
+    lib.wfft_set_model.argtypes = [vp, vp, C.c_size_t]
+    lib.wfft_trainer_create.argtypes = [vp, C.c_size_t, vp, P(vp)]
+    lib.wfft_trainer_collect.argtypes = [vp, vp, P(d), i, P(StepInfo)]
+    lib.wfft_trainer_samples.argtypes = [vp]
+    lib.wfft_trainer_samples.restype = C.c_longlong
+    lib.wfft_trainer_fit.argtypes = [vp, i, i, d, C.c_ulonglong, P(d)]
+    lib.wfft_trainer_get_model.argtypes = [vp, vp, C.c_size_t]
+    lib.wfft_trainer_error.argtypes = [vp]
+    lib.wfft_trainer_error.restype = C.c_char_p
+    lib.wfft_trainer_destroy.argtypes = [vp]
+    lib.wfft_trainer_destroy.restype = None
+    lib.wfft_net_forward.argtypes = [vp, C.c_size_t, P(i), vp, vp]
+    lib.wfft_net_loss_grad.argtypes = [vp, C.c_size_t, P(i), i, vp, vp, vp, vp, P(d)]
     _lib = lib
     return lib
 
@@ -221,6 +238,15 @@ class Solver:
     def rfft3(self, inp, out, precision: int = FP64, direction: int = -1, ncomp: int = 1):
         self._check(self.lib.wfft_rfft3(self.h, precision, direction, ncomp, _dptr(inp), _dptr(out)))
 
+    # ---- learned warm start
+    def set_model(self, blob: Optional[np.ndarray]):
+        """Load a model blob (uint8 array) for warm_start = WARM_LEARNED; None unloads."""
+        if blob is None:
+            self._check(self.lib.wfft_set_model(self.h, None, 0))
+        else:
+            b = np.ascontiguousarray(blob, dtype=np.uint8)
+            self._check(self.lib.wfft_set_model(self.h, _ptr(b), b.nbytes))
+
     # ---- launch accounting
     def profile(self, enable: bool):
         self._check(self.lib.wfft_profile(self.h, int(enable)))
@@ -270,3 +296,149 @@ def batch_step(solvers, U: np.ndarray):
     infos = (StepInfo * n)()
     rc = lib.wfft_batch_step(hs, n, Ua.ctypes.data_as(C.POINTER(C.c_double)), infos)
     return rc, [infos[i].as_dict() for i in range(n)]
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: model blobs, GPU trainer, single-call network evaluation
+# ---------------------------------------------------------------------------
+NET_IN, NET_OUT, NET_OUT_PAD, NET_LAYERS = 16, 3, 16, 4
+_HEADER_INTS = 8
+
+
+def _raise_global(rc: int):
+    if rc != OK:
+        raise WfftError(rc, load().wfft_last_error(None).decode())
+
+
+def model_bytes(hidden: int) -> int:
+    return int(load().wfft_model_bytes(int(hidden)))
+
+
+def model_init(hidden: int = 32, seed: int = 0) -> np.ndarray:
+    """Seeded initial model blob (uint8); its last layer is zero (Taylor warm start)."""
+    nb = model_bytes(hidden)
+    if nb == 0:
+        raise WfftError(EINVAL, "hidden width must be 16 or 32")
+    b = np.zeros(nb, dtype=np.uint8)
+    _raise_global(load().wfft_model_init(int(hidden), int(seed), _ptr(b), nb))
+    return b
+
+
+def layer_shapes(hidden: int):
+    """(cout, cin) of the four layers as stored."""
+    return [(hidden, NET_IN), (hidden, hidden), (hidden, hidden), (NET_OUT_PAD, hidden)]
+
+
+def blob_params(blob: np.ndarray):
+    """Model blob -> (hidden, [(W[27, cout, cin], b[cout]) per layer]) as float32 copies."""
+    b = np.ascontiguousarray(blob, dtype=np.uint8)
+    hd = b[:4 * _HEADER_INTS].view(np.int32)
+    hidden = int(hd[4])
+    th = b[4 * _HEADER_INTS:].view(np.float32)
+    out, off = [], 0
+    for co, ci in layer_shapes(hidden):
+        nw = 27 * co * ci
+        W = th[off:off + nw].reshape(27, co, ci).copy()
+        off += nw
+        out.append((W, th[off:off + co].copy()))
+        off += co
+    return hidden, out
+
+
+def params_blob(hidden: int, params) -> np.ndarray:
+    """Inverse of blob_params."""
+    hd = np.array([0x314E4657, 1, NET_LAYERS, NET_IN, hidden, NET_OUT, NET_OUT_PAD, 0], dtype=np.int32)
+    parts = [hd.view(np.uint8)]
+    for (W, bias), (co, ci) in zip(params, layer_shapes(hidden)):
+        parts.append(np.ascontiguousarray(W, dtype=np.float32).reshape(27 * co * ci).view(np.uint8))
+        parts.append(np.ascontiguousarray(bias, dtype=np.float32).reshape(co).view(np.uint8))
+    return np.concatenate(parts)
+
+
+def grad_params(hidden: int, grad: np.ndarray):
+    """Flat FP32 gradient (parameter layout) -> [(dW, db)] per layer."""
+    out, off = [], 0
+    for co, ci in layer_shapes(hidden):
+        nw = 27 * co * ci
+        dW = grad[off:off + nw].reshape(27, co, ci)
+        off += nw
+        out.append((dW, grad[off:off + co]))
+        off += co
+    return out
+
+
+def net_forward(blob: np.ndarray, n, x: np.ndarray) -> np.ndarray:
+    """Network output y [V, 3] for host features x [V, 16] on the periodic grid n = (N1, N2, N3)."""
+    b = np.ascontiguousarray(blob, dtype=np.uint8)
+    nn = (C.c_int * 3)(*[int(v) for v in n])
+    V = int(n[0]) * int(n[1]) * int(n[2])
+    xf = np.ascontiguousarray(x, dtype=np.float32).reshape(V, NET_IN)
+    y = np.empty((V, NET_OUT), dtype=np.float32)
+    _raise_global(load().wfft_net_forward(_ptr(b), b.nbytes, nn, _ptr(xf), _ptr(y)))
+    return y
+
+
+def net_loss_grad(blob: np.ndarray, n, c: int, x: np.ndarray, target: np.ndarray, mask: Optional[np.ndarray] = None):
+    """(loss, flat FP32 gradient) of one training pair."""
+    b = np.ascontiguousarray(blob, dtype=np.uint8)
+    hidden = int(b[:32].view(np.int32)[4])
+    nn = (C.c_int * 3)(*[int(v) for v in n])
+    V = int(n[0]) * int(n[1]) * int(n[2])
+    xf = np.ascontiguousarray(x, dtype=np.float32).reshape(V, NET_IN)
+    tf = np.ascontiguousarray(target, dtype=np.float32).reshape(V, NET_OUT)
+    mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(V)
+    nparam = (model_bytes(hidden) - 4 * _HEADER_INTS) // 4
+    g = np.empty(nparam, dtype=np.float32)
+    loss = C.c_double()
+    _raise_global(load().wfft_net_loss_grad(_ptr(b), b.nbytes, nn, int(c), _ptr(xf), _ptr(tf),
+                                            None if mk is None else _ptr(mk), _ptr(g), C.byref(loss)))
+    return loss.value, g
+
+
+class Trainer:
+    """GPU trainer of the warm-start network (wfft_trainer_*)."""
+
+    def __init__(self, blob: np.ndarray, stream: int = 0):
+        self.lib = load()
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        self.nbytes = b.nbytes
+        t = C.c_void_p()
+        _raise_global(self.lib.wfft_trainer_create(_ptr(b), b.nbytes, C.c_void_p(stream or None), C.byref(t)))
+        self.t = t
+
+    def _check(self, rc):
+        if rc != OK:
+            raise WfftError(rc, self.lib.wfft_trainer_error(self.t).decode())
+
+    def collect(self, solver: Solver, U: np.ndarray):
+        """Step `solver` through U (nsteps x 3), keeping one training pair per step; returns the step infos."""
+        Ua = np.ascontiguousarray(np.asarray(U, dtype=np.float64).reshape(-1, 3))
+        infos = (StepInfo * max(1, Ua.shape[0]))()
+        self._check(self.lib.wfft_trainer_collect(self.t, solver.h, Ua.ctypes.data_as(C.POINTER(C.c_double)),
+                                                  Ua.shape[0], infos))
+        return [infos[i].as_dict() for i in range(Ua.shape[0])]
+
+    @property
+    def samples(self) -> int:
+        return int(self.lib.wfft_trainer_samples(self.t))
+
+    def fit(self, epochs: int, batch: int = 4, lr: float = 1e-3, seed: int = 0) -> float:
+        loss = C.c_double()
+        self._check(self.lib.wfft_trainer_fit(self.t, int(epochs), int(batch), float(lr), int(seed), C.byref(loss)))
+        return loss.value
+
+    def model(self) -> np.ndarray:
+        b = np.zeros(self.nbytes, dtype=np.uint8)
+        self._check(self.lib.wfft_trainer_get_model(self.t, _ptr(b), b.nbytes))
+        return b
+
+    def close(self):
+        if getattr(self, "t", None):
+            self.lib.wfft_trainer_destroy(self.t)
+            self.t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -78,3 +78,43 @@ def test_create_rejects_bad_inputs_before_device_work(lib, case):
 
 def test_last_error_without_handle_is_text(lib):
     assert isinstance(lib.wfft_last_error(None), bytes)
+
+
+def test_model_blob_layout_and_initial_model(lib):
+    """Host-only parts of the learned warm start: blob size, header, the zero
+    output layer of an initial model (it reproduces the Taylor warm start) and the
+    He scale of the hidden layers; round trip through the Python (un)packing."""
+    from paper_2211_08263_gb300 import wfft
+    assert wfft.model_bytes(8) == 0 and wfft.model_bytes(64) == 0
+    for H in (16, 32):
+        nparam = sum(27 * co * ci + co for co, ci in wfft.layer_shapes(H))
+        assert wfft.model_bytes(H) == 32 + 4 * nparam
+        blob = wfft.model_init(H, seed=3)
+        hd = blob[:32].view(np.int32)
+        assert list(hd) == [0x314E4657, 1, 4, 16, H, 3, 16, 0]
+        hidden, params = wfft.blob_params(blob)
+        assert hidden == H
+        assert not params[3][0].any() and not params[3][1].any()
+        for (W, b), (co, ci) in zip(params[:3], wfft.layer_shapes(H)[:3]):
+            assert W.shape == (27, co, ci) and not b.any()
+            assert abs(W.std() - np.sqrt(2.0 / (27 * ci))) < 0.1 * np.sqrt(2.0 / (27 * ci))
+        assert np.array_equal(wfft.params_blob(H, params), blob)
+        assert np.array_equal(wfft.model_init(H, seed=3), blob)
+        assert not np.array_equal(wfft.model_init(H, seed=4), blob)
+
+
+def test_trainer_and_network_calls_fail_cleanly(lib):
+    from paper_2211_08263_gb300 import wfft
+    blob = wfft.model_init(16, 0)
+    with pytest.raises(wfft.WfftError) as e:
+        wfft.Trainer(blob[:-4])
+    assert e.value.code == wfft.EINVAL
+    bad = blob.copy()
+    bad[:4] = 0
+    with pytest.raises(wfft.WfftError) as e:
+        wfft.net_forward(bad, (4, 4, 4), np.zeros((64, 16), np.float32))
+    assert e.value.code == wfft.EINVAL
+    with pytest.raises(wfft.WfftError) as e:
+        wfft.net_forward(blob, (0, 4, 4), np.zeros((0, 16), np.float32))
+    assert e.value.code == wfft.EINVAL
+    assert lib.wfft_set_model(None, None, 0) == wfft.EINVAL

@@ -363,13 +363,14 @@ def test_conv_oracle_matches_direct_sum_and_finite_differences():
     params = [(0.3 * rng.standard_normal((27, 4, 3)), 0.1 * rng.standard_normal(4)),
               (0.3 * rng.standard_normal((27, 2, 4)), 0.1 * rng.standard_normal(2))]
     target = rng.standard_normal((5, 4, 6, 2))
+    free = rng.random((5, 4, 6, 2)) > 0.3
 
     def loss(ps, xin):
         out, _ = conv.net_forward(xin, ps)
-        return conv.masked_mse(out, target, 1)[0]
+        return conv.masked_mse(out, target, free)[0]
 
     out, cache = conv.net_forward(x, params)
-    L, dout = conv.masked_mse(out, target, 1)
+    L, dout = conv.masked_mse(out, target, free)
     grads, gx = conv.net_backward(params, cache, dout)
     eps = 1e-6
     for li in range(2):
