@@ -137,13 +137,21 @@ struct Dft<T, 7> {
 // log2 of v if v is a power of two, else -1
 __device__ __forceinline__ int log2_if_pow2(int v) { return (v & (v - 1)) ? -1 : __ffs(v) - 1; }
 
+// Row tiles store element e of a line at rowpad(e): one unused slot after every
+// 8 elements.  The radix-8 stages write butterfly outputs at stride 8 (and 8 Ns)
+// elements; with the pad, 16 consecutive butterflies land in 16 distinct 8-byte
+// bank pairs instead of 2.
+__host__ __device__ __forceinline__ constexpr int rowpad(int e) { return e + (e >> 3); }
+// Line stride (complex elements) of a row tile of lines of length N.
+__host__ __device__ __forceinline__ constexpr int row_stride(int N) { return N + (N >> 3) + 1; }
+
 // One in-place Stockham stage over `nlines` lines of length N.
-// Row tiles (ES == 1): element e of line l at buf[l * lstride + e]; consecutive
-// threads take consecutive butterflies of a line.  Column tiles (ES > 1, NL
-// lines, both compile-time): element e of line l at buf[l + e * ES];
-// consecutive threads take consecutive lines.  Both keep shared-memory
-// accesses conflict-free; compile-time strides and line counts and shifts for
-// power-of-two N and Ns keep the index arithmetic off the integer divider.
+// Row tiles (ES == 1): element e of line l at buf[l * lstride + rowpad(e)];
+// consecutive threads take consecutive butterflies of a line.  Column tiles
+// (ES > 1, NL lines, both compile-time): element e of line l at buf[l + e * ES];
+// consecutive threads take consecutive lines.  Compile-time strides and line
+// counts and shifts for power-of-two N and Ns keep the index arithmetic off the
+// integer divider.
 template <typename T, int R, int ES, int NL>
 __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int lstride, int Ns, const cplx<T>* tw,
                                           int sgn) {
@@ -180,7 +188,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
     if (id < total) {
       const cplx<T>* src = LF ? buf + line : buf + (size_t)line * lstride;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = src[(j + r * nb) * ES];
+      for (int r = 0; r < R; ++r) v[i][r] = src[LF ? (j + r * nb) * ES : rowpad(j + r * nb)];
     }
   }
   __syncthreads();
@@ -210,7 +218,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
       cplx<T>* dst = LF ? buf + line : buf + (size_t)line * lstride;
       const int base = g * Ns * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ES] = v[i][r];
+      for (int r = 0; r < R; ++r) dst[LF ? (base + r * Ns) * ES : rowpad(base + r * Ns)] = v[i][r];
     }
   }
   __syncthreads();

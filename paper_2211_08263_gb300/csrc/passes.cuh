@@ -34,7 +34,7 @@ __device__ __forceinline__ T rho_at(const Desc<T>& D, long long vox) {
 // Element x of real line q (pair q/2, part q&1) of a packed buffer.
 template <typename T>
 __device__ __forceinline__ T& packed(cplx<T>* buf, int lstr, int q, int x) {
-  return reinterpret_cast<T*>(buf + (size_t)(q >> 1) * lstr + x)[q & 1];
+  return reinterpret_cast<T*>(buf + (size_t)(q >> 1) * lstr + rowpad(x))[q & 1];
 }
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
@@ -56,8 +56,8 @@ __device__ __forceinline__ void store_unpacked(const Desc<T>& D, const cplx<T>* 
     cplx<T>* db = D.spec + (long long)(qb % nc) * D.Vh + lb * D.pitch;
     const cplx<T>* row = buf + (size_t)p * lstr;
     for (int kx = lane_id(); kx < nh; kx += 32) {
-      const cplx<T> Z = row[kx];
-      const cplx<T> W = row[kx == 0 ? 0 : N - kx];
+      const cplx<T> Z = row[rowpad(kx)];
+      const cplx<T> W = row[rowpad(kx == 0 ? 0 : N - kx)];
       const T h = (T)0.5;
       if (la < nsp) da[kx] = cmake<T>((Z.x + W.x) * h, (Z.y - W.y) * h);
       if (lb < nsp) db[kx] = cmake<T>((Z.y + W.y) * h, (W.x - Z.x) * h);
@@ -82,26 +82,36 @@ __device__ __forceinline__ void load_packed(const Desc<T>& D, cplx<T>* buf, int 
     const cplx<T>* sa = D.spec + (long long)(qa % nc) * D.Vh + la * D.pitch;
     const cplx<T>* sb = D.spec + (long long)(qb % nc) * D.Vh + lb * D.pitch;
     cplx<T>* row = buf + (size_t)p * lstr;
-    for (int k0 = lane_id(); k0 < nh; k0 += 32 * U) {
+    // the Nyquist column of an even N is taken by lane 0 next to kx = 0, so that
+    // the main loop covers exactly N/2 columns (one pass of 32 U for N = 256)
+    const int nk = (N & 1) ? nh : nh - 1;
+    const bool ny = !(N & 1) && lane_id() == 0;
+    cplx<T> An = cmake<T>(0, 0), Bn = cmake<T>(0, 0);
+    if (ny) {
+      if (la < nsp) An = sa[N / 2];
+      if (lb < nsp) Bn = sb[N / 2];
+    }
+    for (int k0 = lane_id(); k0 < nk; k0 += 32 * U) {
       cplx<T> A[U], B[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int kx = k0 + 32 * u;
-        A[u] = (kx < nh && la < nsp) ? sa[kx] : cmake<T>(0, 0);
-        B[u] = (kx < nh && lb < nsp) ? sb[kx] : cmake<T>(0, 0);
+        A[u] = (kx < nk && la < nsp) ? sa[kx] : cmake<T>(0, 0);
+        B[u] = (kx < nk && lb < nsp) ? sb[kx] : cmake<T>(0, 0);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int kx = k0 + 32 * u;
-        if (kx >= nh) continue;
-        if (kx == 0 || 2 * kx == N) {
-          row[kx] = cmake<T>(A[u].x, B[u].x);
+        if (kx >= nk) continue;
+        if (kx == 0) {
+          row[rowpad(0)] = cmake<T>(A[u].x, B[u].x);
         } else {
-          row[kx] = cmake<T>(A[u].x - B[u].y, A[u].y + B[u].x);
-          row[N - kx] = cmake<T>(A[u].x + B[u].y, B[u].x - A[u].y);
+          row[rowpad(kx)] = cmake<T>(A[u].x - B[u].y, A[u].y + B[u].x);
+          row[rowpad(N - kx)] = cmake<T>(A[u].x + B[u].y, B[u].x - A[u].y);
         }
       }
     }
+    if (ny) row[rowpad(N / 2)] = cmake<T>(An.x, Bn.x);
   }
 }
 
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc
   const int N = D.n1, nc = D.c;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* buf = tw + N;
-  const int lstr = N;
+  const int lstr = row_stride(N);
   const long long nsp = (long long)D.n2 * D.n3;
   const long long l0 = (long long)blk * LX;
   const long long V = D.V;
@@ -152,12 +162,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc
   DotAcc<T> acc;
   constexpr int U = 4;  // elements per lane kept in flight
   const int nq = LX * nc;
-  for (int q = warp_id(); q < nq; q += num_warps()) {
+  // work items (line, chunk of 32 U elements) spread evenly over the warps
+  const int nch = (N + 32 * U - 1) / (32 * U);
+  for (int it = warp_id(); it < nq * nch; it += num_warps()) {
+    const int q = it / nch;
     const int k = q % nc, l = q / nc;
     const long long line = l0 + l;
     const bool valid = line < nsp;
     const long long g0 = (long long)k * V + line * N;
-    for (int x0 = lane_id(); x0 < N; x0 += 32 * U) {
+    {
+      const int x0 = (it - q * nch) * 32 * U + lane_id();
       T a[U], b[U], c[U], e[U];
       double w[U];
 #pragma unroll
@@ -258,7 +272,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc
   const int N = D.n1, nc = D.c;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* buf = tw + N;
-  const int lstr = N;
+  const int lstr = row_stride(N);
   const long long nsp = (long long)D.n2 * D.n3;
   const long long l0 = (long long)blk * LX;
   const long long V = D.V;
@@ -269,11 +283,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc
   DotAcc<T> acc;
   constexpr int U = 4;  // elements per lane kept in flight
   const int nq = LX * nc;
-  for (int q = warp_id(); q < nq; q += num_warps()) {
+  // work items (line, chunk of 32 U elements) spread evenly over the warps
+  const int nch = (N + 32 * U - 1) / (32 * U);
+  for (int it = warp_id(); it < nq * nch; it += num_warps()) {
+    const int q = it / nch;
     const int k = q % nc, l = q / nc;
     const long long line = l0 + l;
     if (line >= nsp) continue;
-    for (int x0 = lane_id(); x0 < N; x0 += 32 * U) {
+    {
+      const int x0 = (it - q * nch) * 32 * U + lane_id();
       T a[U], b[U], rho[U];
       uint8_t m[U];
 #pragma unroll
@@ -377,7 +395,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc
   const int N = D.n1, ns = D.s;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* buf = tw + N;
-  const int lstr = N;
+  const int lstr = row_stride(N);
   const long long nsp = (long long)D.n2 * D.n3;
   const long long l0 = (long long)blk * LX;
   load_twiddles<T>(tw, D.tw[0], N);
@@ -385,28 +403,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc
   __syncthreads();
   fft_lines<T, 1>(buf, D.ax[0], LX * ns / 2, lstr, tw, +1);
   const int cstride = (ns == 6) ? kCtabStride3 : kCtabStride2;
-  for (int l = warp_id(); l < LX; l += num_warps()) {
+  // every thread of the block takes voxels (consecutive x across a warp)
+  const int lgN = log2_if_pow2(N);
+  for (int e = threadIdx.x; e < LX * N; e += blockDim.x) {
+    const int l = lgN >= 0 ? e >> lgN : e / N;
+    const int x = e - l * N;
     const long long line = l0 + l;
     if (line >= nsp) continue;
-    for (int x = lane_id(); x < N; x += 32) {
-      const long long vox = line * N + x;
-      const long long row = D.phase ? (long long)D.phase[vox] : vox;
-      T C[24];
-      load_row<T>(D.ctab + row * cstride, C, ns == 6 ? 24 : 8);
-      T ev[6];
-      if (ns == 6) {
+    const long long vox = line * N + x;
+    const long long row = D.phase ? (long long)D.phase[vox] : vox;
+    T C[24];
+    load_row<T>(D.ctab + row * cstride, C, ns == 6 ? 24 : 8);
+    T ev[6];
+    if (ns == 6) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) ev[k] = packed<T>(buf, lstr, l * 6 + k, x);
-        hooke3<T>(C, ev);
+      for (int k = 0; k < 6; ++k) ev[k] = packed<T>(buf, lstr, l * 6 + k, x);
+      hooke3<T>(C, ev);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) packed<T>(buf, lstr, l * 6 + k, x) = ev[k];
-      } else {
+      for (int k = 0; k < 6; ++k) packed<T>(buf, lstr, l * 6 + k, x) = ev[k];
+    } else {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) ev[k] = packed<T>(buf, lstr, l * 3 + k, x);
-        hooke2<T>(C, ev);
+      for (int k = 0; k < 3; ++k) ev[k] = packed<T>(buf, lstr, l * 3 + k, x);
+      hooke2<T>(C, ev);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) packed<T>(buf, lstr, l * 3 + k, x) = ev[k];
-      }
+      for (int k = 0; k < 3; ++k) packed<T>(buf, lstr, l * 3 + k, x) = ev[k];
     }
   }
   __syncthreads();

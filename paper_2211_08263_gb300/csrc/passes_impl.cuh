@@ -48,8 +48,8 @@ void plan_geometry(Plan<T>& P) {
   g.blk_x = (int)((nsp + g.LX - 1) / g.LX);
   g.blk_xm = (int)((nsp + g.LXm - 1) / g.LXm);
   const size_t cs = sizeof(cplx<T>);
-  g.sm_x = (size_t)(D.n1 + (g.LX * D.c / 2) * D.n1) * cs;
-  g.sm_xm = (size_t)(D.n1 + (g.LXm * D.s / 2) * D.n1) * cs;
+  g.sm_x = (size_t)(D.n1 + (g.LX * D.c / 2) * row_stride(D.n1)) * cs;
+  g.sm_xm = (size_t)(D.n1 + (g.LXm * D.s / 2) * row_stride(D.n1)) * cs;
   // column passes: per axis and op, the widest tile (kx columns) whose every
   // radix stage fits the register batch and whose slots fit 64 KB of shared memory
   const int maxbx = sizeof(T) == 4 ? 8 : 4;
@@ -413,19 +413,19 @@ __global__ void __launch_bounds__(256) k_xplain(const Desc<T>* __restrict__ dd, 
     for (int e = threadIdx.x; e < LX * nc * N; e += blockDim.x) {
       const int x = e % N, q = e / N, k = q % nc, l = q / nc;
       const long long line = l0 + l;
-      packed<T>(buf, N, q, x) = line < nsp ? f[(long long)k * D.V + line * N + x] : (T)0;
+      packed<T>(buf, row_stride(N), q, x) = line < nsp ? f[(long long)k * D.V + line * N + x] : (T)0;
     }
     __syncthreads();
-    fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, N, tw, -1);
-    store_unpacked<T>(D, buf, N, LX * nc, l0, nc, nsp);
+    fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, row_stride(N), tw, -1);
+    store_unpacked<T>(D, buf, row_stride(N), LX * nc, l0, nc, nsp);
   } else {
-    load_packed<T>(D, buf, N, LX * nc, l0, nc, nsp);
+    load_packed<T>(D, buf, row_stride(N), LX * nc, l0, nc, nsp);
     __syncthreads();
-    fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, N, tw, +1);
+    fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, row_stride(N), tw, +1);
     for (int e = threadIdx.x; e < LX * nc * N; e += blockDim.x) {
       const int x = e % N, q = e / N, k = q % nc, l = q / nc;
       const long long line = l0 + l;
-      if (line < nsp) f[(long long)k * D.V + line * N + x] = packed<T>(buf, N, q, x);
+      if (line < nsp) f[(long long)k * D.V + line * N + x] = packed<T>(buf, row_stride(N), q, x);
     }
   }
 }
@@ -441,7 +441,7 @@ void launch_rfft3(const Plan<T>& P, int dir, int ncomp, int real_slot, cudaStrea
   while (lx > 1 && ((lx * ncomp) & 1)) --lx;
   if ((lx * ncomp) & 1) lx = 2;
   const int nb = (int)((nsp + lx - 1) / lx);
-  const size_t sm = (size_t)(D.n1 + (lx * ncomp / 2) * D.n1) * sizeof(cplx<T>);
+  const size_t sm = (size_t)(D.n1 + (lx * ncomp / 2) * row_stride(D.n1)) * sizeof(cplx<T>);
   const int axes[2] = {1, 2};
   const Launch<T, 0> L{P, nullptr};
   if (dir < 0) {
