@@ -220,8 +220,8 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    l0 = s.launch_count()
     s.profile(True)
+    l0 = s.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     ev0.record(stream)

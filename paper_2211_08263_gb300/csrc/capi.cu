@@ -1295,9 +1295,6 @@ extern "C" int wfft_profile_read(wfft_handle* h, int precision, int kind, long l
 
 extern "C" int wfft_launch_count(const wfft_handle* h, long long* launches) {
   if (!h || !launches) return fail(nullptr, WFFT_EINVAL, "null argument");
-  long long n = 0;
-  for (int p = 0; p < 2; ++p)
-    for (int k = 0; k < KK_NKIND; ++k) n += h->prof.launches[p][k];
-  *launches = n;
+  *launches = h->prof.lifetime;
   return WFFT_OK;
 }

@@ -21,6 +21,7 @@ enum KernelKind {
 struct Profiler {
   bool on = false;
   long long launches[2][KK_NKIND] = {};
+  long long lifetime = 0;  // every launch since creation (not reset by profiling)
   long long timed[2][KK_NKIND] = {};
   double ms[2][KK_NKIND] = {};
   double bytes[2][KK_NKIND] = {};
@@ -77,6 +78,7 @@ inline void prof_launch(int prec, int kind, double bytes, double flops, cudaStre
     return;
   }
   p->launches[prec][kind] += 1;
+  p->lifetime += 1;
   if (!p->on) {
     launch();
     return;

@@ -185,3 +185,24 @@ def test_checkpoint_resume_is_bitwise():
         c.step(prob.U[k])
     for x, y in zip(a.get_state(), c.get_state()):
         assert np.array_equal(x, y)
+
+
+def test_launch_count_is_a_lifetime_counter_across_profiling():
+    """wfft_launch_count keeps counting through wfft_profile(1), which resets only
+    the per-kind totals; the per-kind launches of a profiled step add up to the
+    lifetime counter's increase."""
+    torch_cuda()
+    wfft = solver_lib()
+    prob = inputs.random_problem(np.random.default_rng(4), 3, (16, 12, 10), nphase=2, mask_width=2, nsteps=3)
+    s = wfft.Solver.from_problem(prob, options=wfft.default_options(precision=wfft.MIXED))
+    s.step(prob.U[0])
+    n0 = s.launch_count()
+    assert n0 > 0
+    s.profile(True)
+    s.step(prob.U[1])
+    n1 = s.launch_count()
+    prof = s.profile_read()
+    s.profile(False)
+    assert n1 > n0
+    assert sum(d["launches"] for d in prof.values()) == n1 - n0
+    s.close()
