@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the launch-bound C1 (64^2) measurement")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
     return ap.parse_args()
 
@@ -199,8 +200,12 @@ def train_warm_start(wfft, args, stream):
     return blob, info
 
 
+PROF_STEPS = 3
+
+
 def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None):
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     _, prec, warm = MODES[mode]
     opt = wfft.default_options(precision=getattr(wfft, prec), tol=1e-10, maxit=500, check_every=4,
                                warm_start=getattr(wfft, warm))
@@ -220,7 +225,6 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    s.profile(True)
     l0 = s.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
@@ -233,6 +237,11 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
         torch.distributed.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count() - l0
+    # per-kernel CUDA-event times (for the kernel table and the roofline) on the steps
+    # after the timed ones: event pairs around every launch would perturb the timed region
+    s.profile(True)
+    for n in range(W + K, W + K + PROF_STEPS):
+        s.step(prob.U[n])
     prof = s.profile_read()
     s.profile(False)
     res = {"ms_total": ms, "iters": sum(i["iters"] for i in infos),
@@ -297,6 +306,37 @@ def kernel_table(prof, hbm_peak, total_ms):
     return out
 
 
+def small_grid(wfft, torch, steps=50):
+    """The launch-bound end of the workloads: C1 (2-D plane strain 64 x 64, homogeneous steel,
+    sin^2 strip load, FP64 to 1e-10), microseconds per Newmark step with the PCG iteration
+    blocks as CUDA graphs and as plain launches."""
+    from paper_2211_08263_gb300 import inputs
+    prob = inputs.config_c1(nsteps=steps)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"workload": "C1: 2-D plane strain 64x64, E 200 GPa, nu 0.3, rho 7800, strip x<3 u_x = 1e-6 "
+                       "sin^2(pi t / 2e-5), dt 2e-7 s, %d steps, FP64, tol 1e-10" % steps}
+    for g in (1, 0):
+        s = wfft.Solver.from_problem(prob, options=wfft.default_options(precision=wfft.FP64, tol=1e-10, use_graphs=g),
+                                     stream=stream.cuda_stream)
+        for k in range(5):
+            s.step(prob.U[k])
+        s.set_state()
+        torch.cuda.synchronize()
+        l0 = s.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        its = sum(s.step(prob.U[k])["iters"] for k in range(steps))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        key = "graphs" if g else "plain"
+        out["us_per_step_" + key] = 1e3 * ev0.elapsed_time(ev1) / steps
+        out["kernels_per_step"] = (s.launch_count() - l0) / steps
+        out["krylov_iters_per_step"] = its / steps
+        s.close()
+    return out
+
+
 def cpu_oracle_iteration(prob, reps=1):
     """One FP64 oracle PCG iteration (operator + preconditioner + updates) on the workload."""
     import numpy as np
@@ -348,7 +388,7 @@ def main():
     rank, world, local = dist_env()
     from paper_2211_08263_gb300 import inputs
     W, K = args.warmup, args.steps
-    prob = inputs.config_c3(nsteps=W + K, n=args.n)
+    prob = inputs.config_c3(nsteps=W + K + PROF_STEPS, n=args.n)
     if args.impl == "reference":
         return run_reference(args, prob, rank, world)
 
@@ -417,13 +457,16 @@ def main():
                        "l2": "inputs larger than L2 (every field >= 64 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "modes": modes_out, "roofline": rl,
-            "kernels": kernel_table(head["profile"], hbm_peak, head["ms_total"]),
+            "kernels": kernel_table(head["profile"], hbm_peak,
+                                    sum(d["ms"] for d in head["profile"].values())),
             "gpu_launches": head["launches"], "clocks": clk}
     if learned:
         line["learned"] = learned
         nr = net_roofline(results["learned"]["profile"])
         if nr:
             line["roofline_net"] = nr
+    if not args.no_small:
+        line["small_grid"] = small_grid(wfft, torch)
     if "e2e_s" in head:
         line["e2e"] = {"value": V * head["e2e_iters"] * world / head["e2e_s"], "unit": UNIT,
                        "h2d_bytes_per_step": 24, "d2h_bytes_per_step": head["d2h_bytes"],

@@ -81,6 +81,8 @@ typedef struct {
   int max_sweeps;    /* mixed: cap on FP64 refinement sweeps per solve */
   int check_every;   /* iterations between host reads of the device convergence flag */
   int watchdog_iters;/* hard cap on iterations per step, across sweeps (0 = 4*maxit) */
+  int use_graphs;    /* 1: each block of check_every PCG iterations is one CUDA graph launch (captured
+                        once per handle on an internal stream; not while profiling is on); 0: plain launches */
 } wfft_options;
 
 typedef struct {
@@ -95,7 +97,7 @@ typedef struct {
 } wfft_step_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-10, maxit 1000, WARM_PREV, inner_tol 1e-5,
-   max_sweeps 20, check_every 4. */
+   max_sweeps 20, check_every 4, use_graphs 1. */
 WFFT_API int wfft_default_options(wfft_options* opt);
 
 /*

@@ -48,6 +48,10 @@ struct wfft_handle {
   double U_prev[3] = {0, 0, 0};
   double cbar[21] = {0};
   double rhobar = 0;
+  // CUDA graphs of one block of check_every PCG iterations, per precision (captured lazily)
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+  long long chunk_launches[2] = {0, 0};
   NetDev* net = nullptr;    // learned warm start (wfft_set_model)
   NetWork nw;
   float* delta = nullptr;   // FP64 handles: FP32 warm-start increment
@@ -205,6 +209,7 @@ extern "C" int wfft_default_options(wfft_options* o) {
   o->inner_tol = 1e-5;
   o->max_sweeps = 20;
   o->check_every = 4;
+  o->use_graphs = 1;
   o->watchdog_iters = 0;
   return WFFT_OK;
 }
@@ -441,6 +446,9 @@ extern "C" void wfft_destroy(wfft_handle* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  for (int k = 0; k < 2; ++k)
+    if (h->chunk[k]) cudaGraphExecDestroy(h->chunk[k]);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (void* p : h->dev_allocs) cudaFree(p);
   net_free(h->net);
   net_work_free(&h->nw);
@@ -527,20 +535,65 @@ static int read_scalars(wfft_handle* h) {
   return WFFT_OK;
 }
 
+// One block of check_every PCG iterations on stream st (every kernel returns at once
+// when the solve's done flag is set, so a block may overrun convergence harmlessly).
+template <typename T>
+static void pcg_chunk(wfft_handle* h, Plan<T>& P, Scalars* sc, cudaStream_t st) {
+  const Desc<T>& D = P.h;
+  const int op = D.opAxis;
+  for (int i = 0; i < h->opt.check_every; ++i) {
+    launch_apply<T>(P, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, st);
+    launch_fin(sc, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_ALPHA, nullptr, st);
+    launch_precond<T>(P, PRE_RUPD, SL_R, SL_Z, 1, st);
+    launch_fin(sc, D.part[PT_A], P.g.blk_x, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_BETA, nullptr, st);
+  }
+}
+
+// Launch one block of iterations, as a CUDA graph when enabled: the block is captured
+// once per handle and precision on the handle's internal stream (capture needs a
+// stream other than the legacy default one) and replayed on the solve's stream.
+// Every kernel argument is a pointer to device-resident descriptors and scalars,
+// so a replay computes exactly what direct launches would.
+template <typename T>
+static int pcg_chunk_launch(wfft_handle* h, Plan<T>& P, Scalars* sc, int which) {
+  if (!h->opt.use_graphs || h->prof.on) {
+    pcg_chunk<T>(h, P, sc, h->st);
+    return WFFT_OK;
+  }
+  if (!h->chunk[which]) {
+    if (!h->cap_st) CKH(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    const long long before = h->prof.lifetime;
+    cudaGraph_t g = nullptr;
+    CKH(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+    pcg_chunk<T>(h, P, sc, h->cap_st);
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_st, &g);
+    if (ec != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return fail(h, WFFT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->chunk[which], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->chunk[which] = nullptr;
+      return fail(h, WFFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    }
+    // the capture counted the block's kernels once; they are counted again per replay
+    h->chunk_launches[which] = h->prof.lifetime - before;
+    h->prof.lifetime = before;
+  }
+  CKH(h, cudaGraphLaunch(h->chunk[which], h->st));
+  h->prof.lifetime += h->chunk_launches[which];
+  return WFFT_OK;
+}
+
 // PCG iterations on plan P (scalars sc) until its done flag is set; counts in *iters.
 template <typename T>
 static int pcg_loop(wfft_handle* h, Plan<T>& P, Scalars* sc, int which, int budget, int* iters) {
-  const Desc<T>& D = P.h;
-  const int op = D.opAxis;
   int launched = 0;
   for (;;) {
-    for (int i = 0; i < h->opt.check_every; ++i) {
-      launch_apply<T>(P, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, h->st);
-      launch_fin(sc, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_ALPHA, nullptr, h->st);
-      launch_precond<T>(P, PRE_RUPD, SL_R, SL_Z, 1, h->st);
-      launch_fin(sc, D.part[PT_A], P.g.blk_x, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_BETA, nullptr, h->st);
-      ++launched;
-    }
+    int rc0 = pcg_chunk_launch<T>(h, P, sc, which);
+    if (rc0) return rc0;
+    launched += h->opt.check_every;
     CKH(h, cudaGetLastError());
     int rc = read_scalars(h);
     if (rc) return rc;

@@ -206,3 +206,27 @@ def test_launch_count_is_a_lifetime_counter_across_profiling():
     assert n1 > n0
     assert sum(d["launches"] for d in prof.values()) == n1 - n0
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cuda_graph_blocks_match_plain_launches_bitwise(precision):
+    """use_graphs replays a captured block of check_every PCG iterations; it must
+    compute exactly what plain launches compute (same kernels, same arguments),
+    with the same iteration and kernel-launch counts, on the legacy default stream
+    and on a user stream."""
+    torch = torch_cuda()
+    wfft = solver_lib()
+    prob = inputs.random_problem(np.random.default_rng(12), 3, (20, 16, 12), nphase=3, mask_width=2, nsteps=4)
+    side = torch.cuda.Stream()
+    for stream in (0, side.cuda_stream):
+        runs = []
+        for g in (1, 0):
+            s = wfft.Solver.from_problem(prob, options=wfft.default_options(precision=precision, use_graphs=g),
+                                         stream=stream)
+            n0 = s.launch_count()
+            its = [s.step(prob.U[k])["iters"] for k in range(prob.nsteps)]
+            runs.append((s.get_state()[:3], its, s.launch_count() - n0))
+            s.close()
+        (sa, ia, la), (sb, ib, lb) = runs
+        assert all(np.array_equal(x, y) for x, y in zip(sa, sb))
+        assert ia == ib and la == lb
