@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the launch-bound C1 (64^2) measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT plans (no wfft_autotune)")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
     return ap.parse_args()
 
@@ -203,7 +204,7 @@ def train_warm_start(wfft, args, stream):
 PROF_STEPS = 3
 
 
-def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None):
+def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None, autotune=True):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     _, prec, warm = MODES[mode]
@@ -219,6 +220,7 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
         return sv
 
     s = make()
+    tuned = s.autotune(3) if autotune else None
     for n in range(W):
         s.step(prob.U[n])
     torch.cuda.synchronize()
@@ -247,12 +249,15 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
     res = {"ms_total": ms, "iters": sum(i["iters"] for i in infos),
            "outer_applies": sum(i["outer_applies"] for i in infos),
            "sweeps": sum(i["sweeps"] for i in infos), "rel_res_max": max(i["rel_res"] for i in infos),
-           "launches": launches, "profile": prof, "iters_per_step": [i["iters"] for i in infos]}
+           "launches": launches, "profile": prof, "iters_per_step": [i["iters"] for i in infos],
+           "autotune_changed": tuned}
     if e2e:
         # end to end through the C ABI: U(t_n) from host memory in, the displacement
         # field u_n copied back to pinned host memory after every step
         host_u = torch.empty(s.shape, dtype=torch.float64, pin_memory=True).numpy()
         s2 = make()
+        if autotune:
+            s2.autotune(3)  # the plan cached by the first handle: no timing
         for n in range(W):
             s2.step(prob.U[n])
         torch.cuda.synchronize()
@@ -415,7 +420,7 @@ def main():
         if m == modes[0]:
             clocks.start()
         results[m] = run_mode(wfft, torch, prob, m, blob, W, K, world, e2e=(m == modes[0] and not args.no_e2e),
-                              inner_tol=args.inner_tol)
+                              inner_tol=args.inner_tol, autotune=not args.no_autotune)
         if m == modes[0]:
             clk = clocks.stop()
     head = results[modes[0]]
@@ -436,6 +441,7 @@ def main():
                         "voxel_iters_per_s": V * r["iters"] / (r["ms_total"] * 1e-3),
                         "krylov_iters_per_step": r["iters"] / K, "fp64_applies_per_step": r["outer_applies"] / K,
                         "sweeps_per_step": r["sweeps"] / K, "max_rel_res": r["rel_res_max"],
+                        "autotune_changed": r["autotune_changed"],
                         "iters_per_step": r["iters_per_step"]}
     rl = roofline(head["profile"], V, hbm_peak, peak_kind)
     traffic_file = os.path.join(ROOT, "profiles", "ncu_traffic.json")

@@ -270,6 +270,22 @@ WFFT_API int wfft_net_forward(const void* blob, size_t bytes, const int n[3], co
 WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], int c, const float* x,
                                 const float* target, const unsigned char* mask, float* grad, double* loss);
 
+/*
+ * Autotuner (not in the paper).  Times, on this handle's grid and device, every
+ * radix decomposition the FFT stages support for each axis (the power-of-two part
+ * as radix-8 / radix-4 / one radix-2 stage in any mix) and then every feasible
+ * column-tile width of each column pass, one choice at a time, each candidate by
+ * `reps` (0: 3) operator + preconditioner applications; keeps the fastest plan for
+ * the handle's solve precision(s) and caches it per (precision, grid, device) for
+ * later handles of the process (which then need no timing).  Plans that would need
+ * more partial-sum slots than the handle allocated are skipped.  Only speed
+ * changes: results may differ from the default plan in the last bits (a different
+ * FFT rounding order), never beyond the solver tolerance.  *changed (optional):
+ * how many choices differ from the handle's previous plan.  Overwrites the Krylov
+ * scratch vectors (not the state); synchronises the stream; EINVAL while profiling.
+ */
+WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
+
 /* Kernel kinds of the launch accounting (wfft_profile_read). */
 #define WFFT_K_XFWD_PLAIN 0   /* x-axis real->half-spectrum pass */
 #define WFFT_K_XFWD_PUPD 1    /* ... fused with p = z + beta p */

@@ -7,6 +7,9 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1350,4 +1353,151 @@ extern "C" int wfft_launch_count(const wfft_handle* h, long long* launches) {
   if (!h || !launches) return fail(nullptr, WFFT_EINVAL, "null argument");
   *launches = h->prof.lifetime;
   return WFFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: radix decomposition of each axis and column-tile width of each column
+// pass, timed on the handle's own grid and device
+// ---------------------------------------------------------------------------
+namespace {
+struct TunedPlan {
+  AxisPlan ax[3];
+  int bx[3][5];
+};
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, TunedPlan> g_tuned;  // (precision, ndim, N1, N2, N3, device)
+
+// one operator application + one preconditioner application on the Krylov scratch vectors
+template <typename T>
+float time_iteration(wfft_handle* h, Plan<T>& P, int reps) {
+  launch_set_done(P.h.sc, 0, h->st);
+  launch_apply<T>(P, PRE_PLAIN, SL_P, POST_APPLY, SL_Q, 1, 0, h->st);
+  cudaEventRecord(h->ev0, h->st);
+  for (int r = 0; r < reps; ++r) {
+    launch_apply<T>(P, PRE_PLAIN, SL_P, POST_APPLY, SL_Q, 1, 0, h->st);
+    launch_precond<T>(P, PRE_PLAIN, SL_Q, SL_Z, 1, h->st);
+  }
+  cudaEventRecord(h->ev1, h->st);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(h->ev1) != cudaSuccess || cudaEventElapsedTime(&ms, h->ev0, h->ev1) != cudaSuccess)
+    ms = 1e30f;
+  return ms;
+}
+
+template <typename T>
+bool ops_of_axis(const Desc<T>& D, int axis, int op) {
+  if (axis == D.opAxis) return op == OP_GRAD || op == OP_DIV || op == OP_PREC;
+  if (axis == D.midAxis) return op == OP_FWD || op == OP_INV;
+  return false;
+}
+
+template <typename T>
+int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
+  Desc<T>& D = P.h;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::array<int, 6> key{prec, h->ndim, h->n[0], h->n[1], h->n[2], dev};
+  TunedPlan before;
+  for (int a = 0; a < 3; ++a) {
+    before.ax[a] = D.ax[a];
+    for (int op = 0; op < 5; ++op) before.bx[a][op] = P.g.bx[a][op];
+  }
+  TunedPlan best;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    // 1. radix decomposition, axis by axis
+    for (int a = 0; a < 3; ++a) {
+      const std::vector<AxisPlan> cands = factor_candidates(h->n[a]);
+      if (h->n[a] == 1 || cands.size() < 2) continue;
+      AxisPlan keep = D.ax[a];
+      float tbest = 1e30f;
+      for (const AxisPlan& c : cands) {
+        D.ax[a] = c;
+        plan_geometry<T>(P);
+        if (P.g.max_blocks > h->nparts) continue;  // partial-sum arrays are sized at creation
+        CKH(h, upload_desc(P));
+        const float t = time_iteration<T>(h, P, reps);
+        if (t < tbest) {
+          tbest = t;
+          keep = c;
+        }
+      }
+      D.ax[a] = keep;
+      plan_geometry<T>(P);
+      CKH(h, upload_desc(P));
+    }
+    // 2. column-tile widths, pass by pass
+    for (int a = 1; a <= 2; ++a)
+      for (int op = 0; op < 5; ++op) {
+        if (!ops_of_axis(D, a, op)) continue;
+        int keep = P.g.bx[a][op];
+        float tbest = 1e30f;
+        for (int bx = 1; bx <= 8; bx <<= 1) {
+          if (!col_bx_feasible<T>(P, a, op, bx)) continue;
+          set_col_bx<T>(P, a, op, bx);
+          const float t = time_iteration<T>(h, P, reps);
+          if (t < tbest) {
+            tbest = t;
+            keep = bx;
+          }
+        }
+        set_col_bx<T>(P, a, op, keep);
+      }
+    for (int a = 0; a < 3; ++a) {
+      best.ax[a] = D.ax[a];
+      for (int op = 0; op < 5; ++op) best.bx[a][op] = P.g.bx[a][op];
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+  } else {
+    for (int a = 0; a < 3; ++a) D.ax[a] = best.ax[a];
+    plan_geometry<T>(P);
+    if (P.g.max_blocks > h->nparts) {
+      for (int a = 0; a < 3; ++a) D.ax[a] = before.ax[a];
+      plan_geometry<T>(P);
+    } else {
+      for (int a = 1; a <= 2; ++a)
+        for (int op = 0; op < 5; ++op)
+          if (ops_of_axis(D, a, op) && col_bx_feasible<T>(P, a, op, best.bx[a][op]))
+            set_col_bx<T>(P, a, op, best.bx[a][op]);
+    }
+    CKH(h, upload_desc(P));
+  }
+  for (int a = 0; a < 3; ++a) {
+    bool same = D.ax[a].n == before.ax[a].n;
+    for (int r = 0; r < 6; ++r) same = same && D.ax[a].cnt[r] == before.ax[a].cnt[r];
+    if (!same) ++*changed;
+    for (int op = 0; op < 5; ++op)
+      if (ops_of_axis(D, a, op) && P.g.bx[a][op] != before.bx[a][op]) ++*changed;
+  }
+  CKH(h, cudaStreamSynchronize(h->st));
+  return WFFT_OK;
+}
+}  // namespace
+
+extern "C" int wfft_autotune(wfft_handle* h, int reps, int* changed) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (h->prof.on) return fail(h, WFFT_EINVAL, "switch profiling off before tuning");
+  ProfScope ps_(h);
+  int ch = 0;
+  const int r = reps > 0 ? reps : 3;
+  CKH(h, cudaStreamSynchronize(h->st));
+  int rc = tune_plan<double>(h, h->P64, 0, r, &ch);
+  if (rc == WFFT_OK && h->opt.precision == WFFT_MIXED) rc = tune_plan<float>(h, h->P32, 1, r, &ch);
+  // graphs captured with the old plan are stale
+  for (int k = 0; k < 2; ++k)
+    if (h->chunk[k]) {
+      cudaGraphExecDestroy(h->chunk[k]);
+      h->chunk[k] = nullptr;
+    }
+  if (changed) *changed = ch;
+  return rc;
 }

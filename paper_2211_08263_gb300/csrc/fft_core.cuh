@@ -146,9 +146,9 @@ __host__ __device__ __forceinline__ constexpr int rowpad(int e) { return e + (e 
 __host__ __device__ __forceinline__ constexpr int row_stride(int N) { return N + (N >> 3) + 1; }
 
 // One in-place Stockham stage over `nlines` lines of length N.
-// Row tiles (ES == 1): element e of line l at buf[l * lstride + rowpad(e)];
+// Row tiles (NL == 0, ES == 1): element e of line l at buf[l * lstride + rowpad(e)];
 // consecutive threads take consecutive butterflies of a line.  Column tiles
-// (ES > 1, NL lines, both compile-time): element e of line l at buf[l + e * ES];
+// (NL > 0 lines and element stride ES, both compile-time): element e of line l at buf[l + e * ES];
 // consecutive threads take consecutive lines.  Compile-time strides and line
 // counts and shifts for power-of-two N and Ns keep the index arithmetic off the
 // integer divider.
@@ -156,7 +156,7 @@ template <typename T, int R, int ES, int NL>
 __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int lstride, int Ns, const cplx<T>* tw,
                                           int sgn) {
   constexpr int NB = NbOf<T, R>::v;
-  constexpr bool LF = ES > 1;
+  constexpr bool LF = NL > 0;  // column tile (a 1-column tile has ES = 1)
   const int nb = N / R;
   const int nl = LF ? NL : nlines;
   const int total = nb * nl;
@@ -228,8 +228,8 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
 // Stages are applied radix by radix (8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
 // formulation is valid for any order of the radices, and one loop per radix
 // keeps each stage's registers apart.  ES = 1: row tiles with line stride
-// `lstride` (nlines at run time); ES > 1: column tiles (line stride 1, element
-// stride ES, NL lines).  Must be called by every thread of the block (barriers).
+// `lstride` (nlines at run time), NL = 0; NL > 0: column tiles (line stride 1,
+// element stride ES, NL lines).  Must be called by every thread of the block (barriers).
 template <typename T, int ES, int NL = 0>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int nlines, int lstride, const cplx<T>* tw,
                                           int sgn) {

@@ -36,6 +36,27 @@ static inline bool factorize(int n, AxisPlan& pl) {
   return m == 1;
 }
 
+// Every decomposition of n the FFT stages support: the power-of-two part as radix-8,
+// radix-4 and at most one radix-2 stage in any mix, the odd part as 3s, 5s and 7s
+// (the stage order is fixed: 8s, 4s, 2s, 3s, 5s, 7s).  Empty if n is not supported.
+static inline std::vector<AxisPlan> factor_candidates(int n) {
+  std::vector<AxisPlan> out;
+  AxisPlan base;
+  if (!factorize(n, base)) return out;
+  const int e2 = 3 * base.cnt[0] + 2 * base.cnt[1] + base.cnt[2];
+  for (int n8 = 0; 3 * n8 <= e2; ++n8)
+    for (int n2 = 0; n2 <= 1; ++n2) {
+      const int rest = e2 - 3 * n8 - n2;
+      if (rest < 0 || (rest & 1)) continue;
+      AxisPlan c = base;
+      c.cnt[0] = n8;
+      c.cnt[1] = rest / 2;
+      c.cnt[2] = n2;
+      out.push_back(c);
+    }
+  return out;
+}
+
 // W_n^m = exp(-2 pi i m / n), m = 0..n-1, evaluated in long double on the host
 template <typename T>
 static inline void fill_twiddles(cplx<T>* w, int n) {

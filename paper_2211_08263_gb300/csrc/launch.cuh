@@ -48,6 +48,10 @@ struct BatchLaunch {
 // Compute tile geometry from h's sizes (elements budget per block).
 template <typename T>
 void plan_geometry(Plan<T>& P);
+template <typename T>
+bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx);
+template <typename T>
+void set_col_bx(Plan<T>& P, int axis, int op, int bx);
 
 // q(out_slot) = [P] A in, where `pre` selects the fused x-pass prologue
 // (PRE_PLAIN reads in_slot) and `post` the epilogue (POST_APPLY / POST_RESID).

@@ -78,6 +78,35 @@ void plan_geometry(Plan<T>& P) {
   }
 }
 
+// Column-tile width bx of pass (axis, op): feasible when every radix stage fits the
+// per-thread register batch and the tile fits 64 KB of shared memory (the rule
+// plan_geometry applies to its default choice); set_col_bx applies it to the plan.
+template <typename T>
+bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx) {
+  const Desc<T>& D = P.h;
+  const int N = axis == 1 ? D.n2 : D.n3;
+  const bool plain = op == OP_FWD || op == OP_INV;
+  const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
+  const int thr = plain ? kColThreadsPlain : kColThreadsOp;
+  const int maxbx = plain && sizeof(T) == 4 ? 8 : 4;
+  if (bx < 1 || bx > maxbx || (bx & (bx - 1))) return false;
+  return (long long)ns * bx * N <= max_tile_elems<T>(D.ax[axis], thr) &&
+         (size_t)ns * bx * N * sizeof(cplx<T>) <= 64 * 1024;
+}
+
+template <typename T>
+void set_col_bx(Plan<T>& P, int axis, int op, int bx) {
+  const Desc<T>& D = P.h;
+  const int N = axis == 1 ? D.n2 : D.n3;
+  const int nouter = axis == 1 ? D.n3 : D.n2;
+  const bool plain = op == OP_FWD || op == OP_INV;
+  const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
+  P.g.bx[axis][op] = bx;
+  P.g.blk_col[axis][op] = ((D.nh + bx - 1) / bx) * nouter;
+  P.g.sm_col[axis][op] = (size_t)(N + ns * bx * N) * sizeof(cplx<T>);
+  P.g.max_blocks = std::max(P.g.max_blocks, P.g.blk_col[axis][op]);
+}
+
 // ---------------------------------------------------------------------------
 // algorithmic cost model of one launch (compulsory DRAM bytes: every input read
 // once and every output written once, spectra at their unpadded size; flops:
@@ -503,6 +532,8 @@ cudaError_t init_kernel_attributes_impl() {
 // Single-instance kernels and the shared host helpers.
 #define WFFT_INSTANTIATE(T)                                                                                  \
   template void plan_geometry<T>(Plan<T>&);                                                                  \
+  template bool col_bx_feasible<T>(const Plan<T>&, int, int, int);                                          \
+  template void set_col_bx<T>(Plan<T>&, int, int, int);                                                     \
   template void launch_apply_impl<T, 0>(const Plan<T>&, int, int, int, int, int, int, cudaStream_t,          \
                                         const BatchLaunch<T>*);                                              \
   template void launch_precond_impl<T, 0>(const Plan<T>&, int, int, int, int, cudaStream_t,                  \

@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     lib.wfft_profile.argtypes = [vp, i]
     lib.wfft_profile_read.argtypes = [vp, i, i, P(C.c_longlong), P(C.c_longlong), P(d), P(d), P(d)]
     lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
+    lib.wfft_autotune.argtypes = [vp, i, P(i)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
     lib.wfft_model_bytes.argtypes = [i]
     lib.wfft_model_bytes.restype = C.c_size_t
@@ -237,6 +238,13 @@ class Solver:
 
     def rfft3(self, inp, out, precision: int = FP64, direction: int = -1, ncomp: int = 1):
         self._check(self.lib.wfft_rfft3(self.h, precision, direction, ncomp, _dptr(inp), _dptr(out)))
+
+    def autotune(self, reps: int = 3) -> int:
+        """Time and keep the fastest radix decompositions and column-tile widths
+        (wfft_autotune); returns how many choices changed."""
+        ch = C.c_int()
+        self._check(self.lib.wfft_autotune(self.h, int(reps), C.byref(ch)))
+        return ch.value
 
     # ---- learned warm start
     def set_model(self, blob: Optional[np.ndarray]):

@@ -230,3 +230,30 @@ def test_cuda_graph_blocks_match_plain_launches_bitwise(precision):
         (sa, ia, la), (sb, ib, lb) = runs
         assert all(np.array_equal(x, y) for x, y in zip(sa, sb))
         assert ia == ib and la == lb
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-12, 1e-10), (1, 1e-10, 1e-6)])
+def test_autotuned_plan_keeps_the_results(precision, tol, bar):
+    """wfft_autotune may pick other radix decompositions and column-tile widths; the
+    steps must still agree with the default plan and the oracle within the solver
+    bars, and a second handle of the same grid takes the cached plan."""
+    from oracle import newmark
+    torch_cuda()
+    wfft = solver_lib()
+    prob = inputs.random_problem(np.random.default_rng(21), 3, (32, 24, 16), nphase=3, mask_width=2, nsteps=3)
+    opt = lambda: wfft.default_options(precision=precision, tol=tol)
+    tuned = wfft.Solver.from_problem(prob, options=opt())
+    changed = tuned.autotune(2)
+    plain = wfft.Solver.from_problem(prob, options=opt())
+    again = wfft.Solver.from_problem(prob, options=opt())
+    assert again.autotune(2) == changed
+    for k in range(prob.nsteps):
+        for s in (tuned, plain, again):
+            assert s.step(prob.U[k])["status"] == 0
+    ut, up, ua = (s.get_state()[0] for s in (tuned, plain, again))
+    assert np.array_equal(ut, ua)
+    assert rel(ut, up) < bar
+    so, _ = newmark.oracle_from_problem(prob, tol=1e-13).run(prob.U)
+    assert rel(oracle_field(prob, ut), so.u) < bar
+    for s in (tuned, plain, again):
+        s.close()
