@@ -395,3 +395,91 @@ def test_conv_oracle_matches_direct_sum_and_finite_differences():
         xm[idx] -= eps
         fd = (loss(params, xp) - loss(params, xm)) / (2 * eps)
         assert abs(fd - gx[idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------
+# explicit central-difference scheme (Sec. 2.3)
+# --------------------------------------------------------------------------
+
+def _iso_medium(shape, h, E=200e9, nu=0.3, rho=7800.0):
+    C = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(inputs.isotropic_voigt(E, nu)))
+    d = len(shape)
+    L = tuple(shape[d - 1 - i] * h for i in range(d))
+    return medium.homogeneous_medium(d, shape, L, C, rho), C
+
+
+def test_explicit_plane_wave_follows_the_central_difference_recurrence():
+    """A longitudinal Fourier mode u = cos(k x1) e1 in a homogeneous isotropic
+    medium (spectral derivatives exact for |m| < N/2): with v0 = 0 and a0 = -w^2 u0,
+    beta = 0, gamma = 1/2 gives u_n = cos(n W dt) u0 with cos(W dt) = 1 - (w dt)^2/2."""
+    from oracle import explicit
+    E, nu, rho, h = 200e9, 0.3, 7800.0, 1e-3
+    shape = (4, 4, 16)
+    med, _ = _iso_medium(shape, h, E, nu, rho)
+    lam, mu = analytic.lame(E, nu)
+    cL = np.sqrt((lam + 2 * mu) / rho)
+    k = 2 * np.pi * 3 / (16 * h)
+    w = cL * k
+    x1 = (np.arange(16) + 0.5) * h
+    u0 = np.zeros((3,) + shape)
+    u0[0] = np.cos(k * x1)[None, None, :]
+    dt = 0.5 * explicit.stable_dt(med)
+    nm = explicit.ExplicitOracle(med, np.zeros((3,) + shape, bool), dt)
+    s = newmark.State(u0.copy(), np.zeros_like(u0), -w * w * u0)
+    n = 50
+    s, _ = nm.run(np.zeros((n, 3)), state=s)
+    W = np.arccos(1 - 0.5 * (w * dt) ** 2) / dt
+    assert rel(s.u, np.cos(n * W * dt) * u0) < 1e-11
+
+
+def test_explicit_step_matches_dense_operator_and_enforces_gamma_velocity():
+    """One step on a random heterogeneous medium from a random state: the update of u
+    is the Taylor formula, off Gamma rho a_n = -K u_n with K the assembled dense
+    operator (Trefethen differentiation matrices, independent of the FFTs), on Gamma
+    v_n = Udot, and the reaction equals sum rho a_n."""
+    from oracle import explicit
+    rng = np.random.default_rng(71)
+    prob = inputs.random_problem(rng, 3, (5, 4, 3), nphase=3, mask_width=1, nsteps=1)
+    med = medium.medium_from_problem(prob)
+    mask = medium.mask_to_oracle(prob)
+    shape = (3,) + tuple(med.shape)
+    s0 = newmark.State(*(1e-6 * rng.standard_normal(shape) for _ in range(3)))
+    dt = 0.3 * explicit.stable_dt(med)
+    Udot = np.array([1e-3, -2e-3, 5e-4])
+    nm = explicit.ExplicitOracle(med, mask, dt)
+    s1, react = nm.step(s0, Udot)
+    assert rel(s1.u, s0.u + dt * s0.v + 0.5 * dt * dt * s0.a) < 1e-15
+    A = dense.dense_operator(med, 1.0)
+    rho = np.tile(med.rho.reshape(-1), 3)
+    K = A - np.diag(rho)
+    ra = (rho * s1.a.reshape(-1))
+    free = ~mask.reshape(-1)
+    assert rel(ra[free], -(K @ s1.u.reshape(-1))[free]) < 1e-10
+    for j in range(3):
+        # v_n = v_b + (Udot - v_b): exact up to the rounding of v_b (|v_b| >> |Udot| here)
+        assert np.abs(s1.v[j][mask[j]] - Udot[j]).max() <= 1e-14 * max(1.0, np.abs(s1.v).max())
+        assert abs(react[j] - float((med.rho * s1.a[j]).sum())) <= 1e-9 * abs(react[j])
+
+
+def test_explicit_stable_increment_closed_form_and_stability():
+    """Isotropic homogeneous medium: omega_max = c_L |xi| at xi_i = N_i pi / L_i, so
+    dt_max = 2 / (c_L |xi|).  The scheme stays bounded at dt_max (the discrete
+    operator's top frequency, Nyquist multiplier 0, is below N pi / L) and blows up
+    at 1.5 dt_max."""
+    from oracle import explicit
+    E, nu, rho, h = 200e9, 0.3, 7800.0, 1e-3
+    shape = (4, 6, 16)
+    med, _ = _iso_medium(shape, h, E, nu, rho)
+    lam, mu = analytic.lame(E, nu)
+    cL = np.sqrt((lam + 2 * mu) / rho)
+    xi = np.pi * np.sqrt(sum((n / (n * h)) ** 2 for n in shape))
+    assert abs(explicit.stable_dt(med) - 2 / (cL * xi)) <= 1e-14 * 2 / (cL * xi)
+    rng = np.random.default_rng(72)
+    u0 = rng.standard_normal((3,) + shape)
+    amp = {}
+    for f in (1.0, 1.5):
+        nm = explicit.ExplicitOracle(med, np.zeros((3,) + shape, bool), f * explicit.stable_dt(med))
+        s = newmark.State(u0.copy(), np.zeros_like(u0), np.zeros_like(u0))
+        s, _ = nm.run(np.zeros((60, 3)), state=s)
+        amp[f] = np.abs(s.u).max() / np.abs(u0).max()
+    assert amp[1.0] < 5.0 and amp[1.5] > 1e6, amp
