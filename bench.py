@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the launch-bound C1 (64^2) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT plans (no wfft_autotune)")
+    ap.add_argument("--no-explicit", action="store_true", help="skip the explicit-scheme measurement")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
     return ap.parse_args()
 
@@ -342,6 +343,36 @@ def small_grid(wfft, torch, steps=50):
     return out
 
 
+def explicit_scheme(wfft, torch, prob, W, K):
+    """The paper's explicit central-difference variant (Sec. 2.3) on the same 256^3 medium:
+    one FP64 operator application per step at 0.9 of the CFL increment."""
+    import numpy as np
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    dtc = wfft.explicit_dt(prob.ndim, prob.h, prob.C, prob.rho)
+    dt = 0.9 * dtc
+    s = wfft.Solver(prob.ndim, prob.n, prob.h, prob.C, prob.rho, prob.phase, prob.mask, dt, beta=0.0, gamma=0.5,
+                    stream=stream.cuda_stream)
+    t = dt * np.arange(1, W + K + 1)
+    Ud = np.zeros((W + K, 3))
+    w = 50 * prob.dt  # the workload's Gaussian pulse (sigma 50 dt, centre 4 sigma, amplitude 1e-6 m), differentiated
+    Ud[:, 0] = -(t - 4 * w) / w ** 2 * 1e-6 * np.exp(-((t - 4 * w) ** 2) / (2 * w * w))
+    for k in range(W):
+        s.explicit_step(Ud[k])
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(W, W + K):
+        s.explicit_step(Ud[k])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / K
+    s.close()
+    return {"ms_per_step": ms, "dt": dt, "cfl_dt": dtc, "implicit_dt": prob.dt,
+            "ms_per_implicit_dt_of_simulated_time": ms * prob.dt / dt,
+            "note": "explicit central difference (beta 0, gamma 1/2), FP64, prescribed u_x velocity on the slab"}
+
+
 def cpu_oracle_iteration(prob, reps=1):
     """One FP64 oracle PCG iteration (operator + preconditioner + updates) on the workload."""
     import numpy as np
@@ -473,6 +504,8 @@ def main():
             line["roofline_net"] = nr
     if not args.no_small:
         line["small_grid"] = small_grid(wfft, torch)
+    if not args.no_explicit:
+        line["explicit"] = explicit_scheme(wfft, torch, prob, W, K)
     if "e2e_s" in head:
         line["e2e"] = {"value": V * head["e2e_iters"] * world / head["e2e_s"], "unit": UNIT,
                        "h2d_bytes_per_step": 24, "d2h_bytes_per_step": head["d2h_bytes"],

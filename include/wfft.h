@@ -111,7 +111,9 @@ WFFT_API int wfft_default_options(wfft_options* opt);
  *   rho       : host, nphase (or V) densities, > 0.
  *   mask      : host uint8 [c][N3][N2][N1], 1 = prescribed DOF (Gamma), may be
  *               NULL (no prescribed region); must leave at least one free DOF.
- *   dt, beta, gamma : Newmark constants (Eq. Newmark); dt > 0, beta > 0.
+ *   dt, beta, gamma : Newmark constants (Eq. Newmark); dt > 0, beta > 0; or beta = 0 with
+ *                     gamma = 1/2 (FP64 only): an explicit-scheme handle, stepped by
+ *                     wfft_explicit_step (wfft_step / wfft_solve / wfft_batch_step: EINVAL).
  *   opt       : options (NULL = defaults).
  *   stream    : cudaStream_t cast to void* (NULL = legacy default stream).
  *   out       : receives the handle (owned by the caller, free with wfft_destroy).
@@ -285,6 +287,32 @@ WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], 
  * scratch vectors (not the state); synchronises the stream; EINVAL while profiling.
  */
 WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
+
+/*
+ * Explicit central-difference scheme (Sec. 2.3, Eq. Central_diff_rule, Eq.
+ * Explicit_linear_momentum_arranged_3D), on a handle created with beta = 0,
+ * gamma = 1/2.  One step, with the velocity Udot(t_n) prescribed on Gamma
+ * (uniform per component, as U in wfft_step):
+ *   u_n = u + dt v + dt^2/2 a on every DOF;
+ *   v_b = v + dt/2 a + dt/(2 rho) div(C : grad^s u_n)   (the spectral operator, one FP64
+ *         application, no Krylov solve);
+ *   f_n = 2 rho/dt (Udot - v_b) on Gamma, 0 elsewhere;  v_n = v_b + dt/(2 rho) f_n (= Udot on Gamma);
+ *   a_n = 2 (v_n - v)/dt - a.
+ * info: iters 0, outer_applies 1, reaction = sum of f_n per component, ms.  The scheme is
+ * conditionally stable: see wfft_explicit_dt.
+ */
+WFFT_API int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_step_info* info);
+/*
+ * Largest stable increment of the explicit scheme (Eq. Courant_stable, Eq.
+ * Eigenvalues_1D_homogeneo): 2 / omega_max, omega_max^2 the largest eigenvalue of
+ * Q_ik = C_ijkl xi_j xi_l / rho at xi_i = N_i pi / L_i = pi / h_i, taken over the
+ * nrows material rows (C: 21 Voigt values per row as in wfft_create, rho per row; 2-D
+ * uses the in-plane block).  Host computation only (no GPU needed).  The operator's
+ * own top frequency is below N_i pi / L_i (the Nyquist multiplier is 0), so this
+ * bound is on the safe side.
+ */
+WFFT_API int wfft_explicit_dt(int ndim, const double h[3], const double* C, const double* rho, long long nrows,
+                              double* dt_max);
 
 /* Kernel kinds of the launch accounting (wfft_profile_read). */
 #define WFFT_K_XFWD_PLAIN 0   /* x-axis real->half-spectrum pass */

@@ -55,6 +55,7 @@ struct wfft_handle {
   cudaStream_t cap_st = nullptr;
   cudaGraphExec_t chunk[2] = {nullptr, nullptr};
   long long chunk_launches[2] = {0, 0};
+  bool explicit_scheme = false;  // beta = 0, gamma = 1/2 (wfft_explicit_step)
   NetDev* net = nullptr;    // learned warm start (wfft_set_model)
   NetWork nw;
   float* delta = nullptr;   // FP64 handles: FP32 warm-start increment
@@ -239,7 +240,11 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   }
   if (grid->ndim == 2 && grid->n[2] != 1) return fail(nullptr, WFFT_EINVAL, "2-D grids need n[2] == 1");
   if (grid->n[1] == 1 && grid->n[2] == 1) return fail(nullptr, WFFT_EUNSUPPORTED, "N2 = N3 = 1 is not supported");
-  if (!(dt > 0) || !(beta > 0) || !(gamma >= 0)) return fail(nullptr, WFFT_EINVAL, "need dt > 0, beta > 0, gamma >= 0");
+  const bool explicit_scheme = beta == 0.0 && gamma == 0.5;
+  if (!(dt > 0) || !(gamma >= 0) || !(beta > 0 || explicit_scheme))
+    return fail(nullptr, WFFT_EINVAL, "need dt > 0, gamma >= 0 and beta > 0 (or beta = 0, gamma = 1/2: explicit scheme)");
+  if (explicit_scheme && opt && opt->precision != WFFT_FP64)
+    return fail(nullptr, WFFT_EINVAL, "the explicit scheme runs in FP64");
   if (phase && nphase < 1) return fail(nullptr, WFFT_EINVAL, "nphase must be >= 1");
   for (int i = 0; i < 3; ++i) {
     AxisPlan pl;
@@ -259,7 +264,10 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   h->dt = dt;
   h->beta = beta;
   h->gamma = gamma;
-  h->theta = beta * dt * dt;
+  // the explicit scheme has no solve: its operator passes run at theta = 1, so the
+  // divergence pass returns -div(C : grad^s u) itself
+  h->explicit_scheme = explicit_scheme;
+  h->theta = explicit_scheme ? 1.0 : beta * dt * dt;
   if (opt)
     h->opt = *opt;
   else
@@ -429,7 +437,7 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   CKC(cudaEventCreate(&h->ev1));
   // lifting fields w_j = P A(E e_j) for the stopping-test reference norm
   ProfScope ps_(h);
-  if (h->has_mask) {
+  if (h->has_mask && !h->explicit_scheme) {
     double* tmp = reinterpret_cast<double*>(D.slot[SL_Z]);
     for (int j = 0; j < h->ndim; ++j) {
       launch_set_done(h->sc64, 0, h->st);
@@ -708,6 +716,7 @@ __global__ static void k_add_delta(const Desc<double>* dd, const float* delta) {
 extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info) {
   ProfScope ps_(h);
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (h->explicit_scheme) return fail(h, WFFT_EINVAL, "explicit-scheme handle: use wfft_explicit_step");
   if (!U) return fail(h, WFFT_EINVAL, "U is NULL");
   fill_info_base(info);
   const int warm = h->opt.warm_start;
@@ -867,6 +876,7 @@ __global__ static void k_keep_gamma(const Desc<double>* dd, double* x) {
 extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol, int maxit, wfft_step_info* info) {
   ProfScope ps_(h);
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (h->explicit_scheme) return fail(h, WFFT_EINVAL, "explicit-scheme handle: use wfft_explicit_step");
   if (!b || !x) return fail(h, WFFT_EINVAL, "b and x are required");
   fill_info_base(info);
   h->au_valid = false;  // the residual evaluations below overwrite the stored A u
@@ -1161,8 +1171,10 @@ int batch_pcg(BatchCtx& B, const BatchLaunch<T>& bl, const Plan<T>& P0, int whic
 extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step_info* infos) {
   if (!hs || n < 0 || (n > 0 && !U)) return fail(nullptr, WFFT_EINVAL, "bad batch arguments");
   if (n == 0) return WFFT_OK;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!hs[i]) return fail(nullptr, WFFT_EINVAL, "null handle in batch");
+    if (hs[i]->explicit_scheme) return fail(nullptr, WFFT_EINVAL, "explicit-scheme handles step with wfft_explicit_step");
+  }
   wfft_handle* h0 = hs[0];
   // the grouped path needs one structure: same precision, dimensionality, pass
   // sequence, stream and warm start; otherwise the handles step one by one
@@ -1500,4 +1512,59 @@ extern "C" int wfft_autotune(wfft_handle* h, int reps, int* changed) {
     }
   if (changed) *changed = ch;
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// explicit central-difference scheme (Sec. 2.3)
+// ---------------------------------------------------------------------------
+extern "C" int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_step_info* info) {
+  ProfScope ps_(h);
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (!h->explicit_scheme) return fail(h, WFFT_EINVAL, "not an explicit-scheme handle (create it with beta = 0, gamma = 1/2)");
+  if (!Udot) return fail(h, WFFT_EINVAL, "Udot is NULL");
+  fill_info_base(info);
+  Plan<double>& P = h->P64;
+  const double Uv[3] = {Udot[0], h->ndim > 1 ? Udot[1] : 0.0, h->ndim > 2 ? Udot[2] : 0.0};
+  CKH(h, cudaEventRecord(h->ev0, h->st));
+  launch_set_done(h->sc64, 0, h->st);
+  launch_explicit_predict(P, h->st);
+  // q = -div(C : grad^s u_n), every DOF (unmasked)
+  launch_apply<double>(P, PRE_PLAIN, SL_U, POST_PREC, SL_Q, 0, 0, h->st);
+  launch_explicit_update(P, Uv, h->st);
+  const int nb = ew_block_count(P);
+  launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
+  CKH(h, cudaEventRecord(h->ev1, h->st));
+  CKH(h, cudaGetLastError());
+  int rc = read_scalars(h);
+  if (rc) return rc;
+  h->au_valid = false;
+  ++h->nstep;
+  if (info) {
+    info->status = WFFT_OK;
+    info->outer_applies = 1;
+    for (int k = 0; k < 3; ++k) info->reaction[k] = h->host_sc[0].react[k];
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->ms = ms;
+  }
+  return WFFT_OK;
+}
+
+extern "C" int wfft_explicit_dt(int ndim, const double h[3], const double* C, const double* rho, long long nrows,
+                                double* dt_max) {
+  if ((ndim != 2 && ndim != 3) || !h || !C || !rho || nrows < 1 || !dt_max)
+    return fail(nullptr, WFFT_EINVAL, "ndim 2 or 3, h, C, rho, nrows >= 1 and dt_max are required");
+  double xi[3] = {0, 0, 0};
+  for (int i = 0; i < ndim; ++i) {
+    if (!(h[i] > 0)) return fail(nullptr, WFFT_EINVAL, "voxel sizes must be > 0");
+    xi[i] = 3.141592653589793238462643383279502884 / h[i];  // N_i pi / L_i with L_i = N_i h_i
+  }
+  double w2 = 0.0;
+  for (long long r = 0; r < nrows; ++r) {
+    if (!(rho[r] > 0)) return fail(nullptr, WFFT_EINVAL, "rho must be > 0");
+    w2 = std::max(w2, acoustic_max_eig(C + 21 * r, ndim, xi) / rho[r]);
+  }
+  if (!(w2 > 0)) return fail(nullptr, WFFT_EINVAL, "the stiffness gives no positive wave speed");
+  *dt_max = 2.0 / std::sqrt(w2);
+  return WFFT_OK;
 }

@@ -2,6 +2,7 @@
 // allocation-free entry point (noalloc.cu): radix schedules, twiddle tables,
 // stiffness checks and the quadratic-form coefficients of the preconditioner.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -99,6 +100,46 @@ static inline void voigt_full(const double* c21, double* m6) {
       m6[i * 6 + j] = m6[j * 6 + i] = c21[k];
       ++k;
     }
+}
+
+// Largest eigenvalue of Q_ik = C_ijkl xi_j xi_l (the acoustic tensor times |xi|^2,
+// Eq. Eigenvalues_1D_homogeneo without the 1/rho) for one 21-value Voigt row; 2-D
+// uses the in-plane block (i, k in {1, 2}).  Cyclic Jacobi rotations on the 3x3
+// symmetric matrix.
+static inline double acoustic_max_eig(const double* c21, int ndim, const double xi[3]) {
+  double m6[36];
+  voigt_full(c21, m6);
+  static const int vi[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};  // Voigt index of (i, j)
+  const int d = ndim == 3 ? 3 : 2;
+  double Q[3][3] = {};
+  for (int i = 0; i < d; ++i)
+    for (int k = 0; k < d; ++k)
+      for (int j = 0; j < d; ++j)
+        for (int l = 0; l < d; ++l) Q[i][k] += m6[vi[i][j] * 6 + vi[k][l]] * xi[j] * xi[l];
+  if (d == 2) Q[2][2] = 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    const double off = Q[0][1] * Q[0][1] + Q[0][2] * Q[0][2] + Q[1][2] * Q[1][2];
+    const double diag = Q[0][0] * Q[0][0] + Q[1][1] * Q[1][1] + Q[2][2] * Q[2][2];
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (Q[p][q] == 0.0) continue;
+        const double th = (Q[q][q] - Q[p][p]) / (2.0 * Q[p][q]);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < 3; ++r) {  // columns p, q
+          const double a = Q[r][p], b = Q[r][q];
+          Q[r][p] = c * a - sn * b;
+          Q[r][q] = sn * a + c * b;
+        }
+        for (int r = 0; r < 3; ++r) {  // rows p, q
+          const double a = Q[p][r], b = Q[q][r];
+          Q[p][r] = c * a - sn * b;
+          Q[q][r] = sn * a + c * b;
+        }
+      }
+  }
+  return std::max(Q[0][0], std::max(Q[1][1], Q[2][2]));
 }
 
 // Quadratic-form coefficients of theta*K(xi), K = B^T Cbar B (Eq. acous), B the

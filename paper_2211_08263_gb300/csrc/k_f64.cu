@@ -143,6 +143,60 @@ __global__ void k_fill_unit(const Desc<double>* __restrict__ dd, int j, double* 
   }
 }
 
+// Explicit central-difference step (Sec. 2.3, Eq. Central_diff_rule), part 1:
+// u_n = u + dt v + dt^2/2 a on every DOF.
+__global__ void __launch_bounds__(256) k_explicit_predict(const Desc<double>* __restrict__ dd) {
+  const Desc<double>& D = *dd;
+  const long long tot = (long long)D.c * D.V;
+  const double dt = D.dt;
+  double* u = reinterpret_cast<double*>(D.slot[SL_U]);
+  const double* v = reinterpret_cast<const double*>(D.slot[SL_V]);
+  const double* a = reinterpret_cast<const double*>(D.slot[SL_A]);
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x)
+    u[gi] = u[gi] + dt * v[gi] + 0.5 * dt * dt * a[gi];
+}
+
+// Part 2 (Eq. Explicit_linear_momentum_arranged_3D), with q = -div(C : grad^s u_n)
+// from the operator passes run at theta = 1:
+//   v_b = v + dt/2 a + dt/(2 rho) div sigma,  f = 2 rho/dt (Udot - v_b) on Gamma (0 elsewhere),
+//   v_n = v_b + dt/(2 rho) f,  a_n = 2 (v_n - v)/dt - a;
+// partial sums of f per component (the force on Gamma).
+__global__ void __launch_bounds__(256) k_explicit_update(const Desc<double>* __restrict__ dd, double U0, double U1,
+                                                         double U2) {
+  const Desc<double>& D = *dd;
+  const long long V = D.V;
+  const long long tot = (long long)D.c * V;
+  const double dt = D.dt;
+  double* v = reinterpret_cast<double*>(D.slot[SL_V]);
+  double* a = reinterpret_cast<double*>(D.slot[SL_A]);
+  const double* q = reinterpret_cast<const double*>(D.slot[SL_Q]);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(gi / V);
+    const long long vox = gi - (long long)k * V;
+    const double rho = rho_at<double>(D, vox);
+    const double vv = v[gi], aa = a[gi];
+    const double vb = vv + 0.5 * dt * aa + dt / (2.0 * rho) * (-q[gi]);
+    double vn = vb, f = 0.0;
+    if ((D.mask[vox] >> k) & 1) {
+      const double Uk = k == 0 ? U0 : (k == 1 ? U1 : U2);
+      f = 2.0 * rho / dt * (Uk - vb);
+      vn = vb + dt / (2.0 * rho) * f;
+    }
+    v[gi] = vn;
+    a[gi] = 2.0 * (vn - vv) / dt - aa;
+    if (k == 0) acc[0] += f;
+    else if (k == 1) acc[1] += f;
+    else acc[2] += f;
+  }
+  for (int k = 0; k < 3; ++k) {
+    const double sum = block_sum(acc[k]);
+    if (threadIdx.x == 0) D.part[k][blockIdx.x] = sum;
+  }
+}
+
 static int ew_blocks(const Plan<double>& P) {
   const long long tot = (long long)P.h.c * P.h.V;
   long long nb = (tot + 255) / 256;
@@ -181,6 +235,16 @@ void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st
   prof_launch(0, KK_SCALAR, 8.0 * P.h.c * P.h.V, 0.0, st, [&] { k_fill_unit<<<ew_blocks(P), 256, 0, st>>>(P.d, j, dst); });
 }
 int ew_block_count(const Plan<double>& P) { return ew_blocks(P); }
+void launch_explicit_predict(const Plan<double>& P, cudaStream_t st) {
+  const double cv = (double)P.h.c * P.h.V;
+  prof_launch(0, KK_NEWMARK, 8 * cv * 4, cv * 5, st, [&] { k_explicit_predict<<<ew_blocks(P), 256, 0, st>>>(P.d); });
+}
+void launch_explicit_update(const Plan<double>& P, const double Udot[3], cudaStream_t st) {
+  const double cv = (double)P.h.c * P.h.V;
+  prof_launch(0, KK_NEWMARK, 8 * cv * 5 + 3.0 * cv / P.h.c, cv * 14, st, [&] {
+    k_explicit_update<<<ew_blocks(P), 256, 0, st>>>(P.d, Udot[0], Udot[1], Udot[2]);
+  });
+}
 
 // ---------------------------------------------------------------------------
 // finalize kernels (one block)

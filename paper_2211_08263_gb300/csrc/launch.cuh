@@ -105,6 +105,10 @@ inline cudaError_t init_kernel_attributes() {
 // FP64 elementwise kernels of the Newmark step (k_f64.cu).
 void launch_predict(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl = nullptr);
 void launch_correct(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl = nullptr);
+// Explicit central-difference step (Sec. 2.3): Taylor update of u, then v / a / force on Gamma
+// from q = -div(C : grad^s u_n) in SL_Q.
+void launch_explicit_predict(const Plan<double>& P, cudaStream_t st);
+void launch_explicit_update(const Plan<double>& P, const double Udot[3], cudaStream_t st);
 void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st);
 
 }  // namespace wfft

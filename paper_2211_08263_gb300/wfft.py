@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.wfft_profile_read.argtypes = [vp, i, i, P(C.c_longlong), P(C.c_longlong), P(d), P(d), P(d)]
     lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
     lib.wfft_autotune.argtypes = [vp, i, P(i)]
+    lib.wfft_explicit_step.argtypes = [vp, P(d), P(StepInfo)]
+    lib.wfft_explicit_dt.argtypes = [i, P(d), vp, vp, C.c_longlong, P(d)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
     lib.wfft_model_bytes.argtypes = [i]
     lib.wfft_model_bytes.restype = C.c_size_t
@@ -238,6 +240,18 @@ class Solver:
 
     def rfft3(self, inp, out, precision: int = FP64, direction: int = -1, ncomp: int = 1):
         self._check(self.lib.wfft_rfft3(self.h, precision, direction, ncomp, _dptr(inp), _dptr(out)))
+
+    def explicit_step(self, Udot, raise_on_error: bool = True) -> dict:
+        """One explicit central-difference step (handle created with beta = 0, gamma = 1/2)
+        with the velocity Udot(t_n) prescribed on Gamma."""
+        Uv = (C.c_double * 3)(*[float(x) for x in list(Udot)[:3]] + [0.0] * (3 - min(3, len(Udot))))
+        info = StepInfo()
+        rc = self.lib.wfft_explicit_step(self.h, Uv, C.byref(info))
+        if raise_on_error:
+            self._check(rc)
+        d = info.as_dict()
+        d["rc"] = rc
+        return d
 
     def autotune(self, reps: int = 3) -> int:
         """Time and keep the fastest radix decompositions and column-tile widths
@@ -450,3 +464,13 @@ class Trainer:
             self.close()
         except Exception:
             pass
+
+
+def explicit_dt(ndim: int, h, C_table: np.ndarray, rho: np.ndarray) -> float:
+    """Largest stable increment of the explicit scheme over the material rows (wfft_explicit_dt)."""
+    Ct = np.ascontiguousarray(C_table, dtype=np.float64).reshape(-1, 21)
+    r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+    hh = (C.c_double * 3)(*[float(x) for x in list(h)[:3]] + [1.0] * (3 - min(3, len(h))))
+    out = C.c_double()
+    _raise_global(load().wfft_explicit_dt(int(ndim), hh, _ptr(Ct), _ptr(r), Ct.shape[0], C.byref(out)))
+    return out.value

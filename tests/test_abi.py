@@ -118,3 +118,17 @@ def test_trainer_and_network_calls_fail_cleanly(lib):
         wfft.net_forward(blob, (0, 4, 4), np.zeros((0, 16), np.float32))
     assert e.value.code == wfft.EINVAL
     assert lib.wfft_set_model(None, None, 0) == wfft.EINVAL
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_explicit_stable_increment_matches_the_reference(lib, ndim):
+    """wfft_explicit_dt (host only) against the reference's 2 / omega_max over
+    random rotated-cubic and isotropic phases with different densities."""
+    from oracle import explicit, medium
+    from paper_2211_08263_gb300 import inputs, wfft
+    rng = np.random.default_rng(81 + ndim)
+    n = (8, 6, 4) if ndim == 3 else (8, 6, 1)
+    prob = inputs.random_problem(rng, ndim, n, nphase=4, mask_width=1, nsteps=1, h=7e-4)
+    dt = wfft.explicit_dt(ndim, prob.h, prob.C, prob.rho)
+    ref = explicit.stable_dt(medium.medium_from_problem(prob))
+    assert abs(dt - ref) <= 1e-12 * ref, (dt, ref)
