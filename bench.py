@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the launch-bound C1 (64^2) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT plans (no wfft_autotune)")
     ap.add_argument("--no-explicit", action="store_true", help="skip the explicit-scheme measurement")
+    ap.add_argument("--inner-floor", type=float, default=None,
+                    help="mixed modes: stop an inner solve at this fraction of the outer target")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
     return ap.parse_args()
 
@@ -203,6 +205,7 @@ def train_warm_start(wfft, args, stream):
 
 
 PROF_STEPS = 3
+INNER_FLOOR = None  # None: the library default
 
 
 def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None, autotune=True):
@@ -213,6 +216,8 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
                                warm_start=getattr(wfft, warm))
     if inner_tol:
         opt.inner_tol = inner_tol
+    if INNER_FLOOR is not None:
+        opt.inner_floor = INNER_FLOOR
 
     def make():
         sv = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
@@ -421,6 +426,9 @@ def run_reference(args, prob, rank, world):
 
 def main():
     args = parse()
+    global INNER_FLOOR
+    if args.inner_floor is not None:
+        INNER_FLOOR = args.inner_floor
     rank, world, local = dist_env()
     from paper_2211_08263_gb300 import inputs
     W, K = args.warmup, args.steps

@@ -83,6 +83,9 @@ typedef struct {
   int watchdog_iters;/* hard cap on iterations per step, across sweeps (0 = 4*maxit) */
   int use_graphs;    /* 1: each block of check_every PCG iterations is one CUDA graph launch (captured
                         once per handle on an internal stream; not while profiling is on); 0: plain launches */
+  double inner_floor;/* mixed: an FP32 inner solve also stops once its residual is below
+                        inner_floor * tol * ref (the outer target), so the last sweep does not
+                        overshoot it; 0 = off.  The FP64 residual still decides convergence. */
 } wfft_options;
 
 typedef struct {
@@ -97,7 +100,7 @@ typedef struct {
 } wfft_step_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-10, maxit 1000, WARM_PREV, inner_tol 1e-5,
-   max_sweeps 20, check_every 4, use_graphs 1. */
+   max_sweeps 20, check_every 4, use_graphs 1, inner_floor 0.5. */
 WFFT_API int wfft_default_options(wfft_options* opt);
 
 /*

@@ -214,6 +214,7 @@ extern "C" int wfft_default_options(wfft_options* o) {
   o->max_sweeps = 20;
   o->check_every = 4;
   o->use_graphs = 1;
+  o->inner_floor = 0.5;
   o->watchdog_iters = 0;
   return WFFT_OK;
 }
@@ -732,7 +733,7 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
   const double dU[3] = {Uv[0] - h->U_prev[0], Uv[1] - h->U_prev[1], Uv[2] - h->U_prev[2]};
   CKH(h, cudaEventRecord(h->ev0, h->st));
   launch_begin(h->sc64, Uv, delta_mode ? WFFT_WARM_PREV : warm, h->opt.tol * h->opt.tol, h->opt.maxit, h->st,
-               use_au ? 1 : 0, dU);
+               use_au ? 1 : 0, dU, h->opt.inner_floor > 0 ? h->opt.inner_floor : 0.0);
   launch_begin(h->sc32, Uv, delta_mode ? WFFT_WARM_PREV : warm, h->opt.inner_tol * h->opt.inner_tol,
                h->opt.maxit, h->st);
   launch_predict(P, h->st);

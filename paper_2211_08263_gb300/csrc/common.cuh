@@ -40,6 +40,8 @@ struct Scalars {
   double react[3];
   double Ug[3];     // U(t_n) of the current step
   double dU[3];     // U(t_n) - U(t_{n-1}) (stored-A u initial residual)
+  double tol2_base; // inner: inner_tol^2 as set at the start of the step
+  double floor_fac; // outer: an inner solve may stop at floor_fac * tol * ref (0: off)
   int iter;         // operator applications inside the Krylov loop
   int maxit;
   int done;         // 1: every kernel of this solve returns immediately

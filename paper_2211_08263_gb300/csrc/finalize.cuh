@@ -39,7 +39,7 @@ void launch_begin_batch(const BeginJob* jobs, int n, cudaStream_t st);
 void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc, int mode,
                 Scalars* sc2, cudaStream_t st);
 void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st,
-                  int use_au = 0, const double* dU = nullptr);
+                  int use_au = 0, const double* dU = nullptr, double flr = 0.0);
 void launch_set_done(Scalars* sc, int done, cudaStream_t st);
 int ew_block_count(const Plan<double>& P);
 

@@ -346,6 +346,11 @@ __device__ void fin_body(Scalars* sc, const double* pa, int na, const double* pb
         sc2->scale = 1.0 / nr;
         sc2->xcoef = nr;
         sc2->ref2 = 1.0;
+        // the inner solve reduces its (normalised) residual by inner_tol, or stops once it is
+        // below floor_fac * tol * ref: the last sweep need not overshoot the outer target
+        const double base = sc2->tol2_base > 0.0 ? sc2->tol2_base : sc2->tol2;
+        const double fl = sc->floor_fac * sqrt(sc->tol2 * sc->ref2) / nr;
+        sc2->tol2 = fmax(base, fl * fl);
         sc2->iter = 0;
         sc2->done = 0;
         sc2->first = 1;
@@ -376,7 +381,7 @@ __global__ void k_fin_batch(const FinJob* jobs, int mode) {
 }
 
 __global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, double tol2, int maxit, int use_au,
-                        double d0, double d1, double d2) {
+                        double d0, double d1, double d2, double flr) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   sc->Ug[0] = U0;
   sc->Ug[1] = U1;
@@ -400,6 +405,8 @@ __global__ void k_begin(Scalars* sc, double U0, double U1, double U2, int warm, 
   sc->dU[0] = d0;
   sc->dU[1] = d1;
   sc->dU[2] = d2;
+  sc->tol2_base = tol2;
+  sc->floor_fac = flr;
 }
 
 __global__ void k_begin_batch(const BeginJob* jobs, int n) {
@@ -413,6 +420,8 @@ __global__ void k_begin_batch(const BeginJob* jobs, int n) {
   }
   sc->warm = j.warm;
   sc->tol2 = j.tol2;
+  sc->tol2_base = j.tol2;
+  sc->floor_fac = 0.0;
   sc->maxit = j.maxit;
   sc->done = 0;
   sc->status = 0;
@@ -439,10 +448,10 @@ void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb,
               [&] { k_fin<<<1, 256, 0, st>>>(sc, pa, na, pb, nb, pc, nc, mode, sc2); });
 }
 void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st, int use_au,
-                  const double* dU) {
+                  const double* dU, double flr) {
   const double d0 = dU ? dU[0] : 0.0, d1 = dU ? dU[1] : 0.0, d2 = dU ? dU[2] : 0.0;
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st,
-              [&] { k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit, use_au, d0, d1, d2); });
+              [&] { k_begin<<<1, 32, 0, st>>>(sc, U[0], U[1], U[2], warm, tol2, maxit, use_au, d0, d1, d2, flr); });
 }
 void launch_fin_batch(const FinJob* jobs, int n, int mode, cudaStream_t st) {
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_fin_batch<<<n, 256, 0, st>>>(jobs, mode); });

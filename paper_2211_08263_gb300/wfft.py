@@ -41,7 +41,7 @@ class Grid(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("warm_start", C.c_int),
                 ("inner_tol", C.c_double), ("max_sweeps", C.c_int), ("check_every", C.c_int),
-                ("watchdog_iters", C.c_int), ("use_graphs", C.c_int)]
+                ("watchdog_iters", C.c_int), ("use_graphs", C.c_int), ("inner_floor", C.c_double)]
 
 
 class StepInfo(C.Structure):

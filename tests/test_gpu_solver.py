@@ -257,3 +257,26 @@ def test_autotuned_plan_keeps_the_results(precision, tol, bar):
     assert rel(oracle_field(prob, ut), so.u) < bar
     for s in (tuned, plain, again):
         s.close()
+
+
+def test_inner_floor_keeps_the_accuracy_and_never_adds_iterations():
+    """inner_floor lets an FP32 inner solve stop at a fraction of the outer target;
+    the FP64 residual still decides convergence, so the steps stay within the mixed
+    bar of the oracle, every step meets the tolerance, and no iterations are added."""
+    from oracle import newmark
+    torch_cuda()
+    wfft = solver_lib()
+    prob = inputs.random_problem(np.random.default_rng(33), 3, (24, 20, 16), nphase=3, mask_width=2, nsteps=5)
+    runs = {}
+    for fl in (0.0, 0.5):
+        opt = wfft.default_options(precision=wfft.MIXED, tol=1e-10)
+        opt.inner_floor = fl
+        s = wfft.Solver.from_problem(prob, options=opt)
+        infos = [s.step(prob.U[k]) for k in range(prob.nsteps)]
+        runs[fl] = (s.get_state()[0], infos)
+        s.close()
+    so, _ = newmark.oracle_from_problem(prob, tol=1e-13).run(prob.U)
+    for fl, (u, infos) in runs.items():
+        assert rel(oracle_field(prob, u), so.u) < 1e-6
+        assert all(i["rel_res"] <= 1e-10 * 1.0001 for i in infos)
+    assert sum(i["iters"] for i in runs[0.5][1]) <= sum(i["iters"] for i in runs[0.0][1])
