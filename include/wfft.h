@@ -290,6 +290,15 @@ WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], 
  * scratch vectors (not the state); synchronises the stream; EINVAL while profiling.
  */
 WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
+/*
+ * Radix schedule of one axis of one precision's plan, set by hand: cnt[r] stages of
+ * radix 8, 4, 2, 3, 5, 7, 16 (r = 0..6; their product must be the axis length; radix 16
+ * only in the FP32 plan, precision WFFT_MIXED).  The stages run in the order 16s, 8s, 4s,
+ * 2s, 3s, 5s, 7s.  The tile geometry follows; a schedule that would need more
+ * partial-sum slots than the handle allocated is refused (EINVAL, plan unchanged).
+ * Synchronises the stream.
+ */
+WFFT_API int wfft_set_radix(wfft_handle* h, int precision, int axis, const int cnt[7]);
 
 /*
  * Explicit central-difference scheme (Sec. 2.3, Eq. Central_diff_rule, Eq.

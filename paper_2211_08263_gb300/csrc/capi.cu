@@ -1428,7 +1428,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
   if (!cached) {
     // 1. radix decomposition, axis by axis
     for (int a = 0; a < 3; ++a) {
-      const std::vector<AxisPlan> cands = factor_candidates(h->n[a]);
+      const std::vector<AxisPlan> cands = factor_candidates(h->n[a], sizeof(T) == 4);
       if (h->n[a] == 1 || cands.size() < 2) continue;
       AxisPlan keep = D.ax[a];
       float tbest = 1e30f;
@@ -1486,7 +1486,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
   }
   for (int a = 0; a < 3; ++a) {
     bool same = D.ax[a].n == before.ax[a].n;
-    for (int r = 0; r < 6; ++r) same = same && D.ax[a].cnt[r] == before.ax[a].cnt[r];
+    for (int r = 0; r < 7; ++r) same = same && D.ax[a].cnt[r] == before.ax[a].cnt[r];
     if (!same) ++*changed;
     for (int op = 0; op < 5; ++op)
       if (ops_of_axis(D, a, op) && P.g.bx[a][op] != before.bx[a][op]) ++*changed;
@@ -1568,4 +1568,48 @@ extern "C" int wfft_explicit_dt(int ndim, const double h[3], const double* C, co
   if (!(w2 > 0)) return fail(nullptr, WFFT_EINVAL, "the stiffness gives no positive wave speed");
   *dt_max = 2.0 / std::sqrt(w2);
   return WFFT_OK;
+}
+
+namespace {
+template <typename T>
+int set_radix_plan(wfft_handle* h, Plan<T>& P, int axis, const AxisPlan& pl) {
+  Desc<T>& D = P.h;
+  const AxisPlan old = D.ax[axis];
+  D.ax[axis] = pl;
+  plan_geometry<T>(P);
+  if (P.g.max_blocks > h->nparts) {
+    D.ax[axis] = old;
+    plan_geometry<T>(P);
+    return fail(h, WFFT_EINVAL, "this decomposition needs more partial-sum slots than the handle has");
+  }
+  CKH(h, cudaStreamSynchronize(h->st));
+  CKH(h, upload_desc(P));
+  for (int k = 0; k < 2; ++k)
+    if (h->chunk[k]) {
+      cudaGraphExecDestroy(h->chunk[k]);
+      h->chunk[k] = nullptr;
+    }
+  return WFFT_OK;
+}
+}  // namespace
+
+extern "C" int wfft_set_radix(wfft_handle* h, int precision, int axis, const int cnt[7]) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if ((precision != WFFT_FP64 && precision != WFFT_MIXED) || axis < 0 || axis > 2 || !cnt)
+    return fail(h, WFFT_EINVAL, "precision WFFT_FP64 / WFFT_MIXED, axis 0..2 and cnt are required");
+  if (h->prof.on) return fail(h, WFFT_EINVAL, "switch profiling off before changing plans");
+  static const int rad[7] = {8, 4, 2, 3, 5, 7, 16};
+  AxisPlan pl;
+  pl.n = h->n[axis];
+  long long prod = 1;
+  for (int r = 0; r < 7; ++r) {
+    if (cnt[r] < 0 || cnt[r] > 16) return fail(h, WFFT_EINVAL, "stage counts must be 0..16");
+    pl.cnt[r] = cnt[r];
+    for (int k = 0; k < cnt[r]; ++k) prod *= rad[r];
+  }
+  if (prod != h->n[axis]) return fail(h, WFFT_EINVAL, "the stages' radices must multiply to the axis length");
+  if (precision == WFFT_FP64 && cnt[6]) return fail(h, WFFT_EINVAL, "radix-16 stages are FP32 only");
+  ProfScope ps_(h);
+  return precision == WFFT_FP64 ? set_radix_plan<double>(h, h->P64, axis, pl)
+                                : set_radix_plan<float>(h, h->P32, axis, pl);
 }

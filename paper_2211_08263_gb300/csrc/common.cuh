@@ -24,7 +24,7 @@ constexpr int kCtabStride2 = 8;   // 6 in-plane values padded
 // Radix schedule of one axis: cnt[] = number of stages of radix 8, 4, 2, 3, 5, 7.
 struct AxisPlan {
   int n;
-  int cnt[6];
+  int cnt[7];  // stages of radix 8, 4, 2, 3, 5, 7, 16 (16: FP32 plans only)
 };
 
 // Scalars of one Krylov solve, updated only by the single-block finalize kernels.

@@ -31,6 +31,8 @@ template <typename T, int R> struct NbOf {
 #define WFFT_S52 0.58778525229247312917
 #define WFFT_S3 0.86602540378443864676   /* sin(pi/3) = sqrt3/2 */
 #define WFFT_R2 0.70710678118654752440   /* 1/sqrt2 */
+#define WFFT_C8 0.92387953251128675613   /* cos(pi/8) */
+#define WFFT_S8 0.38268343236508977173   /* sin(pi/8) */
 
 // In-register R-point DFT, X_q = sum_m v_m exp(sgn 2 pi i m q / R),
 // sgn = -1 forward, +1 inverse.
@@ -79,6 +81,41 @@ struct Dft<T, 8> {
     v[6] = csub<T>(e[2], o2);
     v[3] = cadd<T>(e[3], o3);
     v[7] = csub<T>(e[3], o3);
+  }
+};
+
+// 16 = 4 x 4: X[k1 + 4 k2] = sum_n2 W16^(n2 k1) W4^(n2 k2) sum_n1 x[4 n1 + n2] W4^(n1 k1):
+// four 4-point DFTs over n1, the twiddles W16^(n2 k1), four 4-point DFTs over n2.
+template <typename T>
+struct Dft<T, 16> {
+  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>*, int) {
+    cplx<T> y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
+      Dft<T, 4>::run(y[n2], sgn, nullptr, 0);
+    }
+    const T c8 = (T)WFFT_C8, s8 = (T)WFFT_S8, r2 = (T)WFFT_R2, sg = (T)sgn;
+    // W16^m = (cos 2 pi m/16, sgn sin 2 pi m/16) for m = 1, 2, 3, 6, 9; W16^4 = sgn i
+    const cplx<T> w1 = cmake<T>(c8, sg * s8), w2 = cmake<T>(r2, sg * r2), w3 = cmake<T>(s8, sg * c8);
+    const cplx<T> w6 = cmake<T>(-r2, sg * r2), w9 = cmake<T>(-c8, -sg * s8);
+    y[1][1] = cmul<T>(y[1][1], w1);
+    y[1][2] = cmul<T>(y[1][2], w2);
+    y[1][3] = cmul<T>(y[1][3], w3);
+    y[2][1] = cmul<T>(y[2][1], w2);
+    y[2][2] = cmuli<T>(y[2][2], sgn);
+    y[2][3] = cmul<T>(y[2][3], w6);
+    y[3][1] = cmul<T>(y[3][1], w3);
+    y[3][2] = cmul<T>(y[3][2], w6);
+    y[3][3] = cmul<T>(y[3][3], w9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      cplx<T> z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      Dft<T, 4>::run(z, sgn, nullptr, 0);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+    }
   }
 };
 
@@ -225,7 +262,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
 }
 
 // Full transform of `nlines` lines.  sgn = -1 forward, +1 inverse (unnormalised).
-// Stages are applied radix by radix (8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
+// Stages are applied radix by radix (16s in FP32 plans, 8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
 // formulation is valid for any order of the radices, and one loop per radix
 // keeps each stage's registers apart.  ES = 1: row tiles with line stride
 // `lstride` (nlines at run time), NL = 0; NL > 0: column tiles (line stride 1,
@@ -235,6 +272,8 @@ __device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int 
                                           int sgn) {
   const int N = pl.n;
   int Ns = 1;
+  if constexpr (sizeof(T) == 4)  // FP32 plans only: 16 complex per butterfly would crowd FP64 registers
+    for (int s = 0; s < pl.cnt[6]; ++s, Ns *= 16) fft_stage<T, 16, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);

@@ -14,7 +14,7 @@ namespace wfft {
 // (4*4 rather than 8*2), then the odd radices 3, 5, 7
 static inline bool factorize(int n, AxisPlan& pl) {
   pl.n = n;
-  for (int i = 0; i < 6; ++i) pl.cnt[i] = 0;
+  for (int i = 0; i < 7; ++i) pl.cnt[i] = 0;
   if (n < 1 || n > 512) return false;
   int m = n, e2 = 0;
   while (m % 2 == 0) {
@@ -37,24 +37,26 @@ static inline bool factorize(int n, AxisPlan& pl) {
   return m == 1;
 }
 
-// Every decomposition of n the FFT stages support: the power-of-two part as radix-8,
-// radix-4 and at most one radix-2 stage in any mix, the odd part as 3s, 5s and 7s
-// (the stage order is fixed: 8s, 4s, 2s, 3s, 5s, 7s).  Empty if n is not supported.
-static inline std::vector<AxisPlan> factor_candidates(int n) {
+// Every decomposition of n the FFT stages support: the power-of-two part as radix-16
+// (when allow16: FP32 plans), radix-8, radix-4 and at most one radix-2 stage in any
+// mix, the odd part as 3s, 5s and 7s.  Empty if n is not supported.
+static inline std::vector<AxisPlan> factor_candidates(int n, bool allow16) {
   std::vector<AxisPlan> out;
   AxisPlan base;
   if (!factorize(n, base)) return out;
   const int e2 = 3 * base.cnt[0] + 2 * base.cnt[1] + base.cnt[2];
-  for (int n8 = 0; 3 * n8 <= e2; ++n8)
-    for (int n2 = 0; n2 <= 1; ++n2) {
-      const int rest = e2 - 3 * n8 - n2;
-      if (rest < 0 || (rest & 1)) continue;
-      AxisPlan c = base;
-      c.cnt[0] = n8;
-      c.cnt[1] = rest / 2;
-      c.cnt[2] = n2;
-      out.push_back(c);
-    }
+  for (int n16 = 0; allow16 ? 4 * n16 <= e2 : n16 == 0; ++n16)
+    for (int n8 = 0; 4 * n16 + 3 * n8 <= e2; ++n8)
+      for (int n2 = 0; n2 <= 1; ++n2) {
+        const int rest = e2 - 4 * n16 - 3 * n8 - n2;
+        if (rest < 0 || (rest & 1)) continue;
+        AxisPlan c = base;
+        c.cnt[6] = n16;
+        c.cnt[0] = n8;
+        c.cnt[1] = rest / 2;
+        c.cnt[2] = n2;
+        out.push_back(c);
+      }
   return out;
 }
 

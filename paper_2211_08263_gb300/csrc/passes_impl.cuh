@@ -14,8 +14,8 @@ namespace wfft {
 template <typename T>
 static int max_tile_elems(const AxisPlan& pl, int thr) {
   int cap = 1 << 30;
-  const int rad[6] = {8, 4, 2, 3, 5, 7};
-  for (int i = 0; i < 6; ++i) {
+  const int rad[7] = {8, 4, 2, 3, 5, 7, 16};
+  for (int i = 0; i < 7; ++i) {
     if (!pl.cnt[i]) continue;
     const int R = rad[i];
     const int capR = sizeof(T) == 8 ? 8 : 16;

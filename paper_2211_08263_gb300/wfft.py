@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
     lib.wfft_profile_read.argtypes = [vp, i, i, P(C.c_longlong), P(C.c_longlong), P(d), P(d), P(d)]
     lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
     lib.wfft_autotune.argtypes = [vp, i, P(i)]
+    lib.wfft_set_radix.argtypes = [vp, i, i, P(i)]
     lib.wfft_explicit_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_dt.argtypes = [i, P(d), vp, vp, C.c_longlong, P(d)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
@@ -252,6 +253,11 @@ class Solver:
         d = info.as_dict()
         d["rc"] = rc
         return d
+
+    def set_radix(self, precision: int, axis: int, counts) -> None:
+        """Stages of radix 8, 4, 2, 3, 5, 7, 16 (counts, 7 entries) for one axis (wfft_set_radix)."""
+        c = (C.c_int * 7)(*[int(x) for x in counts])
+        self._check(self.lib.wfft_set_radix(self.h, int(precision), int(axis), c))
 
     def autotune(self, reps: int = 3) -> int:
         """Time and keep the fastest radix decompositions and column-tile widths

@@ -125,3 +125,42 @@ def test_preconditioner_inverts_homogeneous_operator_on_gpu():
     s.precond(q, z)
     torch.cuda.synchronize()
     assert rel(z.cpu().numpy(), u.cpu().numpy()) < 1e-13
+
+
+# hand-set radix schedules (wfft_set_radix): stages of radix 8, 4, 2, 3, 5, 7, 16
+RADIX_CASES = [
+    (3, (64, 32, 16), 1, [[0, 1, 0, 0, 0, 0, 1], [0, 0, 1, 0, 0, 0, 1], [0, 0, 0, 0, 0, 0, 1]]),
+    (3, (64, 32, 16), 0, [[0, 3, 0, 0, 0, 0, 0], [0, 2, 1, 0, 0, 0, 0], [1, 0, 1, 0, 0, 0, 0]]),
+    (2, (256, 48, 1), 1, [[0, 0, 0, 0, 0, 0, 2], [0, 0, 0, 1, 0, 0, 1], None]),
+]
+
+
+@pytest.mark.parametrize("ndim,n,prec,plans", RADIX_CASES)
+def test_hand_set_radix_schedules_match_oracle(ndim, n, prec, plans):
+    """Radix-16 stages (FP32) and other decompositions than the built-in one give the
+    same operator and preconditioner as the oracle, at the usual tolerances."""
+    from oracle import spectral
+    torch = torch_cuda()
+    wfft = solver_lib()
+    rng = np.random.default_rng(7 * sum(n) + prec)
+    prob = inputs.random_problem(rng, ndim, n, nphase=4, mask_width=2, contrast=4.0, dt=4e-7)
+    s = _solver(prob, prec)
+    for axis, cnt in enumerate(plans):
+        if cnt is not None:
+            s.set_radix(wfft.MIXED if prec else wfft.FP64, axis, cnt)
+    med, sp, th = _oracle_ops(prob)
+    dt = torch.float64 if prec == 0 else torch.float32
+    tol = 1e-12 if prec == 0 else 3e-6
+    p = rng.standard_normal((ndim, n[2], n[1], n[0]))
+    pd = to_dev(torch, p, dt)
+    qd = torch.zeros_like(pd)
+    s.apply(pd, qd, precision=prec, masked=False)
+    zd = torch.zeros_like(pd)
+    s.precond(pd, zd, precision=prec, masked=False)
+    torch.cuda.synchronize()
+    qo = spectral.apply_A(med, sp, oracle_field(prob, p), th)
+    zo = spectral.apply_M(med, sp, oracle_field(prob, p), th)
+    assert rel(oracle_field(prob, qd.cpu().numpy().astype(np.float64)), qo) < tol
+    assert rel(oracle_field(prob, zd.cpu().numpy().astype(np.float64)), zo) < tol
+    with pytest.raises(wfft.WfftError):
+        s.set_radix(wfft.FP64, 0, [0, 0, 0, 0, 0, 0, 1] if n[0] == 16 else [0, 0, 0, 0, 0, 0, 9])
