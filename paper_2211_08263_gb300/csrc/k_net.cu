@@ -172,8 +172,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs p) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[m][n][e] = 0.f;
 #pragma unroll 1
-    for (int o = 0; o < 27; ++o) {
-      const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+    for (int dz = 0; dz < 3; ++dz) {
+      // the nine (y, x) offsets of a z offset unrolled: the next offset's fragment loads
+      // can be issued under the current offset's MMAs
+#pragma unroll
+      for (int o9 = 0; o9 < 9; ++o9) {
+      const int dy = o9 / 3, dx = o9 % 3;
+      const int o = 9 * dz + o9;
 #pragma unroll
       for (int ks = 0; ks < CIN / 16; ++ks) {
         uint32_t A[2][4];
@@ -195,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs p) {
             mma_bf16(acc[m][2 * np + 1], A[m], B[2], B[3]);
           }
         }
+      }
       }
     }
     // epilogue: accumulator (m, n, e) is voxel x0 + g + 8 (e >> 1) of row (wz, wy0 + m),
