@@ -326,6 +326,23 @@ WFFT_API int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_step_
 WFFT_API int wfft_explicit_dt(int ndim, const double h[3], const double* C, const double* rho, long long nrows,
                               double* dt_max);
 
+/*
+ * The paper's own treatment of the prescribed region (Sec. 2.2.3, Eqs. f_discrete,
+ * solve_green, G, Vt, L-determination_ND; Alg. 2), for small regions; FP64 implicit
+ * handles only.  wfft_green_setup solves A g = e_(p,j) without the projection P for a
+ * unit force at every prescribed DOF (p, j) (PCG to tol), stores the responses at the
+ * prescribed DOFs as column (p, j) of the dense Green's matrix G (row = responding
+ * DOF), and inverts G on the GPU (Gauss-Jordan; G is symmetric positive definite).
+ * It refuses more than max_dofs prescribed DOFs (0: 4096) -- G takes n^2 doubles and
+ * n unit solves.  wfft_green_step then advances one Newmark step the paper's way:
+ * u_b = A^-1 b (unconstrained, from u_{n-1}), V = U(t_n) - u_b on Gamma,
+ * f = G^-1 V supported on Gamma, u_f = A^-1 f, u_n = u_b + u_f, then the corrector;
+ * it gives the same u_n as wfft_step up to the solver tolerance.  info: iters of both
+ * solves, outer_applies 2, reaction = sum rho a_n per component.
+ */
+WFFT_API int wfft_green_setup(wfft_handle* h, long long max_dofs);
+WFFT_API int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info* info);
+
 /* Kernel kinds of the launch accounting (wfft_profile_read). */
 #define WFFT_K_XFWD_PLAIN 0   /* x-axis real->half-spectrum pass */
 #define WFFT_K_XFWD_PUPD 1    /* ... fused with p = z + beta p */

@@ -56,6 +56,15 @@ struct wfft_handle {
   cudaGraphExec_t chunk[2] = {nullptr, nullptr};
   long long chunk_launches[2] = {0, 0};
   bool explicit_scheme = false;  // beta = 0, gamma = 1/2 (wfft_explicit_step)
+  int solve_masked = 1;          // 0 while a Green's-matrix solve runs (no projection P)
+  // Green's-matrix treatment of Gamma (wfft_green_setup)
+  long long green_n = 0;         // prescribed DOFs
+  long long* green_idx = nullptr;  // their global indices k V + vox, ascending
+  double* green_ginv = nullptr;  // G^-1, row-major green_n x green_n
+  double* green_v = nullptr;     // mismatch V
+  double* green_f = nullptr;     // G^-1 V
+  double* green_ub = nullptr;    // u_b of the current step
+  double* green_piv = nullptr;
   NetDev* net = nullptr;    // learned warm start (wfft_set_model)
   NetWork nw;
   float* delta = nullptr;   // FP64 handles: FP32 warm-start increment
@@ -554,9 +563,9 @@ static void pcg_chunk(wfft_handle* h, Plan<T>& P, Scalars* sc, cudaStream_t st) 
   const Desc<T>& D = P.h;
   const int op = D.opAxis;
   for (int i = 0; i < h->opt.check_every; ++i) {
-    launch_apply<T>(P, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, st);
+    launch_apply<T>(P, PRE_PUPD, SL_P, POST_APPLY, SL_Q, h->solve_masked, 1, st);
     launch_fin(sc, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_ALPHA, nullptr, st);
-    launch_precond<T>(P, PRE_RUPD, SL_R, SL_Z, 1, st);
+    launch_precond<T>(P, PRE_RUPD, SL_R, SL_Z, h->solve_masked, st);
     launch_fin(sc, D.part[PT_A], P.g.blk_x, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_BETA, nullptr, st);
   }
 }
@@ -568,7 +577,7 @@ static void pcg_chunk(wfft_handle* h, Plan<T>& P, Scalars* sc, cudaStream_t st) 
 // so a replay computes exactly what direct launches would.
 template <typename T>
 static int pcg_chunk_launch(wfft_handle* h, Plan<T>& P, Scalars* sc, int which) {
-  if (!h->opt.use_graphs || h->prof.on) {
+  if (!h->opt.use_graphs || h->prof.on || !h->solve_masked) {
     pcg_chunk<T>(h, P, sc, h->st);
     return WFFT_OK;
   }
@@ -1612,4 +1621,140 @@ extern "C" int wfft_set_radix(wfft_handle* h, int precision, int axis, const int
   ProfScope ps_(h);
   return precision == WFFT_FP64 ? set_radix_plan<double>(h, h->P64, axis, pl)
                                 : set_radix_plan<float>(h, h->P32, axis, pl);
+}
+
+// ---------------------------------------------------------------------------
+// Green's-matrix treatment of Gamma (Sec. 2.2.3, Eqs. f_discrete, G, Vt,
+// L-determination_ND; Alg. 2)
+// ---------------------------------------------------------------------------
+namespace {
+// x <- A^-1 b without the projection P (the unconstrained system of the Green's
+// functions), PCG from the guess in SL_X to tol * ||b||; b in SL_B.
+int green_solve(wfft_handle* h, int* iters) {
+  Plan<double>& P = h->P64;
+  const Desc<double>& D = P.h;
+  const int op = D.opAxis;
+  h->solve_masked = 0;
+  const double zero3[3] = {0.0, 0.0, 0.0};
+  launch_begin(h->sc64, zero3, 0, h->opt.tol * h->opt.tol, h->opt.maxit, h->st);
+  launch_green_norm2(P, reinterpret_cast<const double*>(D.slot[SL_B]), h->st);
+  launch_fin(h->sc64, D.part[PT_A], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
+  launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 0, 1, h->st);
+  launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_RES0, nullptr, h->st);
+  launch_precond<double>(P, PRE_PLAIN, SL_R, SL_Z, 0, h->st);
+  launch_fin(h->sc64, nullptr, 0, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, h->st);
+  const int watchdog = h->opt.watchdog_iters > 0 ? h->opt.watchdog_iters : 4 * h->opt.maxit;
+  int rc = pcg_loop<double>(h, P, h->sc64, 0, watchdog, iters);
+  h->solve_masked = 1;
+  if (rc == WFFT_OK && h->host_sc[0].status) rc = h->host_sc[0].status;
+  return rc;
+}
+}  // namespace
+
+extern "C" int wfft_green_setup(wfft_handle* h, long long max_dofs) {
+  ProfScope ps_(h);
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (h->explicit_scheme || h->opt.precision != WFFT_FP64)
+    return fail(h, WFFT_EINVAL, "the Green's-matrix mode needs an FP64 implicit handle");
+  if (!h->has_mask) return fail(h, WFFT_EINVAL, "no prescribed DOFs");
+  if (h->green_n) return WFFT_OK;
+  const long long cap = max_dofs > 0 ? max_dofs : 4096;
+  Plan<double>& P = h->P64;
+  const Desc<double>& D = P.h;
+  const long long V = h->V;
+  // prescribed DOF list k V + vox in ascending order, from the per-voxel mask bits
+  std::vector<uint8_t> mb((size_t)V);
+  CKH(h, cudaMemcpy(mb.data(), D.mask, (size_t)V, cudaMemcpyDeviceToHost));
+  std::vector<long long> idx;
+  for (int k = 0; k < h->c; ++k)
+    for (long long v = 0; v < V; ++v)
+      if ((mb[v] >> k) & 1) idx.push_back((long long)k * V + v);
+  const long long n = (long long)idx.size();
+  if (n > cap) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%lld prescribed DOFs exceed the Green's-matrix limit %lld (G is dense: n^2 doubles)",
+             n, cap);
+    return fail(h, WFFT_EINVAL, buf);
+  }
+  CKH(h, dalloc(h, &h->green_idx, (size_t)n * sizeof(long long)));
+  CKH(h, cudaMemcpy(h->green_idx, idx.data(), (size_t)n * sizeof(long long), cudaMemcpyHostToDevice));
+  CKH(h, dalloc(h, &h->green_ginv, (size_t)n * n * sizeof(double)));
+  CKH(h, dalloc(h, &h->green_v, (size_t)n * sizeof(double)));
+  CKH(h, dalloc(h, &h->green_f, (size_t)n * sizeof(double)));
+  CKH(h, dalloc(h, &h->green_ub, (size_t)h->c * V * sizeof(double)));
+  CKH(h, dalloc(h, &h->green_piv, sizeof(double)));
+  double* b = reinterpret_cast<double*>(D.slot[SL_B]);
+  double* x = reinterpret_cast<double*>(D.slot[SL_X]);
+  const size_t bytes = (size_t)h->c * V * sizeof(double);
+  // column (p, j) of G: the response at every prescribed DOF to a unit force at (p, j)
+  for (long long col = 0; col < n; ++col) {
+    CKH(h, cudaMemsetAsync(b, 0, bytes, h->st));
+    launch_green_unit(b, idx[col], h->st);
+    CKH(h, cudaMemsetAsync(x, 0, bytes, h->st));
+    int it = 0;
+    int rc = green_solve(h, &it);
+    if (rc) return fail(h, rc, "a unit-force solve of the Green's matrix did not converge");
+    launch_green_gather(x, h->green_idx, n, h->green_ginv + col, n, h->st);
+  }
+  // G^-1 in place (G is symmetric positive definite); green_v holds the pivot column
+  launch_green_invert(h->green_ginv, n, h->green_v, h->green_piv, h->st);
+  CKH(h, cudaGetLastError());
+  CKH(h, cudaStreamSynchronize(h->st));
+  h->green_n = n;
+  return WFFT_OK;
+}
+
+extern "C" int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info* info) {
+  ProfScope ps_(h);
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (!h->green_n) return fail(h, WFFT_EINVAL, "call wfft_green_setup first");
+  if (!U) return fail(h, WFFT_EINVAL, "U is NULL");
+  fill_info_base(info);
+  Plan<double>& P = h->P64;
+  const Desc<double>& D = P.h;
+  const long long n = h->green_n;
+  const double Uv[3] = {U[0], h->ndim > 1 ? U[1] : 0.0, h->ndim > 2 ? U[2] : 0.0};
+  double* b = reinterpret_cast<double*>(D.slot[SL_B]);
+  double* x = reinterpret_cast<double*>(D.slot[SL_X]);
+  const size_t bytes = (size_t)h->c * h->V * sizeof(double);
+  CKH(h, cudaEventRecord(h->ev0, h->st));
+  // predictor: b = rho u~, x = u_{n-1} (the guess of u_b)
+  launch_begin(h->sc64, Uv, WFFT_WARM_PREV, h->opt.tol * h->opt.tol, h->opt.maxit, h->st);
+  launch_predict(P, h->st);
+  CKH(h, cudaMemcpyAsync(x, D.slot[SL_U], bytes, cudaMemcpyDeviceToDevice, h->st));
+  int it1 = 0, it2 = 0;
+  int rc = green_solve(h, &it1);  // u_b = A^-1 b
+  if (rc) return fail(h, rc, "the unconstrained solve did not converge (step not committed)");
+  CKH(h, cudaMemcpyAsync(h->green_ub, x, bytes, cudaMemcpyDeviceToDevice, h->st));
+  // V = U - u_b on Gamma (Eq. Vt); f = G^-1 V; u_f = A^-1 f (f supported on Gamma)
+  launch_green_mismatch(h->green_ub, h->green_idx, n, h->V, Uv, h->green_v, h->st);
+  launch_green_gemv(h->green_ginv, h->green_v, n, h->green_f, h->st);
+  CKH(h, cudaMemsetAsync(b, 0, bytes, h->st));
+  launch_green_scatter(b, h->green_idx, n, h->green_f, h->st);
+  CKH(h, cudaMemsetAsync(x, 0, bytes, h->st));
+  rc = green_solve(h, &it2);
+  if (rc) return fail(h, rc, "the force solve did not converge (step not committed)");
+  // u_n = u_b + u_f, then the corrector (it rebuilds u~ from the unchanged state)
+  launch_green_axpy(P, x, h->green_ub, h->st);
+  launch_begin(h->sc64, Uv, WFFT_WARM_PREV, h->opt.tol * h->opt.tol, h->opt.maxit, h->st);
+  launch_correct(P, h->st);
+  const int nb = ew_block_count(P);
+  launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
+  CKH(h, cudaEventRecord(h->ev1, h->st));
+  CKH(h, cudaGetLastError());
+  rc = read_scalars(h);
+  if (rc) return rc;
+  for (int k = 0; k < 3; ++k) h->U_prev[k] = Uv[k];
+  h->au_valid = false;
+  ++h->nstep;
+  if (info) {
+    info->status = WFFT_OK;
+    info->iters = it1 + it2;
+    info->outer_applies = 2;
+    for (int k = 0; k < 3; ++k) info->reaction[k] = h->host_sc[0].react[k];
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->ms = ms;
+  }
+  return WFFT_OK;
 }

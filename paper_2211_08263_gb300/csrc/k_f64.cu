@@ -1,6 +1,7 @@
 // FP64 instantiation of the pass kernels plus the FP64-only kernels of the
 // Newmark step (Eq. Newmark, Eq. Fourier_ND_b, Alg. 2) and the single-block
 // finalize kernels that turn block partial sums into the Krylov scalars.
+#include <algorithm>
 #include <cmath>
 
 #include "finalize.cuh"
@@ -197,6 +198,89 @@ __global__ void __launch_bounds__(256) k_explicit_update(const Desc<double>* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Green's-matrix treatment of Gamma (Sec. 2.2.3, Eqs. f_discrete, G, Vt,
+// L-determination_ND; Alg. 2) -- small prescribed regions
+// ---------------------------------------------------------------------------
+// partial sums of ||f||^2 over a c-component field
+__global__ void __launch_bounds__(256) k_green_norm2(const Desc<double>* __restrict__ dd, const double* f) {
+  const Desc<double>& D = *dd;
+  const long long tot = (long long)D.c * D.V;
+  double acc = 0.0;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x)
+    acc += f[gi] * f[gi];
+  const double sum = block_sum(acc);
+  if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = sum;
+}
+
+// out[i] = x[idx[i]] (column of G from one unit-force response, or u_b on Gamma)
+__global__ void k_green_gather(const double* x, const long long* idx, long long n, double* out, long long stride) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i * stride] = x[idx[i]];
+}
+
+// V_i = U_k - ub[idx_i] with k the component of prescribed DOF i (Eq. Vt)
+__global__ void k_green_mismatch(const double* ub, const long long* idx, long long n, long long V, double U0,
+                                 double U1, double U2, double* out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx[i] / V);
+    out[i] = (k == 0 ? U0 : (k == 1 ? U1 : U2)) - ub[idx[i]];
+  }
+}
+
+// f = Ginv V: one warp per row (row-major n x n)
+__global__ void k_green_gemv(const double* Ginv, const double* v, long long n, double* f) {
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0;
+  for (long long j = lane; j < n; j += 32) acc += Ginv[row * n + j] * v[j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) f[row] = acc;
+}
+
+// b[idx_i] = f_i on a zeroed field
+__global__ void k_green_scatter(double* b, const long long* idx, long long n, const double* f) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[idx[i]] = f[i];
+}
+
+// dst[idx] = 1 on a zeroed field (unit force of Eq. f_discrete)
+__global__ void k_green_unit(double* b, long long gi) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) b[gi] = 1.0;
+}
+
+// x += y over a c-component field
+__global__ void __launch_bounds__(256) k_green_axpy(double* x, const double* y, long long tot) {
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
+       gi += (long long)gridDim.x * blockDim.x)
+    x[gi] += y[gi];
+}
+
+// In-place Gauss-Jordan inversion of the SPD matrix G (no pivoting needed), pivot k:
+//   piv = A_kk, col_i = A_ik;  A_kj <- (j == k ? 1 : A_kj) / piv;
+//   A_ij <- (j == k ? 0 : A_ij) - col_i A_kj for i != k.
+__global__ void k_gj_pivot(const double* A, long long n, long long k, double* col, double* piv) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    col[i] = A[i * n + k];
+    if (i == k) *piv = A[k * n + k];
+  }
+}
+__global__ void k_gj_row(double* A, long long n, long long k, const double* piv) {
+  const double p = *piv;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    A[k * n + j] = (j == k ? 1.0 : A[k * n + j]) / p;
+}
+__global__ void k_gj_eliminate(double* A, long long n, long long k, const double* col) {
+  const long long tot = n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e - i * n;
+    if (i == k) continue;
+    A[e] = (j == k ? 0.0 : A[e]) - col[i] * A[k * n + j];
+  }
+}
+
 static int ew_blocks(const Plan<double>& P) {
   const long long tot = (long long)P.h.c * P.h.V;
   long long nb = (tot + 255) / 256;
@@ -235,6 +319,46 @@ void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st
   prof_launch(0, KK_SCALAR, 8.0 * P.h.c * P.h.V, 0.0, st, [&] { k_fill_unit<<<ew_blocks(P), 256, 0, st>>>(P.d, j, dst); });
 }
 int ew_block_count(const Plan<double>& P) { return ew_blocks(P); }
+void launch_green_norm2(const Plan<double>& P, const double* f, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 8.0 * P.h.c * P.h.V, 2.0 * P.h.c * P.h.V, st,
+              [&] { k_green_norm2<<<ew_blocks(P), 256, 0, st>>>(P.d, f); });
+}
+static int small_blocks(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 1024)); }
+void launch_green_gather(const double* x, const long long* idx, long long n, double* out, long long stride,
+                         cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 16.0 * n, 0.0, st,
+              [&] { k_green_gather<<<small_blocks(n), 256, 0, st>>>(x, idx, n, out, stride); });
+}
+void launch_green_mismatch(const double* ub, const long long* idx, long long n, long long V, const double U[3],
+                           double* out, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 24.0 * n, (double)n, st, [&] {
+    k_green_mismatch<<<small_blocks(n), 256, 0, st>>>(ub, idx, n, V, U[0], U[1], U[2], out);
+  });
+}
+void launch_green_gemv(const double* Ginv, const double* v, long long n, double* f, cudaStream_t st) {
+  const long long warps = n, blocks = (warps * 32 + 255) / 256;
+  prof_launch(0, KK_SCALAR, 8.0 * n * n, 2.0 * n * n, st,
+              [&] { k_green_gemv<<<(int)blocks, 256, 0, st>>>(Ginv, v, n, f); });
+}
+void launch_green_scatter(double* b, const long long* idx, long long n, const double* f, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 24.0 * n, 0.0, st, [&] { k_green_scatter<<<small_blocks(n), 256, 0, st>>>(b, idx, n, f); });
+}
+void launch_green_unit(double* b, long long gi, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 8.0, 0.0, st, [&] { k_green_unit<<<1, 32, 0, st>>>(b, gi); });
+}
+void launch_green_axpy(const Plan<double>& P, double* x, const double* y, cudaStream_t st) {
+  const long long tot = (long long)P.h.c * P.h.V;
+  prof_launch(0, KK_NEWMARK, 24.0 * tot, (double)tot, st, [&] { k_green_axpy<<<ew_blocks(P), 256, 0, st>>>(x, y, tot); });
+}
+void launch_green_invert(double* A, long long n, double* col, double* piv, cudaStream_t st) {
+  const int eb = (int)std::max<long long>(1, std::min<long long>((n * n + 255) / 256, 4096));
+  for (long long k = 0; k < n; ++k) {
+    prof_launch(0, KK_SCALAR, 8.0 * n, 0.0, st, [&] { k_gj_pivot<<<small_blocks(n), 256, 0, st>>>(A, n, k, col, piv); });
+    prof_launch(0, KK_SCALAR, 16.0 * n, (double)n, st, [&] { k_gj_row<<<small_blocks(n), 256, 0, st>>>(A, n, k, piv); });
+    prof_launch(0, KK_SCALAR, 16.0 * n * n, 2.0 * n * n, st,
+                [&] { k_gj_eliminate<<<eb, 256, 0, st>>>(A, n, k, col); });
+  }
+}
 void launch_explicit_predict(const Plan<double>& P, cudaStream_t st) {
   const double cv = (double)P.h.c * P.h.V;
   prof_launch(0, KK_NEWMARK, 8 * cv * 4, cv * 5, st, [&] { k_explicit_predict<<<ew_blocks(P), 256, 0, st>>>(P.d); });

@@ -109,6 +109,18 @@ void launch_correct(const Plan<double>& P, cudaStream_t st, const BatchLaunch<do
 // from q = -div(C : grad^s u_n) in SL_Q.
 void launch_explicit_predict(const Plan<double>& P, cudaStream_t st);
 void launch_explicit_update(const Plan<double>& P, const double Udot[3], cudaStream_t st);
+// Green's-matrix treatment of Gamma: norms, gathers / scatters on the prescribed-DOF list,
+// G^-1 V, unit forces, and the in-place Gauss-Jordan inversion of G (SPD, no pivoting).
+void launch_green_norm2(const Plan<double>& P, const double* f, cudaStream_t st);
+void launch_green_gather(const double* x, const long long* idx, long long n, double* out, long long stride,
+                         cudaStream_t st);
+void launch_green_mismatch(const double* ub, const long long* idx, long long n, long long V, const double U[3],
+                           double* out, cudaStream_t st);
+void launch_green_gemv(const double* Ginv, const double* v, long long n, double* f, cudaStream_t st);
+void launch_green_scatter(double* b, const long long* idx, long long n, const double* f, cudaStream_t st);
+void launch_green_unit(double* b, long long gi, cudaStream_t st);
+void launch_green_axpy(const Plan<double>& P, double* x, const double* y, cudaStream_t st);
+void launch_green_invert(double* A, long long n, double* col, double* piv, cudaStream_t st);
 void launch_fill_unit(const Plan<double>& P, int j, double* dst, cudaStream_t st);
 
 }  // namespace wfft

@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
     lib.wfft_autotune.argtypes = [vp, i, P(i)]
     lib.wfft_set_radix.argtypes = [vp, i, i, P(i)]
+    lib.wfft_green_setup.argtypes = [vp, C.c_longlong]
+    lib.wfft_green_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_dt.argtypes = [i, P(d), vp, vp, C.c_longlong, P(d)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
@@ -253,6 +255,17 @@ class Solver:
         d = info.as_dict()
         d["rc"] = rc
         return d
+
+    def green_setup(self, max_dofs: int = 0) -> None:
+        """Build and invert the Green's matrix of the prescribed region (wfft_green_setup)."""
+        self._check(self.lib.wfft_green_setup(self.h, int(max_dofs)))
+
+    def green_step(self, U) -> dict:
+        """One Newmark step through the Green's matrix (wfft_green_step)."""
+        Uv = (C.c_double * 3)(*[float(x) for x in list(U)[:3]] + [0.0] * (3 - min(3, len(U))))
+        info = StepInfo()
+        self._check(self.lib.wfft_green_step(self.h, Uv, C.byref(info)))
+        return info.as_dict()
 
     def set_radix(self, precision: int, axis: int, counts) -> None:
         """Stages of radix 8, 4, 2, 3, 5, 7, 16 (counts, 7 entries) for one axis (wfft_set_radix)."""
