@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the launch-bound C1 (64^2) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT plans (no wfft_autotune)")
     ap.add_argument("--no-explicit", action="store_true", help="skip the explicit-scheme measurement")
+    ap.add_argument("--plan", default=None, help="JSON plan choices to apply instead of autotuning")
+    ap.add_argument("--save-plan", default=None, help="write the plan choices of the timed handles (JSON)")
     ap.add_argument("--inner-floor", type=float, default=None,
                     help="mixed modes: stop an inner solve at this fraction of the outer target")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
@@ -206,6 +208,8 @@ def train_warm_start(wfft, args, stream):
 
 PROF_STEPS = 3
 INNER_FLOOR = None  # None: the library default
+PLAN = None         # plan choices to apply instead of tuning (--plan)
+PLANS_USED = {}     # plan choices of the timed handles, per precision
 
 
 def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None, autotune=True):
@@ -226,7 +230,15 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
         return sv
 
     s = make()
-    tuned = s.autotune(3) if autotune else None
+    precs = [wfft.FP64] + ([wfft.MIXED] if prec == "MIXED" else [])
+    if PLAN is not None:
+        for pr in precs:
+            s.set_plan(pr, PLAN["fp64" if pr == wfft.FP64 else "fp32"])
+        tuned = "from plan file"
+    else:
+        tuned = s.autotune(3) if autotune else None
+    for pr in precs:
+        PLANS_USED["fp64" if pr == wfft.FP64 else "fp32"] = s.get_plan(pr)
     for n in range(W):
         s.step(prob.U[n])
     torch.cuda.synchronize()
@@ -262,8 +274,8 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
         # field u_n copied back to pinned host memory after every step
         host_u = torch.empty(s.shape, dtype=torch.float64, pin_memory=True).numpy()
         s2 = make()
-        if autotune:
-            s2.autotune(3)  # the plan cached by the first handle: no timing
+        for pr in precs:
+            s2.set_plan(pr, PLANS_USED["fp64" if pr == wfft.FP64 else "fp32"])
         for n in range(W):
             s2.step(prob.U[n])
         torch.cuda.synchronize()
@@ -426,9 +438,11 @@ def run_reference(args, prob, rank, world):
 
 def main():
     args = parse()
-    global INNER_FLOOR
+    global INNER_FLOOR, PLAN
     if args.inner_floor is not None:
         INNER_FLOOR = args.inner_floor
+    if args.plan:
+        PLAN = json.load(open(args.plan))
     rank, world, local = dist_env()
     from paper_2211_08263_gb300 import inputs
     W, K = args.warmup, args.steps
@@ -510,6 +524,10 @@ def main():
         nr = net_roofline(results["learned"]["profile"])
         if nr:
             line["roofline_net"] = nr
+    line["plans"] = PLANS_USED
+    if args.save_plan and rank == 0:
+        with open(args.save_plan, "w") as f:
+            json.dump(PLANS_USED, f)
     if not args.no_small:
         line["small_grid"] = small_grid(wfft, torch)
     if not args.no_explicit:

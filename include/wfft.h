@@ -299,6 +299,19 @@ WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
  * Synchronises the stream.
  */
 WFFT_API int wfft_set_radix(wfft_handle* h, int precision, int axis, const int cnt[7]);
+/* The plan choices of one precision: radix[axis][r] stage counts (as wfft_set_radix) and
+   bx[axis][op] column-tile widths (axes 1, 2; op 0 forward, 1 inverse, 2 gradient, 3
+   divergence, 4 preconditioner; entries of passes the grid does not run are ignored).
+   wfft_get_plan reads them (e.g. after wfft_autotune); wfft_set_plan applies them to a
+   handle of the same grid, so a tuned plan can be kept and reused without timing.  A
+   choice that does not fit the grid, the register batch, 64 KB of shared memory or the
+   handle's partial-sum slots is refused (EINVAL, plan unchanged). */
+typedef struct {
+  int radix[3][7];
+  int bx[3][5];
+} wfft_plan_choice;
+WFFT_API int wfft_get_plan(const wfft_handle* h, int precision, wfft_plan_choice* out);
+WFFT_API int wfft_set_plan(wfft_handle* h, int precision, const wfft_plan_choice* in);
 
 /*
  * Explicit central-difference scheme (Sec. 2.3, Eq. Central_diff_rule, Eq.

@@ -1758,3 +1758,82 @@ extern "C" int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info
   }
   return WFFT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// plan choices (radix schedules and column-tile widths): export / import
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+void get_plan(const Plan<T>& P, wfft_plan_choice* out) {
+  for (int a = 0; a < 3; ++a) {
+    for (int r = 0; r < 7; ++r) out->radix[a][r] = P.h.ax[a].cnt[r];
+    for (int op = 0; op < 5; ++op) out->bx[a][op] = P.g.bx[a][op];
+  }
+}
+
+template <typename T>
+int set_plan(wfft_handle* h, Plan<T>& P, const wfft_plan_choice* in) {
+  static const int rad[7] = {8, 4, 2, 3, 5, 7, 16};
+  Desc<T>& D = P.h;
+  AxisPlan ax[3];
+  for (int a = 0; a < 3; ++a) {
+    long long prod = 1;
+    ax[a].n = h->n[a];
+    for (int r = 0; r < 7; ++r) {
+      const int c = in->radix[a][r];
+      if (c < 0 || c > 16) return fail(h, WFFT_EINVAL, "stage counts must be 0..16");
+      ax[a].cnt[r] = c;
+      for (int k = 0; k < c; ++k) prod *= rad[r];
+    }
+    if (prod != h->n[a]) return fail(h, WFFT_EINVAL, "a radix schedule does not multiply to its axis length");
+    if (sizeof(T) == 8 && ax[a].cnt[6]) return fail(h, WFFT_EINVAL, "radix-16 stages are FP32 only");
+  }
+  const Desc<T> saved = D;
+  const PassGeo gsaved = P.g;
+  for (int a = 0; a < 3; ++a) D.ax[a] = ax[a];
+  plan_geometry<T>(P);
+  for (int a = 1; a <= 2; ++a)
+    for (int op = 0; op < 5; ++op) {
+      if (!ops_of_axis(D, a, op)) continue;
+      if (!col_bx_feasible<T>(P, a, op, in->bx[a][op])) {
+        D = saved;
+        P.g = gsaved;
+        return fail(h, WFFT_EINVAL, "a column-tile width is not feasible for this plan");
+      }
+      set_col_bx<T>(P, a, op, in->bx[a][op]);
+    }
+  if (P.g.max_blocks > h->nparts) {
+    D = saved;
+    P.g = gsaved;
+    return fail(h, WFFT_EINVAL, "this plan needs more partial-sum slots than the handle has");
+  }
+  CKH(h, cudaStreamSynchronize(h->st));
+  CKH(h, upload_desc(P));
+  for (int k = 0; k < 2; ++k)
+    if (h->chunk[k]) {
+      cudaGraphExecDestroy(h->chunk[k]);
+      h->chunk[k] = nullptr;
+    }
+  return WFFT_OK;
+}
+}  // namespace
+
+extern "C" int wfft_get_plan(const wfft_handle* h, int precision, wfft_plan_choice* out) {
+  if (!h || !out || (precision != WFFT_FP64 && precision != WFFT_MIXED))
+    return fail(nullptr, WFFT_EINVAL, "handle, precision WFFT_FP64 / WFFT_MIXED and out are required");
+  memset(out, 0, sizeof(*out));
+  if (precision == WFFT_FP64)
+    get_plan<double>(h->P64, out);
+  else
+    get_plan<float>(h->P32, out);
+  return WFFT_OK;
+}
+
+extern "C" int wfft_set_plan(wfft_handle* h, int precision, const wfft_plan_choice* in) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (!in || (precision != WFFT_FP64 && precision != WFFT_MIXED))
+    return fail(h, WFFT_EINVAL, "precision WFFT_FP64 / WFFT_MIXED and the plan are required");
+  if (h->prof.on) return fail(h, WFFT_EINVAL, "switch profiling off before changing plans");
+  ProfScope ps_(h);
+  return precision == WFFT_FP64 ? set_plan<double>(h, h->P64, in) : set_plan<float>(h, h->P32, in);
+}

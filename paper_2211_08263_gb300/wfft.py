@@ -44,6 +44,10 @@ class Options(C.Structure):
                 ("watchdog_iters", C.c_int), ("use_graphs", C.c_int), ("inner_floor", C.c_double)]
 
 
+class PlanChoice(C.Structure):
+    _fields_ = [("radix", (C.c_int * 7) * 3), ("bx", (C.c_int * 5) * 3)]
+
+
 class StepInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("outer_applies", C.c_int), ("sweeps", C.c_int),
                 ("ref", C.c_double), ("rel_res", C.c_double), ("reaction", C.c_double * 3), ("ms", C.c_double)]
@@ -98,6 +102,8 @@ def load(path: str = LIB_PATH):
     lib.wfft_launch_count.argtypes = [vp, P(C.c_longlong)]
     lib.wfft_autotune.argtypes = [vp, i, P(i)]
     lib.wfft_set_radix.argtypes = [vp, i, i, P(i)]
+    lib.wfft_get_plan.argtypes = [vp, i, P(PlanChoice)]
+    lib.wfft_set_plan.argtypes = [vp, i, P(PlanChoice)]
     lib.wfft_green_setup.argtypes = [vp, C.c_longlong]
     lib.wfft_green_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_step.argtypes = [vp, P(d), P(StepInfo)]
@@ -266,6 +272,22 @@ class Solver:
         info = StepInfo()
         self._check(self.lib.wfft_green_step(self.h, Uv, C.byref(info)))
         return info.as_dict()
+
+    def get_plan(self, precision: int) -> dict:
+        """{"radix": 3 x 7 stage counts, "bx": 3 x 5 column-tile widths} (wfft_get_plan)."""
+        pc = PlanChoice()
+        self._check(self.lib.wfft_get_plan(self.h, int(precision), C.byref(pc)))
+        return {"radix": [list(r) for r in pc.radix], "bx": [list(r) for r in pc.bx]}
+
+    def set_plan(self, precision: int, plan: dict) -> None:
+        """Apply plan choices read by get_plan (wfft_set_plan)."""
+        pc = PlanChoice()
+        for a in range(3):
+            for r in range(7):
+                pc.radix[a][r] = int(plan["radix"][a][r])
+            for o in range(5):
+                pc.bx[a][o] = int(plan["bx"][a][o])
+        self._check(self.lib.wfft_set_plan(self.h, int(precision), C.byref(pc)))
 
     def set_radix(self, precision: int, axis: int, counts) -> None:
         """Stages of radix 8, 4, 2, 3, 5, 7, 16 (counts, 7 entries) for one axis (wfft_set_radix)."""

@@ -247,15 +247,19 @@ def test_autotuned_plan_keeps_the_results(precision, tol, bar):
     plain = wfft.Solver.from_problem(prob, options=opt())
     again = wfft.Solver.from_problem(prob, options=opt())
     assert again.autotune(2) == changed
+    copied = wfft.Solver.from_problem(prob, options=opt())   # the tuned choices set by hand
+    for pr in ([wfft.FP64] + ([wfft.MIXED] if precision == 1 else [])):
+        copied.set_plan(pr, tuned.get_plan(pr))
+        assert copied.get_plan(pr) == tuned.get_plan(pr)
     for k in range(prob.nsteps):
-        for s in (tuned, plain, again):
+        for s in (tuned, plain, again, copied):
             assert s.step(prob.U[k])["status"] == 0
-    ut, up, ua = (s.get_state()[0] for s in (tuned, plain, again))
-    assert np.array_equal(ut, ua)
+    ut, up, ua, uc = (s.get_state()[0] for s in (tuned, plain, again, copied))
+    assert np.array_equal(ut, ua) and np.array_equal(ut, uc)
     assert rel(ut, up) < bar
     so, _ = newmark.oracle_from_problem(prob, tol=1e-13).run(prob.U)
     assert rel(oracle_field(prob, ut), so.u) < bar
-    for s in (tuned, plain, again):
+    for s in (tuned, plain, again, copied):
         s.close()
 
 
