@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--inner-floor", type=float, default=None,
                     help="mixed modes: stop an inner solve at this fraction of the outer target")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
+    ap.add_argument("--no-incr-resid", action="store_true",
+                    help="mixed modes: every residual is a full FP64 application (no incremental residual)")
     return ap.parse_args()
 
 
@@ -210,6 +212,7 @@ PROF_STEPS = 3
 INNER_FLOOR = None  # None: the library default
 PLAN = None         # plan choices to apply instead of tuning (--plan)
 PLANS_USED = {}     # plan choices of the timed handles, per precision
+NO_INCR = False     # --no-incr-resid: full FP64 residuals only
 
 
 def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None, autotune=True):
@@ -222,6 +225,8 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
         opt.inner_tol = inner_tol
     if INNER_FLOOR is not None:
         opt.inner_floor = INNER_FLOOR
+    if NO_INCR:
+        opt.incr_resid = 0
 
     def make():
         sv = wfft.Solver.from_problem(prob, options=opt, stream=stream.cuda_stream)
@@ -267,6 +272,7 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
     res = {"ms_total": ms, "iters": sum(i["iters"] for i in infos),
            "outer_applies": sum(i["outer_applies"] for i in infos),
            "sweeps": sum(i["sweeps"] for i in infos), "rel_res_max": max(i["rel_res"] for i in infos),
+           "incr_resids": sum(i["incr_resids"] for i in infos),
            "launches": launches, "profile": prof, "iters_per_step": [i["iters"] for i in infos],
            "autotune_changed": tuned}
     if e2e:
@@ -438,9 +444,10 @@ def run_reference(args, prob, rank, world):
 
 def main():
     args = parse()
-    global INNER_FLOOR, PLAN
+    global INNER_FLOOR, PLAN, NO_INCR
     if args.inner_floor is not None:
         INNER_FLOOR = args.inner_floor
+    NO_INCR = args.no_incr_resid
     if args.plan:
         PLAN = json.load(open(args.plan))
     rank, world, local = dist_env()
@@ -493,6 +500,7 @@ def main():
         modes_out[MODES[m][0]] = {"ms_per_step": r["ms_total"] / K, "s_per_step": r["ms_total"] / K / 1e3,
                         "voxel_iters_per_s": V * r["iters"] / (r["ms_total"] * 1e-3),
                         "krylov_iters_per_step": r["iters"] / K, "fp64_applies_per_step": r["outer_applies"] / K,
+                        "incr_resids_per_step": r["incr_resids"] / K,
                         "sweeps_per_step": r["sweeps"] / K, "max_rel_res": r["rel_res_max"],
                         "autotune_changed": r["autotune_changed"],
                         "iters_per_step": r["iters_per_step"]}

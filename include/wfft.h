@@ -86,6 +86,16 @@ typedef struct {
   double inner_floor;/* mixed: an FP32 inner solve also stops once its residual is below
                         inner_floor * tol * ref (the outer target), so the last sweep does not
                         overshoot it; 0 = off.  The FP64 residual still decides convergence. */
+  int incr_resid;    /* mixed: 1 = the residual after a sweep that started from a full FP64
+                        residual evaluation may be formed incrementally, b - (A x + xc A d): A x
+                        the FP64 product kept from that evaluation, A d the FP32 product of the
+                        sweep's correction d, accumulated in FP64.  Taken only when the rounding
+                        estimate 8 * 2^-24 * lam_max(A) * ||xc d|| (lam_max bounded from C, rho,
+                        the grid and theta, see wfft_operator_bound; 8 is eleven times the
+                        largest measured ratio of the FP32 product's error to 2^-24 lam_max ||d||)
+                        is at most tol * ref / 4; the estimate is added to ||r|| in the
+                        convergence test.  At most one such update follows a full evaluation.
+                        0 = every residual is a full FP64 application. */
 } wfft_options;
 
 typedef struct {
@@ -97,10 +107,11 @@ typedef struct {
   double rel_res;      /* final ||P(b - A x)||_2 / ref (FP64 true residual in mixed mode) */
   double reaction[3];  /* sum over the grid of rho a_n per component = total force on Gamma */
   double ms;           /* device time of the call (CUDA events) */
+  int incr_resids;     /* mixed: incremental residual evaluations (see wfft_options.incr_resid) */
 } wfft_step_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-10, maxit 1000, WARM_PREV, inner_tol 1e-5,
-   max_sweeps 20, check_every 4, use_graphs 1, inner_floor 0.5. */
+   max_sweeps 20, check_every 4, use_graphs 1, inner_floor 0.5, incr_resid 1. */
 WFFT_API int wfft_default_options(wfft_options* opt);
 
 /*
@@ -338,6 +349,18 @@ WFFT_API int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_step_
  */
 WFFT_API int wfft_explicit_dt(int ndim, const double h[3], const double* C, const double* rho, long long nrows,
                               double* dt_max);
+
+/*
+ * Upper bound of the largest eigenvalue of the operator A u = rho u + theta B^T C B u
+ * (Eq. A_oper, Eq. G_oper) on the periodic grid n[] with voxel sizes h[]:
+ * max rho + theta * max_x lambda_max(C(x)) * |xi|_max^2, lambda_max of C taken on
+ * symmetric tensors (Mandel form of the Voigt matrix; 2-D: the in-plane block) and
+ * |xi|_max^2 = sum_i (2 pi / (N_i h_i) * floor((N_i - 1) / 2))^2.  Exact per-row
+ * eigenvalues up to 4096 rows, Gershgorin row sums above.  The incremental residual of
+ * a mixed solve scales its rounding bound with this value.  Host computation only.
+ */
+WFFT_API int wfft_operator_bound(int ndim, const int n[3], const double h[3], const double* C, const double* rho,
+                                 long long nrows, double theta, double* lam_max);
 
 /*
  * The paper's own treatment of the prescribed region (Sec. 2.2.3, Eqs. f_discrete,

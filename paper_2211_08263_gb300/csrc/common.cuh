@@ -42,6 +42,9 @@ struct Scalars {
   double dU[3];     // U(t_n) - U(t_{n-1}) (stored-A u initial residual)
   double tol2_base; // inner: inner_tol^2 as set at the start of the step
   double floor_fac; // outer: an inner solve may stop at floor_fac * tol * ref (0: off)
+  double rbound;    // outer: estimate of the rounding error of the next residual evaluation's
+                    // norm (incremental residuals); consumed by that evaluation's finalize
+  double dnorm2;    // outer: ||d||^2 of the latest FP32 inner correction
   int iter;         // operator applications inside the Krylov loop
   int maxit;
   int done;         // 1: every kernel of this solve returns immediately

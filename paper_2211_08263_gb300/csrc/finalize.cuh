@@ -5,7 +5,7 @@
 
 namespace wfft {
 
-enum FinMode { FIN_REF = 0, FIN_RES0, FIN_RZ0, FIN_ALPHA, FIN_BETA, FIN_OUTER, FIN_REACT, FIN_CLOSE };
+enum FinMode { FIN_REF = 0, FIN_RES0, FIN_RZ0, FIN_ALPHA, FIN_BETA, FIN_OUTER, FIN_REACT, FIN_CLOSE, FIN_DNORM };
 
 // Grid size cap of the elementwise FP64 kernels (and so a lower bound on the
 // length of every partial-sum array).
@@ -39,8 +39,20 @@ void launch_begin_batch(const BeginJob* jobs, int n, cudaStream_t st);
 void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb, const double* pc, int nc, int mode,
                 Scalars* sc2, cudaStream_t st);
 void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st,
-                  int use_au = 0, const double* dU = nullptr, double flr = 0.0);
+                  int use_au = 0, const double* dU = nullptr, double flr = 0.0, double rb = 0.0);
 void launch_set_done(Scalars* sc, int done, cudaStream_t st);
 int ew_block_count(const Plan<double>& P);
+
+// Incremental residual of a mixed solve (after a sweep that followed a full FP64
+// residual evaluation):
+//   launch_dnorm2: partial sums of ||d||^2 of the FP32 correction d (P's SL_D) into PT_C;
+//   launch_incr_begin: sc64->rbound = rb (the rounding estimate of the residual about to be
+//     formed) and re-opens the FP32 scalars so that an FP32 application of d runs;
+//   launch_resid_incr: with q32 = A d in FP32 and xc = ||r|| of the sweep's start,
+//     x += xc d, A x += xc q32 (SL_AU), r = [P](b - A x) (SL_R64), partial sums of
+//     ||r||^2 into PT_A (ew_block_count(P) blocks).
+void launch_dnorm2(const Plan<double>& P, cudaStream_t st);
+void launch_incr_begin(Scalars* sc64, Scalars* sc32, double rb, cudaStream_t st);
+void launch_resid_incr(const Plan<double>& P, const float* q32, int masked, cudaStream_t st);
 
 }  // namespace wfft

@@ -144,6 +144,88 @@ static inline double acoustic_max_eig(const double* c21, int ndim, const double 
   return std::max(Q[0][0], std::max(Q[1][1], Q[2][2]));
 }
 
+// Largest eigenvalue of a symmetric n x n matrix (n <= 6, row-major, overwritten):
+// cyclic Jacobi rotations.
+static inline double sym_max_eig(double* a, int n) {
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int p = 0; p < n; ++p) {
+      diag += a[p * n + p] * a[p * n + p];
+      for (int q = p + 1; q < n; ++q) off += a[p * n + q] * a[p * n + q];
+    }
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (a[p * n + q] == 0.0) continue;
+        const double th = (a[q * n + q] - a[p * n + p]) / (2.0 * a[p * n + q]);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < n; ++r) {
+          const double x = a[r * n + p], y = a[r * n + q];
+          a[r * n + p] = c * x - sn * y;
+          a[r * n + q] = sn * x + c * y;
+        }
+        for (int r = 0; r < n; ++r) {
+          const double x = a[p * n + r], y = a[q * n + r];
+          a[p * n + r] = c * x - sn * y;
+          a[q * n + r] = sn * x + c * y;
+        }
+      }
+  }
+  double m = a[0];
+  for (int p = 1; p < n; ++p) m = std::max(m, a[p * n + p]);
+  return m;
+}
+
+// Upper bound of the largest eigenvalue of C(x) as a map on symmetric tensors
+// (Mandel form: the Voigt matrix with the shear rows and columns scaled by sqrt2,
+// so that eps : C : eps = e^T M e with |e| = |eps|_F); 2-D takes the in-plane block.
+// exact: Jacobi; otherwise the Gershgorin row-sum bound (cheap, for per-voxel tables).
+static inline double mandel_max_eig(const double* c21, int ndim, bool exact) {
+  double m6[36];
+  voigt_full(c21, m6);
+  const double w[6] = {1.0, 1.0, 1.0, 1.4142135623730951, 1.4142135623730951, 1.4142135623730951};
+  static const int in2[3] = {0, 1, 5};
+  const int n = ndim == 3 ? 6 : 3;
+  double a[36];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int I = ndim == 3 ? i : in2[i], J = ndim == 3 ? j : in2[j];
+      a[i * n + j] = m6[I * 6 + J] * w[I] * w[J];
+    }
+  if (exact) return sym_max_eig(a, n);
+  double g = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += std::fabs(a[i * n + j]);
+    g = std::max(g, s);
+  }
+  return g;
+}
+
+// Upper bound of the largest eigenvalue of the operator A u = rho u + theta B^T C B u
+// (Eq. A_oper) on a periodic grid: for any u, u^T B^T C B u = sum_x eps : C : eps <=
+// max_x lambda_max(C(x)) |B u|^2 and |B u| <= |xi|_max |u| (|sym(xi (x) u)|_F <= |xi| |u|),
+// with |xi|_max^2 = sum_i (2 pi / L_i * floor((N_i - 1) / 2))^2 (the Nyquist index carries
+// no frequency).  rows: nrows Voigt rows of 21 values with their densities.
+static inline double operator_max_eig_bound(int ndim, const int n[3], const double h[3], const double* c21,
+                                            const double* rho, long long nrows, double theta) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double xi2 = 0.0;
+  for (int i = 0; i < ndim; ++i) {
+    const double k = (double)((n[i] - 1) / 2);
+    const double x = two_pi / (n[i] * h[i]) * k;
+    xi2 += x * x;
+  }
+  const bool exact = nrows <= 4096;
+  double cmax = 0.0, rmax = 0.0;
+  for (long long r = 0; r < nrows; ++r) {
+    cmax = std::max(cmax, mandel_max_eig(c21 + 21 * r, ndim, exact));
+    rmax = std::max(rmax, rho[r]);
+  }
+  return rmax + theta * cmax * xi2;
+}
+
 // Quadratic-form coefficients of theta*K(xi), K = B^T Cbar B (Eq. acous), B the
 // engineering strain-displacement map of xi.
 static inline void precond_coeffs(const double* cbar21, double theta, double kq[6][6]) {

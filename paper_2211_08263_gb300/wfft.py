@@ -41,7 +41,8 @@ class Grid(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("warm_start", C.c_int),
                 ("inner_tol", C.c_double), ("max_sweeps", C.c_int), ("check_every", C.c_int),
-                ("watchdog_iters", C.c_int), ("use_graphs", C.c_int), ("inner_floor", C.c_double)]
+                ("watchdog_iters", C.c_int), ("use_graphs", C.c_int), ("inner_floor", C.c_double),
+                ("incr_resid", C.c_int)]
 
 
 class PlanChoice(C.Structure):
@@ -50,12 +51,13 @@ class PlanChoice(C.Structure):
 
 class StepInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("outer_applies", C.c_int), ("sweeps", C.c_int),
-                ("ref", C.c_double), ("rel_res", C.c_double), ("reaction", C.c_double * 3), ("ms", C.c_double)]
+                ("ref", C.c_double), ("rel_res", C.c_double), ("reaction", C.c_double * 3), ("ms", C.c_double),
+                ("incr_resids", C.c_int)]
 
     def as_dict(self):
         return {"status": self.status, "iters": self.iters, "outer_applies": self.outer_applies,
                 "sweeps": self.sweeps, "ref": self.ref, "rel_res": self.rel_res,
-                "reaction": list(self.reaction), "ms": self.ms}
+                "reaction": list(self.reaction), "ms": self.ms, "incr_resids": self.incr_resids}
 
 
 _lib = None
@@ -108,6 +110,7 @@ def load(path: str = LIB_PATH):
     lib.wfft_green_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_dt.argtypes = [i, P(d), vp, vp, C.c_longlong, P(d)]
+    lib.wfft_operator_bound.argtypes = [i, P(i), P(d), vp, vp, C.c_longlong, d, P(d)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
     lib.wfft_model_bytes.argtypes = [i]
     lib.wfft_model_bytes.restype = C.c_size_t
@@ -505,6 +508,18 @@ class Trainer:
             self.close()
         except Exception:
             pass
+
+
+def operator_bound(ndim: int, n, h, C_table: np.ndarray, rho: np.ndarray, theta: float) -> float:
+    """Upper bound of the largest eigenvalue of A = rho + theta B^T C B (wfft_operator_bound)."""
+    Ct = np.ascontiguousarray(C_table, dtype=np.float64).reshape(-1, 21)
+    r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+    nn = (C.c_int * 3)(*[int(x) for x in list(n)[:3]] + [1] * (3 - min(3, len(n))))
+    hh = (C.c_double * 3)(*[float(x) for x in list(h)[:3]] + [1.0] * (3 - min(3, len(h))))
+    out = C.c_double()
+    _raise_global(load().wfft_operator_bound(int(ndim), nn, hh, _ptr(Ct), _ptr(r), Ct.shape[0], float(theta),
+                                             C.byref(out)))
+    return out.value
 
 
 def explicit_dt(ndim: int, h, C_table: np.ndarray, rho: np.ndarray) -> float:

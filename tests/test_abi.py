@@ -132,3 +132,36 @@ def test_explicit_stable_increment_matches_the_reference(lib, ndim):
     dt = wfft.explicit_dt(ndim, prob.h, prob.C, prob.rho)
     ref = explicit.stable_dt(medium.medium_from_problem(prob))
     assert abs(dt - ref) <= 1e-12 * ref, (dt, ref)
+
+
+@pytest.mark.parametrize("ndim,n,dense_tables", [(2, (8, 6, 1), False), (3, (6, 5, 4), False), (3, (4, 5, 3), True),
+                                                 (2, (7, 9, 1), True)])
+def test_operator_bound_covers_the_dense_operator(lib, ndim, n, dense_tables):
+    """wfft_operator_bound (host only) is an upper bound of the largest eigenvalue of the
+    assembled operator of the oracle (Eq. A_oper), and not a loose one."""
+    from oracle import dense, medium
+    from paper_2211_08263_gb300 import inputs, wfft
+    rng = np.random.default_rng(5 * ndim + sum(n))
+    prob = inputs.random_problem(rng, ndim, n, nphase=4, mask_width=1, nsteps=1, dense=dense_tables,
+                                 contrast=4.0, dt=4e-7)
+    th = prob.beta * prob.dt ** 2
+    A = dense.dense_operator(medium.medium_from_problem(prob), th)
+    lam = np.linalg.eigvalsh(A.toarray() if hasattr(A, "toarray") else A).max()
+    bound = wfft.operator_bound(ndim, prob.n, prob.h, prob.C, prob.rho, th)
+    assert lam <= bound * (1 + 1e-12), (lam, bound)
+    assert bound <= 4.0 * lam, (lam, bound)
+
+
+def test_operator_bound_homogeneous_isotropic_closed_form(lib):
+    """Isotropic C on symmetric tensors has eigenvalues 3 lambda + 2 mu (once) and 2 mu:
+    the bound is rho + theta (3 lambda + 2 mu) |xi|_max^2 with the largest discrete
+    frequency 2 pi floor((N-1)/2) / L per axis."""
+    from paper_2211_08263_gb300 import inputs, wfft
+    E, nu, rho = 200e9, 0.3, 7800.0
+    lam_, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    Cv = inputs.voigt21_from_matrix(inputs.isotropic_voigt(E, nu))[None]
+    n, h, th = (16, 9, 8), (1e-3, 2e-3, 1.5e-3), 1e-14
+    xi2 = sum((2 * np.pi / (n[i] * h[i]) * ((n[i] - 1) // 2)) ** 2 for i in range(3))
+    expect = rho + th * (3 * lam_ + 2 * mu) * xi2
+    got = wfft.operator_bound(3, n, h, Cv, np.array([rho]), th)
+    assert abs(got - expect) <= 1e-12 * expect, (got, expect)
