@@ -289,8 +289,10 @@ WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], 
 /*
  * Autotuner (not in the paper).  Times, on this handle's grid and device, every
  * radix decomposition the FFT stages support for each axis (the power-of-two part
- * as radix-8 / radix-4 / one radix-2 stage in any mix) and then every feasible
- * column-tile width of each column pass, one choice at a time, each candidate by
+ * as radix-16 (FP32) / radix-8 / radix-4 / one radix-2 stage in any mix), then the
+ * x-pass tile size (1024, 2048, 4096 complex elements, capped by the register batch),
+ * then every feasible column-tile width of each column pass, one choice at a time,
+ * each candidate by
  * `reps` (0: 3) operator + preconditioner applications; keeps the fastest plan for
  * the handle's solve precision(s) and caches it per (precision, grid, device) for
  * later handles of the process (which then need no timing).  Plans that would need
@@ -310,9 +312,11 @@ WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
  * Synchronises the stream.
  */
 WFFT_API int wfft_set_radix(wfft_handle* h, int precision, int axis, const int cnt[7]);
-/* The plan choices of one precision: radix[axis][r] stage counts (as wfft_set_radix) and
+/* The plan choices of one precision: radix[axis][r] stage counts (as wfft_set_radix),
    bx[axis][op] column-tile widths (axes 1, 2; op 0 forward, 1 inverse, 2 gradient, 3
-   divergence, 4 preconditioner; entries of passes the grid does not run are ignored).
+   divergence, 4 preconditioner; entries of passes the grid does not run are ignored) and
+   xelems, the complex elements per x-pass tile (0 = the default 2048; 256..8192, capped
+   by the register batch of the radix schedule).
    wfft_get_plan reads them (e.g. after wfft_autotune); wfft_set_plan applies them to a
    handle of the same grid, so a tuned plan can be kept and reused without timing.  A
    choice that does not fit the grid, the register batch, 64 KB of shared memory or the
@@ -320,6 +324,7 @@ WFFT_API int wfft_set_radix(wfft_handle* h, int precision, int axis, const int c
 typedef struct {
   int radix[3][7];
   int bx[3][5];
+  int xelems;
 } wfft_plan_choice;
 WFFT_API int wfft_get_plan(const wfft_handle* h, int precision, wfft_plan_choice* out);
 WFFT_API int wfft_set_plan(wfft_handle* h, int precision, const wfft_plan_choice* in);

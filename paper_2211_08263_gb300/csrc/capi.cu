@@ -1430,6 +1430,7 @@ namespace {
 struct TunedPlan {
   AxisPlan ax[3];
   int bx[3][5];
+  int xelems;
 };
 std::mutex g_tune_mu;
 std::map<std::array<int, 6>, TunedPlan> g_tuned;  // (precision, ndim, N1, N2, N3, device)
@@ -1469,6 +1470,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
     before.ax[a] = D.ax[a];
     for (int op = 0; op < 5; ++op) before.bx[a][op] = P.g.bx[a][op];
   }
+  before.xelems = P.g.xelems;
   TunedPlan best;
   bool cached = false;
   {
@@ -1501,7 +1503,28 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
       plan_geometry<T>(P);
       CKH(h, upload_desc(P));
     }
-    // 2. column-tile widths, pass by pass
+    // 2. x-pass tile size (complex elements per block; larger tiles keep more loads in
+    //    flight and more threads busy in the FFT stages, at the cost of shared memory)
+    {
+      const int keep0 = P.g.xelems;
+      int keep = keep0;
+      float tbest = 1e30f;
+      for (int xe : {1024, 2048, 4096}) {
+        P.g.xelems = xe;
+        plan_geometry<T>(P);
+        if (P.g.max_blocks > h->nparts) continue;
+        CKH(h, upload_desc(P));
+        const float t = time_iteration<T>(h, P, reps);
+        if (t < tbest) {
+          tbest = t;
+          keep = xe;
+        }
+      }
+      P.g.xelems = tbest < 1e30f ? keep : keep0;
+      plan_geometry<T>(P);
+      CKH(h, upload_desc(P));
+    }
+    // 3. column-tile widths, pass by pass
     for (int a = 1; a <= 2; ++a)
       for (int op = 0; op < 5; ++op) {
         if (!ops_of_axis(D, a, op)) continue;
@@ -1522,13 +1545,16 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
       best.ax[a] = D.ax[a];
       for (int op = 0; op < 5; ++op) best.bx[a][op] = P.g.bx[a][op];
     }
+    best.xelems = P.g.xelems;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best;
   } else {
     for (int a = 0; a < 3; ++a) D.ax[a] = best.ax[a];
+    P.g.xelems = best.xelems;
     plan_geometry<T>(P);
     if (P.g.max_blocks > h->nparts) {
       for (int a = 0; a < 3; ++a) D.ax[a] = before.ax[a];
+      P.g.xelems = before.xelems;
       plan_geometry<T>(P);
     } else {
       for (int a = 1; a <= 2; ++a)
@@ -1545,6 +1571,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
     for (int op = 0; op < 5; ++op)
       if (ops_of_axis(D, a, op) && P.g.bx[a][op] != before.bx[a][op]) ++*changed;
   }
+  if (P.g.xelems != before.xelems) ++*changed;
   CKH(h, cudaStreamSynchronize(h->st));
   return WFFT_OK;
 }
@@ -1826,6 +1853,7 @@ void get_plan(const Plan<T>& P, wfft_plan_choice* out) {
     for (int r = 0; r < 7; ++r) out->radix[a][r] = P.h.ax[a].cnt[r];
     for (int op = 0; op < 5; ++op) out->bx[a][op] = P.g.bx[a][op];
   }
+  out->xelems = P.g.xelems > 0 ? P.g.xelems : 2048;
 }
 
 template <typename T>
@@ -1845,9 +1873,12 @@ int set_plan(wfft_handle* h, Plan<T>& P, const wfft_plan_choice* in) {
     if (prod != h->n[a]) return fail(h, WFFT_EINVAL, "a radix schedule does not multiply to its axis length");
     if (sizeof(T) == 8 && ax[a].cnt[6]) return fail(h, WFFT_EINVAL, "radix-16 stages are FP32 only");
   }
+  if (in->xelems != 0 && (in->xelems < 256 || in->xelems > 8192))
+    return fail(h, WFFT_EINVAL, "the x-pass tile size must be 0 or 256..8192 elements");
   const Desc<T> saved = D;
   const PassGeo gsaved = P.g;
   for (int a = 0; a < 3; ++a) D.ax[a] = ax[a];
+  P.g.xelems = in->xelems;
   plan_geometry<T>(P);
   for (int a = 1; a <= 2; ++a)
     for (int op = 0; op < 5; ++op) {

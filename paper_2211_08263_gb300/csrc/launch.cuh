@@ -18,6 +18,7 @@ struct PassGeo {
   int blk_col[3][5];    // [axis][op] grid size (x dimension)
   size_t sm_col[3][5];  // [axis][op] dynamic shared memory
   int max_blocks;
+  int xelems = 0;       // complex elements per x-pass tile (0: the default 2048; capped by the register batch)
 };
 
 template <typename T>

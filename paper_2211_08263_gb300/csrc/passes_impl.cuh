@@ -30,7 +30,7 @@ void plan_geometry(Plan<T>& P) {
   Desc<T>& D = P.h;
   PassGeo& g = P.g;
   g.thr = 256;
-  const int budget = 2048;  // target complex elements per block tile
+  const int budget = g.xelems > 0 ? g.xelems : 2048;  // target complex elements per x-pass tile
   const long long nsp = (long long)D.n2 * D.n3;
   // x passes: npairs * N1 <= elems, LX * nc even
   const int ex = std::min(budget, max_tile_elems<T>(D.ax[0], g.thr));

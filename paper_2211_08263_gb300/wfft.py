@@ -46,7 +46,7 @@ class Options(C.Structure):
 
 
 class PlanChoice(C.Structure):
-    _fields_ = [("radix", (C.c_int * 7) * 3), ("bx", (C.c_int * 5) * 3)]
+    _fields_ = [("radix", (C.c_int * 7) * 3), ("bx", (C.c_int * 5) * 3), ("xelems", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -277,10 +277,11 @@ class Solver:
         return info.as_dict()
 
     def get_plan(self, precision: int) -> dict:
-        """{"radix": 3 x 7 stage counts, "bx": 3 x 5 column-tile widths} (wfft_get_plan)."""
+        """{"radix": 3 x 7 stage counts, "bx": 3 x 5 column-tile widths, "xelems": x-pass tile
+        size} (wfft_get_plan)."""
         pc = PlanChoice()
         self._check(self.lib.wfft_get_plan(self.h, int(precision), C.byref(pc)))
-        return {"radix": [list(r) for r in pc.radix], "bx": [list(r) for r in pc.bx]}
+        return {"radix": [list(r) for r in pc.radix], "bx": [list(r) for r in pc.bx], "xelems": pc.xelems}
 
     def set_plan(self, precision: int, plan: dict) -> None:
         """Apply plan choices read by get_plan (wfft_set_plan)."""
@@ -290,6 +291,7 @@ class Solver:
                 pc.radix[a][r] = int(plan["radix"][a][r])
             for o in range(5):
                 pc.bx[a][o] = int(plan["bx"][a][o])
+        pc.xelems = int(plan.get("xelems", 0))
         self._check(self.lib.wfft_set_plan(self.h, int(precision), C.byref(pc)))
 
     def set_radix(self, precision: int, axis: int, counts) -> None:

@@ -164,3 +164,40 @@ def test_hand_set_radix_schedules_match_oracle(ndim, n, prec, plans):
     assert rel(oracle_field(prob, zd.cpu().numpy().astype(np.float64)), zo) < tol
     with pytest.raises(wfft.WfftError):
         s.set_radix(wfft.FP64, 0, [0, 0, 0, 0, 0, 0, 1] if n[0] == 16 else [0, 0, 0, 0, 0, 0, 9])
+
+
+# x-pass tile sizes other than the default (wfft_plan_choice.xelems): more or fewer lines per block
+XTILE_CASES = [(3, (64, 48, 40), 1, 4096), (3, (64, 48, 40), 1, 1024), (3, (30, 20, 14), 0, 1024),
+               (3, (30, 20, 14), 1, 8192), (2, (80, 96, 1), 1, 4096), (3, (256, 12, 6), 0, 4096)]
+
+
+@pytest.mark.parametrize("ndim,n,prec,xelems", XTILE_CASES)
+def test_x_tile_sizes_match_oracle(ndim, n, prec, xelems):
+    from oracle import spectral
+    torch = torch_cuda()
+    wfft = solver_lib()
+    rng = np.random.default_rng(11 * sum(n) + prec)
+    prob = inputs.random_problem(rng, ndim, n, nphase=4, mask_width=2, contrast=4.0, dt=4e-7)
+    s = _solver(prob, prec)
+    pr = wfft.MIXED if prec else wfft.FP64
+    plan = s.get_plan(pr)
+    assert plan["xelems"] == 2048
+    plan["xelems"] = xelems
+    s.set_plan(pr, plan)
+    assert s.get_plan(pr)["xelems"] == xelems
+    med, sp, th = _oracle_ops(prob)
+    dt = torch.float64 if prec == 0 else torch.float32
+    tol = 1e-12 if prec == 0 else 3e-6
+    p = rng.standard_normal((ndim, n[2], n[1], n[0]))
+    pd = to_dev(torch, p, dt)
+    qd, zd = torch.zeros_like(pd), torch.zeros_like(pd)
+    s.apply(pd, qd, precision=prec, masked=False)
+    s.precond(pd, zd, precision=prec, masked=False)
+    torch.cuda.synchronize()
+    qo = spectral.apply_A(med, sp, oracle_field(prob, p), th)
+    zo = spectral.apply_M(med, sp, oracle_field(prob, p), th)
+    assert rel(oracle_field(prob, qd.cpu().numpy().astype(np.float64)), qo) < tol
+    assert rel(oracle_field(prob, zd.cpu().numpy().astype(np.float64)), zo) < tol
+    plan["xelems"] = 100
+    with pytest.raises(wfft.WfftError):
+        s.set_plan(pr, plan)
