@@ -402,7 +402,8 @@ WFFT_API int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info* 
 #define WFFT_K_SCALAR 14      /* single-block finalize and bookkeeping kernels */
 #define WFFT_K_NET_CONV 15    /* warm-start network convolutions (BF16 MMA, FP32 accumulate; counted as precision 1) */
 #define WFFT_K_NET_AUX 16     /* warm-start scale, features, Taylor increment, training bookkeeping (precision 1) */
-#define WFFT_K_COUNT 17
+#define WFFT_K_XINV_PUPD 17   /* x inverse fused with z = P(...), p = z + beta p and the forward x transform of p */
+#define WFFT_K_COUNT 18
 
 /*
  * Launch accounting.  Every kernel launch of a handle is counted per kind and

@@ -572,15 +572,31 @@ static int read_scalars(wfft_handle* h) {
 // One block of check_every PCG iterations on stream st (every kernel returns at once
 // when the solve's done flag is set, so a block may overrun convergence harmlessly).
 template <typename T>
-static void pcg_chunk(wfft_handle* h, Plan<T>& P, Scalars* sc, cudaStream_t st) {
+static void pcg_chunk(wfft_handle* h, Plan<T>& P, Scalars* sc, cudaStream_t st, int count) {
   const Desc<T>& D = P.h;
   const int op = D.opAxis;
-  for (int i = 0; i < h->opt.check_every; ++i) {
-    launch_apply<T>(P, PRE_PUPD, SL_P, POST_APPLY, SL_Q, h->solve_masked, 1, st);
+  const int m = h->solve_masked;
+  for (int i = 0; i < count; ++i) {
+    // q = P A p from the half spectrum of p left by the previous preconditioner pass
+    launch_apply<T>(P, PRE_NONE, SL_P, POST_APPLY, SL_Q, m, 1, st);
     launch_fin(sc, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_ALPHA, nullptr, st);
-    launch_precond<T>(P, PRE_RUPD, SL_R, SL_Z, h->solve_masked, st);
+    // x += alpha p, r -= alpha q, ||r||^2, M r up to the Parseval (r, z); beta; then
+    // z, p = z + beta p and the half spectrum of p
+    launch_precond_part_impl<T>(P, 0, PRE_RUPD, SL_R, m, st);
     launch_fin(sc, D.part[PT_A], P.g.blk_x, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_BETA, nullptr, st);
+    launch_precond_part_impl<T>(P, 1, 0, 0, m, st);
   }
+}
+
+// First preconditioner application of a solve (or of a mixed inner solve): z = M r
+// with the x-pass prologue `pre`, (r, z), and the first search direction p = z with
+// its half spectrum.
+template <typename T>
+static void precond_start(Plan<T>& P, Scalars* sc, int pre, int masked, cudaStream_t st) {
+  const Desc<T>& D = P.h;
+  launch_precond_part_impl<T>(P, 0, pre, SL_R, masked, st);
+  launch_fin(sc, nullptr, 0, D.part[PT_B], P.g.blk_col[D.opAxis][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, st);
+  launch_precond_part_impl<T>(P, 1, 0, 0, masked, st);
 }
 
 // Launch one block of iterations, as a CUDA graph when enabled: the block is captured
@@ -588,10 +604,18 @@ static void pcg_chunk(wfft_handle* h, Plan<T>& P, Scalars* sc, cudaStream_t st) 
 // stream other than the legacy default one) and replayed on the solve's stream.
 // Every kernel argument is a pointer to device-resident descriptors and scalars,
 // so a replay computes exactly what direct launches would.
+// While profiling, blocks are one iteration long: the iterations of a block that follow
+// convergence launch kernels that return at once, and those would bias the per-launch
+// times of the kernel table.
+template <typename T>
+static int chunk_len(const wfft_handle* h) {
+  return h->prof.on ? 1 : h->opt.check_every;
+}
+
 template <typename T>
 static int pcg_chunk_launch(wfft_handle* h, Plan<T>& P, Scalars* sc, int which) {
   if (!h->opt.use_graphs || h->prof.on || !h->solve_masked) {
-    pcg_chunk<T>(h, P, sc, h->st);
+    pcg_chunk<T>(h, P, sc, h->st, chunk_len<T>(h));
     return WFFT_OK;
   }
   if (!h->chunk[which]) {
@@ -599,7 +623,7 @@ static int pcg_chunk_launch(wfft_handle* h, Plan<T>& P, Scalars* sc, int which) 
     const long long before = h->prof.lifetime;
     cudaGraph_t g = nullptr;
     CKH(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
-    pcg_chunk<T>(h, P, sc, h->cap_st);
+    pcg_chunk<T>(h, P, sc, h->cap_st, h->opt.check_every);
     const cudaError_t ec = cudaStreamEndCapture(h->cap_st, &g);
     if (ec != cudaSuccess || !g) {
       if (g) cudaGraphDestroy(g);
@@ -625,9 +649,10 @@ template <typename T>
 static int pcg_loop(wfft_handle* h, Plan<T>& P, Scalars* sc, int which, int budget, int* iters) {
   int launched = 0;
   for (;;) {
+    const int len = chunk_len<T>(h);
     int rc0 = pcg_chunk_launch<T>(h, P, sc, which);
     if (rc0) return rc0;
-    launched += h->opt.check_every;
+    launched += len;
     CKH(h, cudaGetLastError());
     int rc = read_scalars(h);
     if (rc) return rc;
@@ -647,15 +672,13 @@ static int pcg_loop(wfft_handle* h, Plan<T>& P, Scalars* sc, int which, int budg
 static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false, bool inner_guess = false) {
   Plan<double>& P = h->P64;
   const Desc<double>& D = P.h;
-  const int op = D.opAxis;
   const int watchdog = h->opt.watchdog_iters > 0 ? h->opt.watchdog_iters : 4 * h->opt.maxit;
   int iters = 0, outer = 0, sweeps = 0, incr_count = 0;
   int status = WFFT_OK;
   if (h->opt.precision == WFFT_FP64) {
     launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
     launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_RES0, nullptr, h->st);
-    launch_precond<double>(P, PRE_PLAIN, SL_R, SL_Z, 1, h->st);
-    launch_fin(h->sc64, nullptr, 0, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, h->st);
+    precond_start<double>(P, h->sc64, PRE_PLAIN, 1, h->st);
     outer = 1;
     int rc = pcg_loop<double>(h, P, h->sc64, 0, watchdog, &iters);
     if (rc == WFFT_ETIMEOUT) status = WFFT_ETIMEOUT;
@@ -724,8 +747,7 @@ static int solve_core(wfft_handle* h, wfft_step_info* info, bool use_au = false,
         break;
       }
       ++sweeps;
-      launch_precond<float>(F, inner_guess && sweeps == 1 ? PRE_CONVD : PRE_CONV, SL_R, SL_Z, 1, h->st);
-      launch_fin(h->sc32, nullptr, 0, DF.part[PT_B], F.g.blk_col[DF.opAxis][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, h->st);
+      precond_start<float>(F, h->sc32, inner_guess && sweeps == 1 ? PRE_CONVD : PRE_CONV, 1, h->st);
       int it = 0;
       rc = pcg_loop<float>(h, F, h->sc32, 1, std::max(1, watchdog - iters), &it);
       iters += it;
@@ -1442,8 +1464,9 @@ float time_iteration(wfft_handle* h, Plan<T>& P, int reps) {
   launch_apply<T>(P, PRE_PLAIN, SL_P, POST_APPLY, SL_Q, 1, 0, h->st);
   cudaEventRecord(h->ev0, h->st);
   for (int r = 0; r < reps; ++r) {
-    launch_apply<T>(P, PRE_PLAIN, SL_P, POST_APPLY, SL_Q, 1, 0, h->st);
-    launch_precond<T>(P, PRE_PLAIN, SL_Q, SL_Z, 1, h->st);
+    launch_apply<T>(P, PRE_NONE, SL_P, POST_APPLY, SL_Q, 1, 0, h->st);
+    launch_precond_part_impl<T>(P, 0, PRE_PLAIN, SL_Q, 1, h->st);
+    launch_precond_part_impl<T>(P, 1, 0, 0, 1, h->st);
   }
   cudaEventRecord(h->ev1, h->st);
   float ms = 1e30f;
@@ -1717,7 +1740,6 @@ namespace {
 int green_solve(wfft_handle* h, int* iters) {
   Plan<double>& P = h->P64;
   const Desc<double>& D = P.h;
-  const int op = D.opAxis;
   h->solve_masked = 0;
   const double zero3[3] = {0.0, 0.0, 0.0};
   launch_begin(h->sc64, zero3, 0, h->opt.tol * h->opt.tol, h->opt.maxit, h->st);
@@ -1725,8 +1747,7 @@ int green_solve(wfft_handle* h, int* iters) {
   launch_fin(h->sc64, D.part[PT_A], ew_block_count(P), nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
   launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 0, 1, h->st);
   launch_fin(h->sc64, D.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_RES0, nullptr, h->st);
-  launch_precond<double>(P, PRE_PLAIN, SL_R, SL_Z, 0, h->st);
-  launch_fin(h->sc64, nullptr, 0, D.part[PT_B], P.g.blk_col[op][OP_PREC], nullptr, 0, FIN_RZ0, nullptr, h->st);
+  precond_start<double>(P, h->sc64, PRE_PLAIN, 0, h->st);
   const int watchdog = h->opt.watchdog_iters > 0 ? h->opt.watchdog_iters : 4 * h->opt.maxit;
   int rc = pcg_loop<double>(h, P, h->sc64, 0, watchdog, iters);
   h->solve_masked = 1;

@@ -82,6 +82,15 @@ inline void launch_precond(const Plan<T>& P, int pre, int in_slot, int out_slot,
     launch_precond_impl<T, 0>(P, pre, in_slot, out_slot, masked, st, nullptr);
 }
 
+// The preconditioner in two parts around the finalize of its Parseval dot (r, z):
+// part 0 = x forward pass with prologue `pre` (PRE_RUPD, PRE_CONV, PRE_CONVD, PRE_PLAIN
+// reading in_slot), the plain column pass, the column pass of the closed-form solve;
+// part 1 = the inverse column pass and the x inverse pass that forms z = [P](...),
+// p = z + beta p (p = z when the scalars' first flag is set) and the half spectrum of
+// p, so that the next operator application starts with PRE_NONE.  Single instance.
+template <typename T>
+void launch_precond_part_impl(const Plan<T>& P, int part, int pre, int in_slot, int masked, cudaStream_t st);
+
 // Block count of an instance for a geometry class at a given column-tile width.
 template <typename T>
 int geo_blocks(const Plan<T>& P, int cls, int bx);

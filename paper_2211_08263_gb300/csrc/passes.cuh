@@ -22,8 +22,8 @@
 
 namespace wfft {
 
-enum { PRE_PLAIN = 0, PRE_PUPD = 1, PRE_RUPD = 2, PRE_CONV = 3, PRE_XUPD = 4, PRE_CONVD = 5 };
-enum { POST_APPLY = 0, POST_RESID = 1, POST_PREC = 2 };
+enum { PRE_PLAIN = 0, PRE_PUPD = 1, PRE_RUPD = 2, PRE_CONV = 3, PRE_XUPD = 4, PRE_CONVD = 5, PRE_NONE = 6 };
+enum { POST_APPLY = 0, POST_RESID = 1, POST_PREC = 2, POST_PREC_PUPD = 3 };
 enum { OP_FWD = 0, OP_INV = 1, OP_GRAD = 2, OP_DIV = 3, OP_PREC = 4 };
 
 template <typename T>
@@ -114,6 +114,46 @@ __device__ __forceinline__ void load_packed(const Desc<T>& D, cplx<T>* buf, int 
     if (ny) row[rowpad(N / 2)] = cmake<T>(An.x, Bn.x);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Staging of the elementwise inputs of the FP32 x passes: the rows a block's epilogue
+// (or Hooke phase) reads are copied global -> shared with cp.async at the start of the
+// block, so they arrive while the spectrum is loaded and transformed, with every byte
+// of the block in flight at once.  A block's LX lines of one component are one
+// contiguous run of LX N elements, so each staged array is one run per component.
+// Staging needs N % 16 == 0 (16-byte runs for 1-byte masks); the host decides and
+// sizes the shared memory (stage != 0).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ size_t stage_round(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Byte layout of the staging area of an x inverse pass: p (POST_APPLY: the operator's
+// input; POST_PREC_PUPD: the previous search direction; nc x LX x N floats), rho source
+// (POST_APPLY: LX x N uint16 phase ids, or floats of per-voxel rho), mask (LX x N bytes).
+struct XStage {
+  size_t p, rho, mask, total;
+};
+__host__ __device__ __forceinline__ XStage xinv_stage_layout(int post, int nc, int LX, int N, bool phase) {
+  XStage L;
+  const size_t e = (size_t)LX * N;
+  const bool wp = post == POST_APPLY || post == POST_PREC_PUPD, wr = post == POST_APPLY;
+  L.p = 0;
+  L.rho = stage_round(wp ? (size_t)nc * e * 4 : 0);
+  L.mask = L.rho + stage_round(wr ? e * (phase ? 2 : 4) : 0);
+  L.total = L.mask + stage_round(e);
+  return L;
+}
+
+// Issue 16-byte cp.async copies of `bytes` (a multiple of 16, both ends 16-byte aligned).
+__device__ __forceinline__ void stage_copy(void* sdst, const void* gsrc, size_t bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  const char* g = reinterpret_cast<const char*>(gsrc);
+  for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s + (unsigned)o), "l"(g + o) : "memory");
+}
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Waits for this thread's own copies only (they complete unconditionally); a barrier
+// after it makes every thread's copies visible to the block.
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const cplx<T>* src, int N) {
@@ -258,10 +298,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc
 //   POST_APPLY  q = t + rho p (t = -theta div sigma), mask, (p, q)
 //   POST_RESID  A x = t + rho x (kept when the slot exists), r = P(b - A x), ||r||^2
 //   POST_PREC   z = P(t)
+//   POST_PREC_PUPD  z = P(t), p = z + beta p (p = z on a solve's first iteration), then
+//               the forward x transform of p back into the half spectrum: the next
+//               operator application starts at its first column pass (PRE_NONE), and z
+//               never goes to memory
 // ---------------------------------------------------------------------------
 template <typename T, int POST, int BATCH>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int in_slot,
-                                              int out_slot, int masked, int want_dot) {
+                                              int out_slot, int masked, int want_dot, int stage_arg) {
+  const int stage = sizeof(T) == 4 ? stage_arg : 0;  // FP32 passes only
   int blk;
   const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
   const Desc<T>& D = *Dp;
@@ -276,10 +321,37 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc
   const long long nsp = (long long)D.n2 * D.n3;
   const long long l0 = (long long)blk * LX;
   const long long V = D.V;
+  // staged epilogue inputs (FP32 passes): issued first, consumed after the FFT
+  unsigned char* stg = smraw + stage_round((size_t)(N + (LX * nc / 2) * lstr) * sizeof(cplx<T>));
+  const XStage SL = xinv_stage_layout(POST, nc, LX, N, D.phase != nullptr);
+  // POST_PREC_PUPD: p = z + beta p needs the old p unless this is the first iteration
+  const bool pfirst = POST == POST_PREC_PUPD && sc->first != 0;
+  const T pbeta = POST == POST_PREC_PUPD ? (T)sc->beta : (T)0;
+  const int pin = POST == POST_PREC_PUPD ? (int)SL_P : in_slot;
+  if (stage) {
+    const long long nv = nsp - l0 < LX ? nsp - l0 : LX;  // valid lines of this block
+    const size_t e = (size_t)nv * N;
+    if (POST == POST_APPLY || (POST == POST_PREC_PUPD && !pfirst))
+      for (int k = 0; k < nc; ++k)
+        stage_copy(stg + SL.p + (size_t)k * LX * N * 4,
+                   reinterpret_cast<const float*>(D.slot[pin]) + (long long)k * V + l0 * N, e * 4);
+    if (POST == POST_APPLY) {
+      if (D.phase)
+        stage_copy(stg + SL.rho, D.phase + l0 * N, e * 2);
+      else
+        stage_copy(stg + SL.rho, D.rhotab + l0 * N, e * 4);
+    }
+    if (masked) stage_copy(stg + SL.mask, D.mask + l0 * N, e);
+    stage_commit();
+  }
   load_twiddles<T>(tw, D.tw[0], N);
   load_packed<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
   __syncthreads();
   fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, lstr, tw, +1);
+  if (stage) {
+    stage_wait();
+    __syncthreads();
+  }
   DotAcc<T> acc;
   constexpr int U = 4;  // elements per lane kept in flight
   const int nq = LX * nc;
@@ -299,13 +371,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc
         const int x = x0 + 32 * u;
         a[u] = b[u] = rho[u] = 0;
         m[u] = 0;
-        if (x < N) {
+        if (x < N && stage) {
+          const int ex = l * N + x;  // element of the staged runs
+          if (masked) m[u] = stg[SL.mask + ex];
+          if (POST == POST_APPLY) {
+            a[u] = reinterpret_cast<const T*>(stg + SL.p)[(size_t)k * LX * N + ex];
+            rho[u] = D.phase ? D.rhotab[reinterpret_cast<const uint16_t*>(stg + SL.rho)[ex]]
+                             : reinterpret_cast<const T*>(stg + SL.rho)[ex];
+          } else if (POST == POST_PREC_PUPD && !pfirst) {
+            a[u] = reinterpret_cast<const T*>(stg + SL.p)[(size_t)k * LX * N + ex];
+          }
+        } else if (x < N) {
           const long long vox = line * N + x;
           const long long gi = (long long)k * V + vox;
           if (masked) m[u] = D.mask[vox];
           if (POST == POST_APPLY) {
             a[u] = reinterpret_cast<const T*>(D.slot[in_slot])[gi];
             rho[u] = rho_at<T>(D, vox);
+          } else if (POST == POST_PREC_PUPD && !pfirst) {
+            a[u] = reinterpret_cast<const T*>(D.slot[SL_P])[gi];
           } else if (POST == POST_RESID) {
             a[u] = reinterpret_cast<const T*>(D.slot[SL_X])[gi];
             b[u] = reinterpret_cast<const T*>(D.slot[SL_B])[gi];
@@ -333,15 +417,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc
           if (isg) rv = 0;
           reinterpret_cast<T*>(D.slot[SL_R64])[gi] = rv;
           acc.add_prod(rv, rv);
+        } else if (POST == POST_PREC_PUPD) {
+          const T z = isg ? (T)0 : t;
+          const T pv = pfirst ? z : z + pbeta * a[u];
+          reinterpret_cast<T*>(D.slot[SL_P])[gi] = pv;
+          packed<T>(buf, lstr, q, x) = pv;
         } else {  // POST_PREC
           reinterpret_cast<T*>(D.slot[out_slot])[gi] = isg ? (T)0 : t;
         }
       }
     }
   }
-  if (POST != POST_PREC && want_dot) {
+  if ((POST == POST_APPLY || POST == POST_RESID) && want_dot) {
     const double s = block_sum(acc.value());
     if (threadIdx.x == 0) D.part[PT_A][blk] = s;
+  }
+  if (POST == POST_PREC_PUPD) {
+    __syncthreads();
+    fft_lines<T, 1>(buf, D.ax[0], LX * nc / 2, lstr, tw, -1);
+    store_unpacked<T>(D, buf, lstr, LX * nc, l0, nc, nsp);
   }
 }
 
@@ -385,7 +479,9 @@ __device__ __forceinline__ void load_row(const T* __restrict__ src, T* dst, int 
 }
 
 template <typename T, int BATCH>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc<T>* __restrict__ dd, BatchArgs<T> ba) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc<T>* __restrict__ dd, BatchArgs<T> ba,
+                                                                        int stage_arg) {
+  const int stage = sizeof(T) == 4 ? stage_arg : 0;  // FP32 passes only
   int blk;
   const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
   const Desc<T>& D = *Dp;
@@ -398,10 +494,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc
   const int lstr = row_stride(N);
   const long long nsp = (long long)D.n2 * D.n3;
   const long long l0 = (long long)blk * LX;
+  // staged phase ids of the block's voxels (phase tables, FP32 passes)
+  const uint16_t* sph =
+      reinterpret_cast<const uint16_t*>(smraw + stage_round((size_t)(N + (LX * ns / 2) * lstr) * sizeof(cplx<T>)));
+  if (stage) {
+    const long long nv = nsp - l0 < LX ? nsp - l0 : LX;
+    stage_copy(const_cast<uint16_t*>(sph), D.phase + l0 * N, (size_t)nv * N * 2);
+    stage_commit();
+  }
   load_twiddles<T>(tw, D.tw[0], N);
   load_packed<T>(D, buf, lstr, LX * ns, l0, ns, nsp);
   __syncthreads();
   fft_lines<T, 1>(buf, D.ax[0], LX * ns / 2, lstr, tw, +1);
+  if (stage) {
+    stage_wait();
+    __syncthreads();
+  }
   const int cstride = (ns == 6) ? kCtabStride3 : kCtabStride2;
   // every thread of the block takes voxels (consecutive x across a warp)
   const int lgN = log2_if_pow2(N);
@@ -411,7 +519,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc
     const long long line = l0 + l;
     if (line >= nsp) continue;
     const long long vox = line * N + x;
-    const long long row = D.phase ? (long long)D.phase[vox] : vox;
+    const long long row = stage ? (long long)sph[e] : (D.phase ? (long long)D.phase[vox] : vox);
     T C[24];
     load_row<T>(D.ctab + row * cstride, C, ns == 6 ? 24 : 8);
     T ev[6];
@@ -596,9 +704,17 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3)
   constexpr int kS = (OP == OP_PREC) ? 0 : NS;
   constexpr int NIN = (OP == OP_DIV) ? kS : kC;
   constexpr int NOUT = (OP == OP_GRAD) ? kS : kC;
+  // 3-D gradient / divergence: the six-slot side is transformed as two batches of three
+  // slots, so a tile of BX columns needs only 3 BX N elements per batch in registers
+  constexpr bool kSplit = OP != OP_PREC && NS == 6;
   col_load_all<T, BX, ES, NIN>(D, g, tl);
   __syncthreads();
-  fft_lines<T, ES, NIN * BX>(tl, pl, NIN * BX, 1, tw, -1);
+  if (kSplit && NIN == 6) {
+    fft_lines<T, ES, 3 * BX>(tl, pl, 3 * BX, 1, tw, -1);
+    fft_lines<T, ES, 3 * BX>(tl + 3 * BX, pl, 3 * BX, 1, tw, -1);
+  } else {
+    fft_lines<T, ES, NIN * BX>(tl, pl, NIN * BX, 1, tw, -1);
+  }
   DotAcc<T> acc;
   for (int e = threadIdx.x; e < N * BX; e += blockDim.x) {
     const int y = e / BX, b = e % BX;
@@ -691,7 +807,12 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3)
     if (threadIdx.x == 0) D.part[PT_B][blk] = s;
   }
   __syncthreads();
-  fft_lines<T, ES, NOUT * BX>(tl, pl, NOUT * BX, 1, tw, +1);
+  if (kSplit && NOUT == 6) {
+    fft_lines<T, ES, 3 * BX>(tl, pl, 3 * BX, 1, tw, +1);
+    fft_lines<T, ES, 3 * BX>(tl + 3 * BX, pl, 3 * BX, 1, tw, +1);
+  } else {
+    fft_lines<T, ES, NOUT * BX>(tl, pl, NOUT * BX, 1, tw, +1);
+  }
   for (int k = 0; k < NOUT; ++k) col_store<T, BX, ES>(D, g, k, tl, k);
 }
 

@@ -1,6 +1,7 @@
 // Launch sequences of the fused passes, instantiated per arithmetic type.
 #pragma once
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 
 #include "launch.cuh"
@@ -23,6 +24,12 @@ static int max_tile_elems(const AxisPlan& pl, int thr) {
     cap = std::min(cap, nb * R * thr);
   }
   return cap;
+}
+
+// Slots transformed by one batched FFT call of a column pass: the 3-D gradient and
+// divergence passes transform their six strain / stress slots as two batches of three.
+static inline int col_batch_slots(int op, int ns) {
+  return (op == OP_GRAD || op == OP_DIV) && ns == 6 ? 3 : ns;
 }
 
 template <typename T>
@@ -66,10 +73,11 @@ void plan_geometry(Plan<T>& P) {
     for (int op = 0; op < 5; ++op) {
       const bool plain = op == OP_FWD || op == OP_INV;
       const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
+      const int nb = col_batch_slots(op, ns);
       const int thr = plain ? kColThreadsPlain : kColThreadsOp;
       const int maxe = max_tile_elems<T>(D.ax[ax], thr);
       int bx = plain ? maxbx : std::min(maxbx, 4);
-      while (bx > 1 && ((long long)ns * bx * N > maxe || (size_t)ns * bx * N * cs > 64 * 1024)) bx >>= 1;
+      while (bx > 1 && ((long long)nb * bx * N > maxe || (size_t)ns * bx * N * cs > 64 * 1024)) bx >>= 1;
       g.bx[ax][op] = bx;
       g.blk_col[ax][op] = ((D.nh + bx - 1) / bx) * nouter;
       g.sm_col[ax][op] = (size_t)(N + ns * bx * N) * cs;
@@ -90,7 +98,7 @@ bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx) {
   const int thr = plain ? kColThreadsPlain : kColThreadsOp;
   const int maxbx = plain && sizeof(T) == 4 ? 8 : 4;
   if (bx < 1 || bx > maxbx || (bx & (bx - 1))) return false;
-  return (long long)ns * bx * N <= max_tile_elems<T>(D.ax[axis], thr) &&
+  return (long long)col_batch_slots(op, ns) * bx * N <= max_tile_elems<T>(D.ax[axis], thr) &&
          (size_t)ns * bx * N * sizeof(cplx<T>) <= 64 * 1024;
 }
 
@@ -337,12 +345,27 @@ static void launch_col(const Launch<T, B>& L, int op, int axis, int ncomp, cudaS
   else launch_colop<T, OP_PREC, B>(L, axis, st);
 }
 
+// The FP32 x inverse and middle passes of a single-instance launch stage their
+// elementwise inputs in shared memory when N1 % 16 == 0 (16-byte runs of every
+// staged array) and the staged slot is 16-byte aligned.
+template <typename T, int B>
+static bool x_stage_ok(const Launch<T, B>& L) {
+  return B == 0 && sizeof(T) == 4 && (L.P.h.n1 % 16) == 0;
+}
+
 template <typename T, int B>
 static void launch_xinv(const Launch<T, B>& L, int post, int in_slot, int out_slot, int masked, int want_dot,
                         cudaStream_t st) {
   const int pi = prec_index(sizeof(T));
   const int nb = L.grid(GEO_X);
-  const size_t sm = L.smem(GEO_X);
+  size_t sm = L.smem(GEO_X);
+  int stage = 0;
+  if (x_stage_ok(L) && post != POST_RESID &&
+      (post != POST_APPLY || reinterpret_cast<uintptr_t>(L.P.h.slot[in_slot]) % 16 == 0)) {
+    const Desc<T>& D = L.P.h;
+    stage = 1;
+    sm = stage_round(sm) + xinv_stage_layout(post, D.c, D.lx, D.n1, D.phase != nullptr).total;
+  }
   const BatchArgs<T> ba = L.args(GEO_X);
   const Desc<T>* d = L.P.d;
   double by, fl;
@@ -357,6 +380,9 @@ static void launch_xinv(const Launch<T, B>& L, int post, int in_slot, int out_sl
         } else if (post == POST_RESID) {
           b = in + 24 * k.c * k.V + mat;
           f += 3 * k.c * k.V;
+        } else if (post == POST_PREC_PUPD) {
+          b = 2 * in + 2 * k.real(k.c) + k.V;
+          f = 2 * k.xfft(k.c) + 2 * k.c * k.V;
         } else {
           b = in + k.real(k.c) + k.V;
         }
@@ -365,17 +391,23 @@ static void launch_xinv(const Launch<T, B>& L, int post, int in_slot, int out_sl
   switch (post) {
     case POST_APPLY:
       prof_launch(pi, KK_XINV_APPLY, by, fl, st, [&] {
-        k_xinv<T, POST_APPLY, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, want_dot);
+        k_xinv<T, POST_APPLY, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, want_dot, stage);
       });
       break;
     case POST_RESID:
       prof_launch(pi, KK_XINV_RESID, by, fl, st, [&] {
-        k_xinv<T, POST_RESID, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, want_dot);
+        k_xinv<T, POST_RESID, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, want_dot, 0);
       });
+      break;
+    case POST_PREC_PUPD:
+      if constexpr (B == 0)
+        prof_launch(pi, KK_XINV_PUPD, by, fl, st, [&] {
+          k_xinv<T, POST_PREC_PUPD, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, 0, stage);
+        });
       break;
     default:
       prof_launch(pi, KK_XINV_PREC, by, fl, st,
-                  [&] { k_xinv<T, POST_PREC, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, 0); });
+                  [&] { k_xinv<T, POST_PREC, B><<<nb, 256, sm, st>>>(d, ba, in_slot, out_slot, masked, 0, stage); });
       break;
   }
 }
@@ -383,7 +415,12 @@ static void launch_xinv(const Launch<T, B>& L, int post, int in_slot, int out_sl
 template <typename T, int B>
 static void launch_xmid(const Launch<T, B>& L, cudaStream_t st) {
   const int nb = L.grid(GEO_XM);
-  const size_t sm = L.smem(GEO_XM);
+  size_t sm = L.smem(GEO_XM);
+  int stage = 0;
+  if (x_stage_ok(L) && L.P.h.phase) {
+    stage = 1;
+    sm = stage_round(sm) + stage_round((size_t)L.P.h.lxm * L.P.h.n1 * 2);
+  }
   const BatchArgs<T> ba = L.args(GEO_XM);
   const Desc<T>* d = L.P.d;
   double by, fl;
@@ -394,7 +431,7 @@ static void launch_xmid(const Launch<T, B>& L, cudaStream_t st) {
         f = 2 * k.xfft(k.s) + (Q.h.ndim == 3 ? 66.0 : 15.0) * k.V;
       },
       by, fl);
-  prof_launch(prec_index(sizeof(T)), KK_XMID, by, fl, st, [&] { k_xmid<T, B><<<nb, 256, sm, st>>>(d, ba); });
+  prof_launch(prec_index(sizeof(T)), KK_XMID, by, fl, st, [&] { k_xmid<T, B><<<nb, 256, sm, st>>>(d, ba, stage); });
 }
 
 template <typename T, int B>
@@ -402,7 +439,7 @@ void launch_apply_impl(const Plan<T>& P, int pre, int in_slot, int post, int out
                        cudaStream_t st, const BatchLaunch<T>* bl) {
   const Desc<T>& D = P.h;
   const Launch<T, B> L{P, bl};
-  launch_xfwd<T, B>(L, pre, in_slot, st);
+  if (pre != PRE_NONE) launch_xfwd<T, B>(L, pre, in_slot, st);  // PRE_NONE: the spectrum of in_slot is in place
   if (D.midAxis) launch_col<T, B>(L, OP_FWD, D.midAxis, D.c, st);
   launch_col<T, B>(L, OP_GRAD, D.opAxis, D.c, st);
   if (D.midAxis) launch_col<T, B>(L, OP_INV, D.midAxis, D.s, st);
@@ -424,6 +461,20 @@ void launch_precond_impl(const Plan<T>& P, int pre, int in_slot, int out_slot, i
   launch_col<T, B>(L, OP_PREC, D.opAxis, D.c, st);
   if (D.midAxis) launch_col<T, B>(L, OP_INV, D.midAxis, D.c, st);
   launch_xinv<T, B>(L, POST_PREC, in_slot, out_slot, masked, 0, st);
+}
+
+template <typename T>
+void launch_precond_part_impl(const Plan<T>& P, int part, int pre, int in_slot, int masked, cudaStream_t st) {
+  const Desc<T>& D = P.h;
+  const Launch<T, 0> L{P, nullptr};
+  if (part == 0) {
+    launch_xfwd<T, 0>(L, pre, in_slot, st);
+    if (D.midAxis) launch_col<T, 0>(L, OP_FWD, D.midAxis, D.c, st);
+    launch_col<T, 0>(L, OP_PREC, D.opAxis, D.c, st);
+  } else {
+    if (D.midAxis) launch_col<T, 0>(L, OP_INV, D.midAxis, D.c, st);
+    launch_xinv<T, 0>(L, POST_PREC_PUPD, SL_P, SL_P, masked, 0, st);
+  }
 }
 
 // Plain 3-D transforms for testing: the x pass with c replaced by ncomp.
@@ -504,6 +555,7 @@ cudaError_t init_kernel_attributes_impl() {
   WFFT_SETATTR((k_xinv<T, POST_APPLY, B>));
   WFFT_SETATTR((k_xinv<T, POST_RESID, B>));
   WFFT_SETATTR((k_xinv<T, POST_PREC, B>));
+  if constexpr (B == 0) WFFT_SETATTR((k_xinv<T, POST_PREC_PUPD, B>));
   WFFT_SETATTR((k_xmid<T, B>));
   if (!B) WFFT_SETATTR((k_xplain<T>));
 #define WFFT_SETATTR_BX(BXV)                  \
@@ -538,6 +590,7 @@ cudaError_t init_kernel_attributes_impl() {
                                         const BatchLaunch<T>*);                                              \
   template void launch_precond_impl<T, 0>(const Plan<T>&, int, int, int, int, cudaStream_t,                  \
                                           const BatchLaunch<T>*);                                            \
+  template void launch_precond_part_impl<T>(const Plan<T>&, int, int, int, int, cudaStream_t);              \
   template int geo_blocks<T>(const Plan<T>&, int, int);                                                     \
   template size_t geo_smem<T>(const Plan<T>&, int, int);                                                    \
   template void launch_rfft3<T>(const Plan<T>&, int, int, int, cudaStream_t);                               \

@@ -15,7 +15,7 @@ enum KernelKind {
   KK_XFWD_PLAIN = 0, KK_XFWD_PUPD, KK_XFWD_RUPD, KK_XFWD_CONV,
   KK_XINV_APPLY, KK_XINV_RESID, KK_XINV_PREC, KK_XMID,
   KK_COL_FWD, KK_COL_INV, KK_COL_GRAD, KK_COL_DIV, KK_COL_PREC,
-  KK_NEWMARK, KK_SCALAR, KK_NET_CONV, KK_NET_AUX, KK_NKIND
+  KK_NEWMARK, KK_SCALAR, KK_NET_CONV, KK_NET_AUX, KK_XINV_PUPD, KK_NKIND
 };
 
 struct Profiler {

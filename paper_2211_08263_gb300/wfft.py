@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "wfft.h")
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENUMERIC, ETIMEOUT, EUNSUPPORTED = range(8)
 KERNEL_KINDS = ["xfwd_plain", "xfwd_pupd", "xfwd_rupd", "xfwd_conv", "xinv_apply", "xinv_resid", "xinv_prec",
                 "xmid", "col_fwd", "col_inv", "col_grad", "col_div", "col_prec", "newmark", "scalar", "net_conv",
-                "net_aux"]
+                "net_aux", "xinv_pupd"]
 FP64, MIXED = 0, 1
 WARM_PREV, WARM_TAYLOR, WARM_LEARNED = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ENUMERIC", 6: "ETIMEOUT",

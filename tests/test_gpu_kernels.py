@@ -49,9 +49,11 @@ def test_rfft3_matches_dft_definition(ndim, n, prec):
     assert rel(back.cpu().numpy() / V, f) < tol
 
 
+# N1 % 16 == 0 runs the FP32 x passes with staged elementwise inputs (phase ids, per-voxel
+# densities, masks, operator input); other N1 read them directly
 APPLY_CASES = [(2, (64, 64, 1), False), (2, (30, 28, 1), False), (3, (16, 12, 10), False),
                (3, (24, 20, 18), True), (3, (7, 9, 5), False), (3, (40, 36, 30), False), (3, (8, 1, 6), False),
-               (3, (8, 6, 1), True)]
+               (3, (8, 6, 1), True), (3, (32, 20, 14), True), (2, (64, 40, 1), True), (3, (48, 18, 10), False)]
 
 
 def _oracle_ops(prob):
