@@ -289,7 +289,7 @@ WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], 
 /*
  * Autotuner (not in the paper).  Times, on this handle's grid and device, every
  * radix decomposition the FFT stages support for each axis (the power-of-two part
- * as radix-16 (FP32) / radix-8 / radix-4 / one radix-2 stage in any mix), then the
+ * as radix-16 / radix-8 / radix-4 / one radix-2 stage in any mix), then the
  * x-pass tile size (1024, 2048, 4096 complex elements, capped by the register batch),
  * then every feasible column-tile width of each column pass, one choice at a time,
  * each candidate by
@@ -305,8 +305,8 @@ WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], 
 WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
 /*
  * Radix schedule of one axis of one precision's plan, set by hand: cnt[r] stages of
- * radix 8, 4, 2, 3, 5, 7, 16 (r = 0..6; their product must be the axis length; radix 16
- * only in the FP32 plan, precision WFFT_MIXED).  The stages run in the order 16s, 8s, 4s,
+ * radix 8, 4, 2, 3, 5, 7, 16 (r = 0..6; their product must be the axis length).  The
+ * stages run in the order 16s, 8s, 4s,
  * 2s, 3s, 5s, 7s.  The tile geometry follows; a schedule that would need more
  * partial-sum slots than the handle allocated is refused (EINVAL, plan unchanged).
  * Synchronises the stream.

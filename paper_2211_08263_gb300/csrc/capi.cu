@@ -1507,7 +1507,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
   if (!cached) {
     // 1. radix decomposition, axis by axis
     for (int a = 0; a < 3; ++a) {
-      const std::vector<AxisPlan> cands = factor_candidates(h->n[a], sizeof(T) == 4);
+      const std::vector<AxisPlan> cands = factor_candidates(h->n[a], true);
       if (h->n[a] == 1 || cands.size() < 2) continue;
       AxisPlan keep = D.ax[a];
       float tbest = 1e30f;
@@ -1724,7 +1724,6 @@ extern "C" int wfft_set_radix(wfft_handle* h, int precision, int axis, const int
     for (int k = 0; k < cnt[r]; ++k) prod *= rad[r];
   }
   if (prod != h->n[axis]) return fail(h, WFFT_EINVAL, "the stages' radices must multiply to the axis length");
-  if (precision == WFFT_FP64 && cnt[6]) return fail(h, WFFT_EINVAL, "radix-16 stages are FP32 only");
   ProfScope ps_(h);
   return precision == WFFT_FP64 ? set_radix_plan<double>(h, h->P64, axis, pl)
                                 : set_radix_plan<float>(h, h->P32, axis, pl);
@@ -1892,7 +1891,6 @@ int set_plan(wfft_handle* h, Plan<T>& P, const wfft_plan_choice* in) {
       for (int k = 0; k < c; ++k) prod *= rad[r];
     }
     if (prod != h->n[a]) return fail(h, WFFT_EINVAL, "a radix schedule does not multiply to its axis length");
-    if (sizeof(T) == 8 && ax[a].cnt[6]) return fail(h, WFFT_EINVAL, "radix-16 stages are FP32 only");
   }
   if (in->xelems != 0 && (in->xelems < 256 || in->xelems > 8192))
     return fail(h, WFFT_EINVAL, "the x-pass tile size must be 0 or 256..8192 elements");

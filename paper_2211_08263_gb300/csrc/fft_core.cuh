@@ -262,7 +262,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
 }
 
 // Full transform of `nlines` lines.  sgn = -1 forward, +1 inverse (unnormalised).
-// Stages are applied radix by radix (16s in FP32 plans, 8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
+// Stages are applied radix by radix (16s, 8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
 // formulation is valid for any order of the radices, and one loop per radix
 // keeps each stage's registers apart.  ES = 1: row tiles with line stride
 // `lstride` (nlines at run time), NL = 0; NL > 0: column tiles (line stride 1,
@@ -272,8 +272,7 @@ __device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int 
                                           int sgn) {
   const int N = pl.n;
   int Ns = 1;
-  if constexpr (sizeof(T) == 4)  // FP32 plans only: 16 complex per butterfly would crowd FP64 registers
-    for (int s = 0; s < pl.cnt[6]; ++s, Ns *= 16) fft_stage<T, 16, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
+  for (int s = 0; s < pl.cnt[6]; ++s, Ns *= 16) fft_stage<T, 16, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);

@@ -38,7 +38,7 @@ static inline bool factorize(int n, AxisPlan& pl) {
 }
 
 // Every decomposition of n the FFT stages support: the power-of-two part as radix-16
-// (when allow16: FP32 plans), radix-8, radix-4 and at most one radix-2 stage in any
+// (when allow16), radix-8, radix-4 and at most one radix-2 stage in any
 // mix, the odd part as 3s, 5s and 7s.  Empty if n is not supported.
 static inline std::vector<AxisPlan> factor_candidates(int n, bool allow16) {
   std::vector<AxisPlan> out;

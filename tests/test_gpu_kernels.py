@@ -134,12 +134,14 @@ RADIX_CASES = [
     (3, (64, 32, 16), 1, [[0, 1, 0, 0, 0, 0, 1], [0, 0, 1, 0, 0, 0, 1], [0, 0, 0, 0, 0, 0, 1]]),
     (3, (64, 32, 16), 0, [[0, 3, 0, 0, 0, 0, 0], [0, 2, 1, 0, 0, 0, 0], [1, 0, 1, 0, 0, 0, 0]]),
     (2, (256, 48, 1), 1, [[0, 0, 0, 0, 0, 0, 2], [0, 0, 0, 1, 0, 0, 1], None]),
+    (3, (256, 32, 48), 0, [[0, 0, 0, 0, 0, 0, 2], [0, 0, 1, 0, 0, 0, 1], [0, 0, 0, 1, 0, 0, 1]]),
+    (2, (80, 64, 1), 0, [[0, 0, 0, 0, 1, 0, 1], [0, 1, 0, 0, 0, 0, 1], None]),
 ]
 
 
 @pytest.mark.parametrize("ndim,n,prec,plans", RADIX_CASES)
 def test_hand_set_radix_schedules_match_oracle(ndim, n, prec, plans):
-    """Radix-16 stages (FP32) and other decompositions than the built-in one give the
+    """Radix-16 stages and other decompositions than the built-in one give the
     same operator and preconditioner as the oracle, at the usual tolerances."""
     from oracle import spectral
     torch = torch_cuda()
@@ -165,7 +167,7 @@ def test_hand_set_radix_schedules_match_oracle(ndim, n, prec, plans):
     assert rel(oracle_field(prob, qd.cpu().numpy().astype(np.float64)), qo) < tol
     assert rel(oracle_field(prob, zd.cpu().numpy().astype(np.float64)), zo) < tol
     with pytest.raises(wfft.WfftError):
-        s.set_radix(wfft.FP64, 0, [0, 0, 0, 0, 0, 0, 1] if n[0] == 16 else [0, 0, 0, 0, 0, 0, 9])
+        s.set_radix(wfft.FP64, 0, [0, 0, 0, 0, 0, 0, 9])
 
 
 # x-pass tile sizes other than the default (wfft_plan_choice.xelems): more or fewer lines per block
