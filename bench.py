@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--inner-floor", type=float, default=None,
                     help="mixed modes: stop an inner solve at this fraction of the outer target")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
+    ap.add_argument("--nz", type=int, default=None, help="z extent of an n x n x nz slab instead of the cube")
+    ap.add_argument("--xelems", type=int, default=None,
+                    help="x-pass tile size (complex elements) applied after tuning / plan loading")
     ap.add_argument("--no-incr-resid", action="store_true",
                     help="mixed modes: every residual is a full FP64 application (no incremental residual)")
     return ap.parse_args()
@@ -213,6 +216,7 @@ INNER_FLOOR = None  # None: the library default
 PLAN = None         # plan choices to apply instead of tuning (--plan)
 PLANS_USED = {}     # plan choices of the timed handles, per precision
 NO_INCR = False     # --no-incr-resid: full FP64 residuals only
+XELEMS = None       # --xelems: x-pass tile size set after tuning
 
 
 def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None, autotune=True):
@@ -242,6 +246,11 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
         tuned = "from plan file"
     else:
         tuned = s.autotune(3) if autotune else None
+    if XELEMS:
+        for pr in precs:
+            pl = s.get_plan(pr)
+            pl["xelems"] = XELEMS
+            s.set_plan(pr, pl)
     for pr in precs:
         PLANS_USED["fp64" if pr == wfft.FP64 else "fp32"] = s.get_plan(pr)
     for n in range(W):
@@ -444,16 +453,17 @@ def run_reference(args, prob, rank, world):
 
 def main():
     args = parse()
-    global INNER_FLOOR, PLAN, NO_INCR
+    global INNER_FLOOR, PLAN, NO_INCR, XELEMS
     if args.inner_floor is not None:
         INNER_FLOOR = args.inner_floor
     NO_INCR = args.no_incr_resid
+    XELEMS = args.xelems
     if args.plan:
         PLAN = json.load(open(args.plan))
     rank, world, local = dist_env()
     from paper_2211_08263_gb300 import inputs
     W, K = args.warmup, args.steps
-    prob = inputs.config_c3(nsteps=W + K + PROF_STEPS, n=args.n)
+    prob = inputs.config_c3(nsteps=W + K + PROF_STEPS, n=args.n, nz=args.nz)
     if args.impl == "reference":
         return run_reference(args, prob, rank, world)
 

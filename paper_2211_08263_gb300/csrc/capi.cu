@@ -160,10 +160,10 @@ static int build_plan(wfft_handle* h, Plan<T>& P, const std::vector<double>& cta
     for (int b = 0; b < 6; ++b) D.kq[a][b] = (T)kq[a][b];
   for (int ax = 0; ax < 3; ++ax) {
     if (!factorize(h->n[ax], D.ax[ax])) return fail(h, WFFT_EUNSUPPORTED, "axis length not supported");
-    auto tw = twiddles<T>(h->n[ax]);
+    // per-stage twiddles of the axis' radix schedule (rewritten by upload_desc when the
+    // schedule changes)
     cplx<T>* dtw;
-    CKH(h, dalloc(h, &dtw, tw.size() * sizeof(cplx<T>)));
-    CKH(h, cudaMemcpy(dtw, tw.data(), tw.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+    CKH(h, dalloc(h, &dtw, (size_t)h->n[ax] * sizeof(cplx<T>)));
     D.tw[ax] = dtw;
   }
   // material tables in T
@@ -206,10 +206,18 @@ static int build_plan(wfft_handle* h, Plan<T>& P, const std::vector<double>& cta
   return WFFT_OK;
 }
 
+// Descriptor and the per-stage twiddle tables of its radix schedules to the device.
 template <typename T>
 static cudaError_t upload_desc(Plan<T>& P) {
   if (!P.d) {
     cudaError_t e = cudaMalloc(&P.d, sizeof(Desc<T>));
+    if (e != cudaSuccess) return e;
+  }
+  for (int ax = 0; ax < 3; ++ax) {
+    std::vector<cplx<T>> w((size_t)P.h.ax[ax].n);
+    fill_stage_twiddles<T>(w.data(), P.h.ax[ax]);
+    cudaError_t e = cudaMemcpy(const_cast<cplx<T>*>(P.h.tw[ax]), w.data(), w.size() * sizeof(cplx<T>),
+                               cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
   }
   return cudaMemcpy(P.d, &P.h, sizeof(Desc<T>), cudaMemcpyHostToDevice);

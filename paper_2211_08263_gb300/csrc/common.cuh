@@ -88,7 +88,7 @@ struct Desc {
   T kq[6][6];              // K_ij(xi) = sum_m kq[pair][m] mono_m(xi); pairs 00,11,22,12,02,01;
                            // monomials xi1^2, xi2^2, xi3^2, xi2 xi3, xi1 xi3, xi1 xi2
   AxisPlan ax[3];
-  const cplx<T>* tw[3];    // W_N^m = exp(-2 pi i m / N), m = 0..N-1
+  const cplx<T>* tw[3];    // per-stage twiddles of ax[] (N entries; see fill_stage_twiddles)
   const uint16_t* phase;   // null: per-voxel tables
   const T* ctab;           // rows of kCtabStride3 / kCtabStride2
   const T* rhotab;

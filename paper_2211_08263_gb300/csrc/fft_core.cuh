@@ -8,8 +8,8 @@
 // y[(j div Ns) Ns R + (j mod Ns) + r Ns].  Each thread keeps its butterflies'
 // inputs in registers between two barriers, so every stage runs in place
 // on one shared-memory buffer.  Output is in natural order.  Twiddles come
-// from a table W_N^m = exp(-2 pi i m/N) (conjugated for the inverse), so no
-// trigonometric function is evaluated on the device.
+// from a per-stage table of W_{Ns R}^{r k} (host-built; conjugated for the
+// inverse), so no trigonometric function is evaluated on the device.
 #pragma once
 #include "common.cuh"
 
@@ -149,21 +149,25 @@ struct Dft<T, 5> {
   }
 };
 
-// Generic odd radix (7): direct sum with the table roots W_N^{(m q mod R) N/R}.
+// Radix 7: direct sum with the 7th roots of unity W_7^j = (cos 2 pi j/7, -sin 2 pi j/7),
+// j = (m q) mod 7, conjugated for the inverse.
 template <typename T>
 struct Dft<T, 7> {
-  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>* tw, int N) {
+  __device__ __forceinline__ static void run(cplx<T>* v, int sgn, const cplx<T>*, int) {
+    const T c7[7] = {(T)1, (T)0.62348980185873353053, (T)-0.22252093395631440429, (T)-0.90096886790241912624,
+                     (T)-0.90096886790241912624, (T)-0.22252093395631440429, (T)0.62348980185873353053};
+    const T s7[7] = {(T)0, (T)0.78183148246802980871, (T)0.97492791218182360702, (T)0.43388373911755812048,
+                     (T)-0.43388373911755812048, (T)-0.97492791218182360702, (T)-0.78183148246802980871};
     cplx<T> in[7];
 #pragma unroll
     for (int m = 0; m < 7; ++m) in[m] = v[m];
-    const int step = N / 7;
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       cplx<T> acc = in[0];
 #pragma unroll
       for (int m = 1; m < 7; ++m) {
-        cplx<T> w = tw[((m * q) % 7) * step];
-        if (sgn > 0) w.y = -w.y;
+        const int j = (m * q) % 7;
+        const cplx<T> w = cmake<T>(c7[j], sgn > 0 ? s7[j] : -s7[j]);
         acc = cadd<T>(acc, cmul<T>(in[m], w));
       }
       v[q] = acc;
@@ -243,10 +247,11 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
         g = j / Ns;
       }
       if (Ns > 1) {
-        const int step = (N / (Ns * R)) * k;
+        // per-stage table: W_{Ns R}^{r k} at (Ns - 1) + (r - 1) Ns + k
+        const cplx<T>* tws = tw + (Ns - 1) + k;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          cplx<T> w = tw[step * r];
+          cplx<T> w = tws[(r - 1) * Ns];
           if (sgn > 0) w.y = -w.y;
           v[i][r] = cmul<T>(v[i][r], w);
         }

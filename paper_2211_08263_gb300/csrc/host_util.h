@@ -77,6 +77,36 @@ static inline std::vector<cplx<T>> twiddles(int n) {
   return w;
 }
 
+// Per-stage twiddle table of a radix schedule (the stages in the order the FFT runs
+// them: 16s, 8s, 4s, 2s, 3s, 5s, 7s).  The stage of radix R after Ns points have
+// been combined uses W_{Ns R}^{r k} (r = 1..R-1, k = 0..Ns-1), kept at
+// (Ns - 1) + (r - 1) Ns + k: consecutive butterflies of a stage read consecutive
+// entries (no shared-memory bank conflicts), and since the blocks of successive stages
+// have Ns (R - 1) = Ns' - Ns entries the table has exactly n - 1 entries (n entries
+// are written, the last one unused).
+template <typename T>
+static inline void fill_stage_twiddles(cplx<T>* w, const AxisPlan& pl) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const int rad[7] = {16, 8, 4, 2, 3, 5, 7};
+  const int cnt[7] = {pl.cnt[6], pl.cnt[0], pl.cnt[1], pl.cnt[2], pl.cnt[3], pl.cnt[4], pl.cnt[5]};
+  for (int i = 0; i < pl.n; ++i) {
+    w[i].x = (T)1;
+    w[i].y = (T)0;
+  }
+  int Ns = 1;
+  for (int q = 0; q < 7; ++q)
+    for (int s = 0; s < cnt[q]; ++s) {
+      const int R = rad[q];
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          const long double a = -2.0L * pi * (long double)(r * k) / (long double)(Ns * R);
+          w[(Ns - 1) + (r - 1) * Ns + k].x = (T)cosl(a);
+          w[(Ns - 1) + (r - 1) * Ns + k].y = (T)sinl(a);
+        }
+      Ns *= R;
+    }
+}
+
 // Cholesky test of a symmetric matrix (row-major, size k)
 static inline bool spd(const double* m, int k) {
   double L[36] = {0};

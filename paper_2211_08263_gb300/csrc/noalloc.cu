@@ -136,7 +136,7 @@ extern "C" int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21]
   double2 tw[512];
   size_t off = off_tw;
   for (int ax = 0; ax < 3; ++ax) {
-    fill_twiddles<double>(tw, grid->n[ax]);
+    fill_stage_twiddles<double>(tw, D.ax[ax]);
     e = cudaMemcpyAsync(base + off, tw, (size_t)grid->n[ax] * sizeof(double2), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return na_fail(WFFT_ECUDA, cudaGetErrorString(e));
     D.tw[ax] = reinterpret_cast<const double2*>(base + off);
