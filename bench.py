@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the launch-bound C1 (64^2) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT plans (no wfft_autotune)")
     ap.add_argument("--no-explicit", action="store_true", help="skip the explicit-scheme measurement")
-    ap.add_argument("--plan", default=None, help="JSON plan choices to apply instead of autotuning")
+    ap.add_argument("--plan", default=None,
+                    help="plan choices to apply instead of autotuning: a JSON file, or the JSON text itself")
     ap.add_argument("--save-plan", default=None, help="write the plan choices of the timed handles (JSON)")
     ap.add_argument("--inner-floor", type=float, default=None,
                     help="mixed modes: stop an inner solve at this fraction of the outer target")
@@ -459,7 +460,7 @@ def main():
     NO_INCR = args.no_incr_resid
     XELEMS = args.xelems
     if args.plan:
-        PLAN = json.load(open(args.plan))
+        PLAN = json.loads(args.plan) if args.plan.lstrip().startswith("{") else json.load(open(args.plan))
     rank, world, local = dist_env()
     from paper_2211_08263_gb300 import inputs
     W, K = args.warmup, args.steps

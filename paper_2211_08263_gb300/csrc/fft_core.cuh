@@ -179,12 +179,14 @@ struct Dft<T, 7> {
 __device__ __forceinline__ int log2_if_pow2(int v) { return (v & (v - 1)) ? -1 : __ffs(v) - 1; }
 
 // Row tiles store element e of a line at rowpad(e): one unused slot after every
-// 8 elements.  The radix-8 stages write butterfly outputs at stride 8 (and 8 Ns)
-// elements; with the pad, 16 consecutive butterflies land in 16 distinct 8-byte
-// bank pairs instead of 2.
-__host__ __device__ __forceinline__ constexpr int rowpad(int e) { return e + (e >> 3); }
+// 16 elements (128 bytes of FP32 complex).  The first stage of radix R writes
+// butterfly outputs at stride R (R = 2, 4, 8, 16); with the pad, the 16 butterflies of
+// a half-warp land in 16 distinct 8-byte bank pairs, and consecutive-element reads and
+// writes of two lines of a warp (line stride N + N/16 + 1) take the minimum of two
+// wavefronts (a one-slot pad per 8 elements made them take three).
+__host__ __device__ __forceinline__ constexpr int rowpad(int e) { return e + (e >> 4); }
 // Line stride (complex elements) of a row tile of lines of length N.
-__host__ __device__ __forceinline__ constexpr int row_stride(int N) { return N + (N >> 3) + 1; }
+__host__ __device__ __forceinline__ constexpr int row_stride(int N) { return N + (N >> 4) + 1; }
 
 // One in-place Stockham stage over `nlines` lines of length N.
 // Row tiles (NL == 0, ES == 1): element e of line l at buf[l * lstride + rowpad(e)];
