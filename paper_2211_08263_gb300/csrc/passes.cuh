@@ -552,6 +552,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc
 constexpr int kColThreadsPlain = 256;  // plain transforms (one component per block)
 constexpr int kColThreadsOp = 256;     // fused gradient / divergence / preconditioner
 
+// Element stride of a column tile of ns slots x bx columns: ns bx plus a pad for the
+// six-slot (3-D gradient / divergence) tiles, chosen so that the FFT stages' reads and
+// writes of 3 bx interleaved lines spread over the shared-memory banks (e.g. 24 -> 28
+// for bx = 4 in FP32: three wavefronts per warp access on average become two).
+__host__ __device__ __forceinline__ constexpr int col_es(int ns, int bx, int tsize) {
+  return ns * bx + (ns != 6 ? 0
+                    : tsize == 4 ? (bx == 1 ? 1 : bx == 2 ? 7 : bx == 4 ? 4 : 8)
+                                 : (bx == 1 ? 5 : bx == 2 ? 2 : bx == 4 ? 4 : 0));
+}
+
 template <typename T>
 struct ColGeo {
   int N;          // axis length
@@ -685,7 +695,7 @@ __global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4)
 template <typename T, int OP, int BX, int NS, int BATCH>
 __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3)
     k_colop(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int axis) {
-  constexpr int ES = NS * BX;
+  constexpr int ES = col_es(NS, BX, (int)sizeof(T));
   int blk;
   const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
   const Desc<T>& D = *Dp;

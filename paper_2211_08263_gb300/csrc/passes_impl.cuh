@@ -77,10 +77,11 @@ void plan_geometry(Plan<T>& P) {
       const int thr = plain ? kColThreadsPlain : kColThreadsOp;
       const int maxe = max_tile_elems<T>(D.ax[ax], thr);
       int bx = plain ? maxbx : std::min(maxbx, 4);
-      while (bx > 1 && ((long long)nb * bx * N > maxe || (size_t)ns * bx * N * cs > 64 * 1024)) bx >>= 1;
+      while (bx > 1 && ((long long)nb * bx * N > maxe || (size_t)col_es(ns, bx, sizeof(T)) * N * cs > 64 * 1024))
+        bx >>= 1;
       g.bx[ax][op] = bx;
       g.blk_col[ax][op] = ((D.nh + bx - 1) / bx) * nouter;
-      g.sm_col[ax][op] = (size_t)(N + ns * bx * N) * cs;
+      g.sm_col[ax][op] = (size_t)(N + col_es(ns, bx, sizeof(T)) * N) * cs;
       g.max_blocks = std::max(g.max_blocks, g.blk_col[ax][op]);
     }
   }
@@ -99,7 +100,7 @@ bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx) {
   const int maxbx = plain && sizeof(T) == 4 ? 8 : 4;
   if (bx < 1 || bx > maxbx || (bx & (bx - 1))) return false;
   return (long long)col_batch_slots(op, ns) * bx * N <= max_tile_elems<T>(D.ax[axis], thr) &&
-         (size_t)ns * bx * N * sizeof(cplx<T>) <= 64 * 1024;
+         (size_t)col_es(ns, bx, sizeof(T)) * N * sizeof(cplx<T>) <= 64 * 1024;
 }
 
 template <typename T>
@@ -111,7 +112,7 @@ void set_col_bx(Plan<T>& P, int axis, int op, int bx) {
   const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
   P.g.bx[axis][op] = bx;
   P.g.blk_col[axis][op] = ((D.nh + bx - 1) / bx) * nouter;
-  P.g.sm_col[axis][op] = (size_t)(N + ns * bx * N) * sizeof(cplx<T>);
+  P.g.sm_col[axis][op] = (size_t)(N + col_es(ns, bx, sizeof(T)) * N) * sizeof(cplx<T>);
   P.g.max_blocks = std::max(P.g.max_blocks, P.g.blk_col[axis][op]);
 }
 
@@ -168,7 +169,7 @@ size_t geo_smem(const Plan<T>& P, int cls, int bx) {
   const int N = axis == 1 ? D.n2 : D.n3;
   const bool plain = op == OP_FWD || op == OP_INV;
   const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
-  return (size_t)(N + ns * bx * N) * cs;
+  return (size_t)(N + col_es(ns, bx, (int)sizeof(T)) * N) * cs;
 }
 
 template <typename T, int B>
