@@ -173,7 +173,7 @@ def net_roofline(prof):
     ach = d["flops"] / d["timed"] / (per * 1e-3) / 1e12
     return {"kernel": "net_conv (bf16 mma.sync, f32 accumulate)", "bound": "tensor", "achieved": ach, "peak": peak,
             "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src, "ms_per_launch": per,
-            "launches": d["timed"], "ms_total": d["ms"]}
+            "launches": d["timed"], "ms_total": d["ms"], "traffic": None}
 
 
 # FP64 FMA throughput of a GB300, measured with an FMA-chain microbenchmark

@@ -314,7 +314,8 @@ WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
 WFFT_API int wfft_set_radix(wfft_handle* h, int precision, int axis, const int cnt[7]);
 /* The plan choices of one precision: radix[axis][r] stage counts (as wfft_set_radix),
    bx[axis][op] column-tile widths (axes 1, 2; op 0 forward, 1 inverse, 2 gradient, 3
-   divergence, 4 preconditioner; entries of passes the grid does not run are ignored) and
+   divergence, 4 preconditioner; powers of two up to 4, or 16 for the FP32 plain passes;
+   entries of passes the grid does not run are ignored) and
    xelems, the complex elements per x-pass tile (0 = the default 2048; 256..8192, capped
    by the register batch of the radix schedule).
    wfft_get_plan reads them (e.g. after wfft_autotune); wfft_set_plan applies them to a

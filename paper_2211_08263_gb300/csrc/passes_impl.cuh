@@ -97,7 +97,7 @@ bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx) {
   const bool plain = op == OP_FWD || op == OP_INV;
   const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
   const int thr = plain ? kColThreadsPlain : kColThreadsOp;
-  const int maxbx = plain && sizeof(T) == 4 ? 8 : 4;
+  const int maxbx = plain && sizeof(T) == 4 ? 16 : 4;  // 16-wide plain tiles: FP32 only (tuned, not default)
   if (bx < 1 || bx > maxbx || (bx & (bx - 1))) return false;
   return (long long)col_batch_slots(op, ns) * bx * N <= max_tile_elems<T>(D.ax[axis], thr) &&
          (size_t)col_es(ns, bx, sizeof(T)) * N * sizeof(cplx<T>) <= 64 * 1024;
@@ -334,6 +334,9 @@ template <typename T, int B>
 static void launch_col(const Launch<T, B>& L, int op, int axis, int ncomp, cudaStream_t st) {
   if (op == OP_FWD || op == OP_INV) {
     switch (L.bx(axis, op)) {
+      case 16:
+        if constexpr (sizeof(T) == 4) launch_colplain_bx<T, 16, B>(L, op, axis, ncomp, st);
+        break;
       case 8: launch_colplain_bx<T, 8, B>(L, op, axis, ncomp, st); break;
       case 4: launch_colplain_bx<T, 4, B>(L, op, axis, ncomp, st); break;
       case 2: launch_colplain_bx<T, 2, B>(L, op, axis, ncomp, st); break;
@@ -577,6 +580,10 @@ cudaError_t init_kernel_attributes_impl() {
   WFFT_SETATTR((k_colplain<T, OP_INV, 4, B>));
   WFFT_SETATTR((k_colplain<T, OP_FWD, 8, B>));
   WFFT_SETATTR((k_colplain<T, OP_INV, 8, B>));
+  if constexpr (sizeof(T) == 4) {
+    WFFT_SETATTR((k_colplain<T, OP_FWD, 16, B>));
+    WFFT_SETATTR((k_colplain<T, OP_INV, 16, B>));
+  }
 #undef WFFT_SETATTR_BX
 #undef WFFT_SETATTR
   return e;

@@ -205,3 +205,32 @@ def test_x_tile_sizes_match_oracle(ndim, n, prec, xelems):
     plan["xelems"] = 100
     with pytest.raises(wfft.WfftError):
         s.set_plan(pr, plan)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_wide_plain_column_tiles_match_oracle(prec):
+    """Plain column passes 16 columns wide (FP32 only; FP64 refuses them) give the oracle's operator."""
+    from oracle import spectral
+    torch = torch_cuda()
+    wfft = solver_lib()
+    n = (64, 48, 20)
+    rng = np.random.default_rng(77 + prec)
+    prob = inputs.random_problem(rng, 3, n, nphase=4, mask_width=2, contrast=4.0, dt=4e-7)
+    s = _solver(prob, prec)
+    pr = wfft.MIXED if prec else wfft.FP64
+    plan = s.get_plan(pr)
+    plan["bx"][1][0] = plan["bx"][1][1] = 16
+    if prec == 0:
+        with pytest.raises(wfft.WfftError):
+            s.set_plan(pr, plan)
+        return
+    s.set_plan(pr, plan)
+    assert s.get_plan(pr)["bx"][1][:2] == [16, 16]
+    med, sp, th = _oracle_ops(prob)
+    p = rng.standard_normal((3, n[2], n[1], n[0]))
+    pd = to_dev(torch, p, torch.float32)
+    qd = torch.zeros_like(pd)
+    s.apply(pd, qd, precision=prec, masked=False)
+    torch.cuda.synchronize()
+    qo = spectral.apply_A(med, sp, oracle_field(prob, p), th)
+    assert rel(oracle_field(prob, qd.cpu().numpy().astype(np.float64)), qo) < 3e-6
