@@ -173,7 +173,7 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const cplx<T>* src, i
 //              finished inner correction into the FP64 solution) and transform x
 // ---------------------------------------------------------------------------
 template <typename T, int PRE, int BATCH>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int in_slot) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_xfwd(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int in_slot) {
   int blk;
   const Desc<T>* __restrict__ Dp = pick_ptr<T, BATCH>(dd, ba, blk);
   const Desc<T>& D = *Dp;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xfwd(const Desc
 //               never goes to memory
 // ---------------------------------------------------------------------------
 template <typename T, int POST, int BATCH>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xinv(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int in_slot,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_xinv(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int in_slot,
                                               int out_slot, int masked, int want_dot, int stage_arg) {
   const int stage = sizeof(T) == 4 ? stage_arg : 0;  // FP32 passes only
   int blk;
@@ -479,7 +479,7 @@ __device__ __forceinline__ void load_row(const T* __restrict__ src, T* dst, int 
 }
 
 template <typename T, int BATCH>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3) k_xmid(const Desc<T>* __restrict__ dd, BatchArgs<T> ba,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 4) k_xmid(const Desc<T>* __restrict__ dd, BatchArgs<T> ba,
                                                                         int stage_arg) {
   const int stage = sizeof(T) == 4 ? stage_arg : 0;  // FP32 passes only
   int blk;
