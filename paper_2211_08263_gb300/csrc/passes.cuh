@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4)
 //   OP_PREC: c residuals r^ -> z^ = (1/V) (theta K(xi) + rho_bar I)^-1 r^, with the
 //            Parseval partial sum of (r, z) over the half spectrum
 template <typename T, int OP, int BX, int NS, int BATCH>
-__global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 3)
+__global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 4)
     k_colop(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int axis) {
   constexpr int ES = col_es(NS, BX, (int)sizeof(T));
   int blk;
