@@ -152,6 +152,16 @@ WFFT_API int wfft_set_state(wfft_handle* h, const double* u, const double* v, co
 
 /* Copy the state to host arrays (any pointer may be NULL) and return the step counter in *n. */
 WFFT_API int wfft_get_state(const wfft_handle* h, double* u, double* v, double* a, long long* n);
+/* Asynchronous download of the state (u, v, a; NULL entries skipped) to host memory
+   (pinned memory for overlap; pageable memory works but is staged): the copies are
+   ordered after all work issued so far on the handle's stream and run on an internal
+   copy stream, so they overlap the next wfft_step's solve; the next call that writes
+   the state (the corrector of wfft_step / wfft_green_step / wfft_batch_step, the
+   explicit predictor, wfft_set_state*) waits for them on the device.  The host buffers
+   must stay valid until wfft_download_wait returns. */
+WFFT_API int wfft_download_async(wfft_handle* h, double* u, double* v, double* a);
+/* Blocks until the latest wfft_download_async of h has completed. */
+WFFT_API int wfft_download_wait(wfft_handle* h);
 
 /* Device-pointer variants (caller-owned FP64 device arrays, same layout). */
 WFFT_API int wfft_set_state_dev(wfft_handle* h, const double* u, const double* v, const double* a, long long n);

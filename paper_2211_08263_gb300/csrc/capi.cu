@@ -47,7 +47,8 @@ struct wfft_handle {
   Plan<float> P32;
   Scalars* sc64 = nullptr;
   Scalars* sc32 = nullptr;
-  Scalars* host_sc = nullptr;  // pinned: [0] = sc64, [1] = sc32
+  Scalars* host_sc = nullptr;  // host-mapped pinned: [0] = sc64, [1] = sc32
+  Scalars* host_sc_dev = nullptr;  // its device address
   std::vector<void*> dev_allocs;
   int nparts = 0;
   long long nstep = 0;
@@ -63,6 +64,11 @@ struct wfft_handle {
   double rhobar = 0;
   // CUDA graphs of one block of check_every PCG iterations, per precision (captured lazily)
   cudaStream_t cap_st = nullptr;
+  // asynchronous state downloads (wfft_download_async): copy stream, "state ready" and
+  // "copies done" events; the next kernel that writes the state waits for the copies
+  cudaStream_t dl_st = nullptr;
+  cudaEvent_t dl_ready = nullptr, dl_done = nullptr;
+  bool dl_pending = false;
   cudaGraphExec_t chunk[2] = {nullptr, nullptr};
   long long chunk_launches[2] = {0, 0};
   bool explicit_scheme = false;  // beta = 0, gamma = 1/2 (wfft_explicit_step)
@@ -460,7 +466,8 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   D.sc = h->sc64;
   F.sc = h->sc32;
   D.sc_inner = h->sc32;
-  CKC(cudaMallocHost(&h->host_sc, 2 * sizeof(Scalars)));
+  CKC(cudaHostAlloc(&h->host_sc, 2 * sizeof(Scalars), cudaHostAllocMapped));
+  CKC(cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->host_sc_dev), h->host_sc, 0));
   memset(h->host_sc, 0, 2 * sizeof(Scalars));
   CKC(upload_desc(h->P64));
   CKC(upload_desc(h->P32));
@@ -491,6 +498,12 @@ extern "C" void wfft_destroy(wfft_handle* h) {
   for (int k = 0; k < 2; ++k)
     if (h->chunk[k]) cudaGraphExecDestroy(h->chunk[k]);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  if (h->dl_st) {
+    cudaStreamSynchronize(h->dl_st);
+    cudaStreamDestroy(h->dl_st);
+  }
+  if (h->dl_ready) cudaEventDestroy(h->dl_ready);
+  if (h->dl_done) cudaEventDestroy(h->dl_done);
   for (void* p : h->dev_allocs) cudaFree(p);
   net_free(h->net);
   net_work_free(&h->nw);
@@ -528,8 +541,20 @@ extern "C" int wfft_spectral_pitch(const wfft_handle* h, int* pitch) {
   return WFFT_OK;
 }
 
+// Orders the next state write on stream st after the pending asynchronous downloads.
+static int wait_downloads(wfft_handle* h, cudaStream_t st) {
+  if (!h->dl_pending) return WFFT_OK;
+  CKH(h, cudaStreamWaitEvent(st, h->dl_done, 0));
+  if (st == h->st) h->dl_pending = false;
+  return WFFT_OK;
+}
+
 static int state_copy(wfft_handle* h, int to_dev, double* u, double* v, double* a, cudaMemcpyKind kind) {
   const size_t bytes = (size_t)h->c * h->V * sizeof(double);
+  if (to_dev) {
+    int rc = wait_downloads(h, h->st);
+    if (rc) return rc;
+  }
   double* dst[3] = {(double*)h->P64.h.slot[SL_U], (double*)h->P64.h.slot[SL_V], (double*)h->P64.h.slot[SL_A]};
   double* src[3] = {u, v, a};
   for (int i = 0; i < 3; ++i) {
@@ -543,6 +568,31 @@ static int state_copy(wfft_handle* h, int to_dev, double* u, double* v, double* 
     }
   }
   CKH(h, cudaStreamSynchronize(h->st));
+  return WFFT_OK;
+}
+
+extern "C" int wfft_download_async(wfft_handle* h, double* u, double* v, double* a) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (!h->dl_st) {
+    CKH(h, cudaStreamCreateWithFlags(&h->dl_st, cudaStreamNonBlocking));
+    CKH(h, cudaEventCreateWithFlags(&h->dl_ready, cudaEventDisableTiming));
+    CKH(h, cudaEventCreateWithFlags(&h->dl_done, cudaEventDisableTiming));
+  }
+  const size_t bytes = (size_t)h->c * h->V * sizeof(double);
+  double* src[3] = {(double*)h->P64.h.slot[SL_U], (double*)h->P64.h.slot[SL_V], (double*)h->P64.h.slot[SL_A]};
+  double* dst[3] = {u, v, a};
+  CKH(h, cudaEventRecord(h->dl_ready, h->st));
+  CKH(h, cudaStreamWaitEvent(h->dl_st, h->dl_ready, 0));
+  for (int i = 0; i < 3; ++i)
+    if (dst[i]) CKH(h, cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToHost, h->dl_st));
+  CKH(h, cudaEventRecord(h->dl_done, h->dl_st));
+  h->dl_pending = true;
+  return WFFT_OK;
+}
+
+extern "C" int wfft_download_wait(wfft_handle* h) {
+  if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
+  if (h->dl_done) CKH(h, cudaEventSynchronize(h->dl_done));
   return WFFT_OK;
 }
 
@@ -571,8 +621,8 @@ extern "C" int wfft_get_state_dev(const wfft_handle* hc, double* u, double* v, d
 }
 
 static int read_scalars(wfft_handle* h) {
-  CKH(h, cudaMemcpyAsync(&h->host_sc[0], h->sc64, sizeof(Scalars), cudaMemcpyDeviceToHost, h->st));
-  CKH(h, cudaMemcpyAsync(&h->host_sc[1], h->sc32, sizeof(Scalars), cudaMemcpyDeviceToHost, h->st));
+  launch_read_scalars(h->sc64, h->sc32, h->host_sc_dev, h->st);
+  CKH(h, cudaGetLastError());
   CKH(h, cudaStreamSynchronize(h->st));
   return WFFT_OK;
 }
@@ -840,6 +890,8 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
   h->au_valid = status == WFFT_OK && mixed && h->last_resid_on_x && !h->host_sc[0].zero_free;
   if (status == WFFT_OK) {
     for (int k = 0; k < 3; ++k) h->U_prev[k] = Uv[k];
+    int rcw = wait_downloads(h, h->st);  // the corrector overwrites u, v, a
+    if (rcw) return rcw;
     launch_correct(P, h->st);
     const int nb = ew_block_count(P);
     launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
@@ -1383,6 +1435,10 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
   std::vector<char> closed(n, 0);
   for (int i = 0; i < n; ++i) closed[i] = !B.host[i].done;
   launch_fin_batch(B.fin[FJ_REF], n, FIN_CLOSE, st);
+  for (int i = 0; i < n; ++i) {
+    int rcw = wait_downloads(hs[i], st);
+    if (rcw) return rcw;
+  }
   launch_correct(P0, st, &B.bl64);
   launch_fin_batch(B.fin[FJ_REACT], n, FIN_REACT, st);
   CKH(h0, cudaEventRecord(h0->ev1, st));
@@ -1640,6 +1696,10 @@ extern "C" int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_ste
   const double Uv[3] = {Udot[0], h->ndim > 1 ? Udot[1] : 0.0, h->ndim > 2 ? Udot[2] : 0.0};
   CKH(h, cudaEventRecord(h->ev0, h->st));
   launch_set_done(h->sc64, 0, h->st);
+  {
+    int rcw = wait_downloads(h, h->st);  // the explicit predictor overwrites u
+    if (rcw) return rcw;
+  }
   launch_explicit_predict(P, h->st);
   // q = -div(C : grad^s u_n), every DOF (unmasked)
   launch_apply<double>(P, PRE_PLAIN, SL_U, POST_PREC, SL_Q, 0, 0, h->st);
@@ -1849,6 +1909,10 @@ extern "C" int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info
   // u_n = u_b + u_f, then the corrector (it rebuilds u~ from the unchanged state)
   launch_green_axpy(P, x, h->green_ub, h->st);
   launch_begin(h->sc64, Uv, WFFT_WARM_PREV, h->opt.tol * h->opt.tol, h->opt.maxit, h->st);
+  {
+    int rcw = wait_downloads(h, h->st);
+    if (rcw) return rcw;
+  }
   launch_correct(P, h->st);
   const int nb = ew_block_count(P);
   launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);

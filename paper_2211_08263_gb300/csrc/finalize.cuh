@@ -41,6 +41,8 @@ void launch_fin(Scalars* sc, const double* pa, int na, const double* pb, int nb,
 void launch_begin(Scalars* sc, const double U[3], int warm, double tol2, int maxit, cudaStream_t st,
                   int use_au = 0, const double* dU = nullptr, double flr = 0.0, double rb = 0.0);
 void launch_set_done(Scalars* sc, int done, cudaStream_t st);
+// sc64 / sc32 of a solve into dst[0..1] (host-mapped memory) with a kernel.
+void launch_read_scalars(const Scalars* a, const Scalars* b, Scalars* dst, cudaStream_t st);
 int ew_block_count(const Plan<double>& P);
 
 // Incremental residual of a mixed solve (after a sweep that followed a full FP64

@@ -677,6 +677,20 @@ void launch_gather_scalars(Scalars* const* src, Scalars* dst, int n, cudaStream_
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_gather_scalars<<<8, 256, 0, st>>>(src, dst, n); });
 }
 
+// Copy of a solve's two scalar blocks into host-mapped memory by the SMs themselves:
+// the read-back needs no copy engine, so it does not queue behind a large
+// asynchronous state download on another stream.
+__global__ void k_read_scalars(const Scalars* a, const Scalars* b, Scalars* dst) {
+  const int words = (int)(sizeof(Scalars) / sizeof(int));
+  for (int t = threadIdx.x; t < 2 * words; t += blockDim.x) {
+    const int i = t / words, w = t - i * words;
+    reinterpret_cast<int*>(dst + i)[w] = reinterpret_cast<const int*>(i ? b : a)[w];
+  }
+}
+void launch_read_scalars(const Scalars* a, const Scalars* b, Scalars* dst, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_read_scalars<<<1, 128, 0, st>>>(a, b, dst); });
+}
+
 void launch_set_done(Scalars* sc, int done, cudaStream_t st) {
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_set_done<<<1, 32, 0, st>>>(sc, done); });
 }

@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH):
     lib.wfft_green_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_step.argtypes = [vp, P(d), P(StepInfo)]
     lib.wfft_explicit_dt.argtypes = [i, P(d), vp, vp, C.c_longlong, P(d)]
+    lib.wfft_download_async.argtypes = [vp, vp, vp, vp]
+    lib.wfft_download_wait.argtypes = [vp]
     lib.wfft_operator_bound.argtypes = [i, P(i), P(d), vp, vp, C.c_longlong, d, P(d)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
     lib.wfft_model_bytes.argtypes = [i]
@@ -215,6 +217,25 @@ class Solver:
         n = C.c_longlong()
         self._check(self.lib.wfft_get_state(self.h, _ptr(out), None, None, C.byref(n)))
         return n.value
+
+    def download_async(self, u: Optional[np.ndarray] = None, v: Optional[np.ndarray] = None,
+                       a: Optional[np.ndarray] = None) -> None:
+        """Start copying the state into host arrays ([c][N3][N2][N1] float64, contiguous;
+        pinned memory overlaps with the next step).  The arrays must stay alive and unread
+        until download_wait() (wfft_download_async)."""
+        ptrs = []
+        for x in (u, v, a):
+            if x is None:
+                ptrs.append(None)
+                continue
+            if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size != self.shape[0] * self.V:
+                raise ValueError("download buffers must be contiguous float64 arrays of the state's size")
+            ptrs.append(_ptr(x))
+        self._check(self.lib.wfft_download_async(self.h, *ptrs))
+
+    def download_wait(self) -> None:
+        """Block until the latest download_async has landed (wfft_download_wait)."""
+        self._check(self.lib.wfft_download_wait(self.h))
 
     def set_state_dev(self, u, v, a, n: int = 0):
         self._check(self.lib.wfft_set_state_dev(self.h, _dptr(u), _dptr(v), _dptr(a), n))

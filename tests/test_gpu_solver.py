@@ -284,3 +284,39 @@ def test_inner_floor_keeps_the_accuracy_and_never_adds_iterations():
         assert rel(oracle_field(prob, u), so.u) < 1e-6
         assert all(i["rel_res"] <= 1e-10 * 1.0001 for i in infos)
     assert sum(i["iters"] for i in runs[0.5][1]) <= sum(i["iters"] for i in runs[0.0][1])
+
+
+def test_async_download_matches_sync_and_is_ordered_before_state_writes():
+    """wfft_download_async copies u_n (and v, a) while the next step runs: the copies equal
+    the synchronous wfft_get_state bit for bit, and a state write issued right after the
+    download (set_state) does not reach the copy."""
+    torch = torch_cuda()
+    wfft = solver_lib()
+    rng = np.random.default_rng(31)
+    prob = inputs.random_problem(rng, 3, (24, 20, 16), nphase=3, mask_width=2, nsteps=5, contrast=3.0)
+    prob.U[:, 0] = 1e-6 * np.arange(1, 6)
+    opts = wfft.default_options(precision=wfft.MIXED, tol=1e-10)
+    ref = wfft.Solver.from_problem(prob, options=opts)
+    want = []
+    for k in range(prob.nsteps):
+        ref.step(prob.U[k])
+        want.append(ref.get_state()[0].copy())
+    ref.close()
+    s = wfft.Solver.from_problem(prob, options=opts)
+    bufs = [torch.empty(s.shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(prob.nsteps)]
+    for k in range(prob.nsteps):
+        s.step(prob.U[k])
+        s.download_async(bufs[k])
+    s.download_wait()
+    for k in range(prob.nsteps):
+        assert np.array_equal(bufs[k], want[k]), k
+    u, v, a = (torch.empty(s.shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3))
+    u0, v0, a0, _ = s.get_state()
+    s.download_async(u, v, a)
+    s.set_state(np.zeros(s.shape), np.zeros(s.shape), np.zeros(s.shape))
+    s.download_wait()
+    assert np.array_equal(u, u0) and np.array_equal(v, v0) and np.array_equal(a, a0)
+    assert not s.get_state()[0].any()
+    with pytest.raises(ValueError):
+        s.download_async(np.zeros(5))
+    s.close()
