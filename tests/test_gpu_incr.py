@@ -139,3 +139,53 @@ def test_tight_tolerance_still_meets_the_true_residual():
     print([i["incr_resids"] for i in infos], [i["outer_applies"] for i in infos], max(tr))
     assert all(i["status"] == 0 for i in infos)
     assert max(tr) <= 1e-12 * (1 + 1e-3), max(tr)
+
+
+@pytest.mark.parametrize("warm", ["taylor", "learned"])
+def test_incremental_residual_with_increment_warm_starts(warm):
+    """With the Taylor or a learned increment as the first inner solve's initial guess
+    (stored A u, FP32 residual of the increment), every step certified with an incremental
+    last residual still meets the true FP64 residual bound."""
+    torch = torch_cuda()
+    wfft = solver_lib()
+    prob = _pulse_problem((32, 32, 32), 17, 8, width=5.0)
+    opts = wfft.default_options(precision=wfft.MIXED, tol=1e-10,
+                                warm_start=wfft.WARM_TAYLOR if warm == "taylor" else wfft.WARM_LEARNED)
+    s = wfft.Solver.from_problem(prob, options=opts)
+    if warm == "learned":
+        rng = np.random.default_rng(3)
+        _, params = wfft.blob_params(wfft.model_init(16, 5))
+        W4 = 0.3 * rng.standard_normal(params[3][0].shape) / np.sqrt(27 * 16)
+        params[3] = (W4.astype(np.float32), params[3][1])
+        s.set_model(wfft.params_blob(16, params))
+    rho = prob.rho_field()[None]
+    gamma_dofs = prob.mask.astype(bool)
+    n_incr, worst = 0, 0.0
+    for k in range(prob.nsteps):
+        u, v, a, _ = s.get_state()
+        b = rho * (u + prob.dt * v + prob.dt ** 2 * (0.5 - prob.beta) * a)
+        info = s.step(prob.U[k])
+        q = torch.zeros(s.shape, dtype=torch.float64, device="cuda")
+        s.apply(to_dev(torch, s.get_state()[0], torch.float64), q, precision=wfft.FP64, masked=False)
+        torch.cuda.synchronize()
+        r = b - q.cpu().numpy()
+        r[gamma_dofs] = 0.0
+        worst = max(worst, np.linalg.norm(r) / info["ref"])
+        n_incr += info["incr_resids"]
+    s.close()
+    assert n_incr >= prob.nsteps // 2
+    assert worst <= prob.tol * (1 + 1e-6), worst
+
+
+def test_incremental_residual_plane_strain_matches_oracle():
+    from oracle import newmark
+    torch = torch_cuda()
+    wfft = solver_lib()
+    rng = np.random.default_rng(23)
+    prob = inputs.random_problem(rng, 2, (96, 64, 1), nphase=4, mask_width=3, nsteps=6, contrast=3.0)
+    prob.U[:, 0] = 1e-6 * np.sin(np.linspace(0.3, 1.5, 6))
+    u_i, inf_i, tr_i = _run_checked(wfft, torch, prob, 1, tol=1e-10)
+    assert all(i["status"] == 0 for i in inf_i)
+    assert max(tr_i) <= 1e-10 * (1 + 1e-6)
+    so, _ = newmark.oracle_from_problem(prob, tol=1e-13).run(prob.U)
+    assert rel(oracle_field(prob, u_i), so.u) < 1e-6
