@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs p) {
             const __nv_bfloat162 gt = reinterpret_cast<const __nv_bfloat162*>(p.gate)[(vox * COUT + col) >> 1];
             const float v0 = __low2float(gt) > 0.f ? c0 : 0.f, v1 = __high2float(gt) > 0.f ? c1 : 0.f;
             reinterpret_cast<__nv_bfloat162*>(p.out)[(vox * COUT + col) >> 1] = __floats2bfloat162_rn(v0, v1);
-          } else {  // EPI_WARM
+          } else {  // EPI_WARM: delta (the Taylor increment, 0 on Gamma) += s (y + b) on free DOFs
             if (col < p.c) {
               const float s = p.scale[0];
               const uint8_t mk = p.mask ? p.mask[vox] : (uint8_t)0;
@@ -237,13 +237,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv(ConvArgs p) {
 #pragma unroll
               for (int e = 0; e < 2; ++e) {
                 const int k = col + e;
-                if (k >= p.c) continue;
+                if (k >= p.c || ((mk >> k) & 1)) continue;
                 const long long gi = (long long)k * p.V + vox;
-                float val = 0.f;
-                if (!((mk >> k) & 1))
-                  val = (float)(p.dt * p.v[gi] + 0.5 * p.dt * p.dt * p.a[gi]) +
-                        s * ((e ? c1 : c0) + p.bias[k]);
-                delta[gi] = val;
+                delta[gi] = delta[gi] + s * ((e ? c1 : c0) + p.bias[k]);
               }
             }
           }
@@ -388,7 +384,16 @@ __global__ void k_warm_scale_fin(const double* part, int n, double cV, float* sc
 // prescribed increment U_n - Taylor on Gamma / s (3), Gamma indicator, rho/rho_bar - 1,
 // normal stiffnesses C_kk / C_bar_kk - 1 (3), shear and off-diagonal normal sums
 // relative to their means - 1.
-__global__ void __launch_bounds__(256) k_warm_features(WarmArgs w, const float* scale, bf16* X) {
+// Taylor part of the warm-start increment, dt v + dt^2/2 a, rounded once to FP32 (the
+// same operations in every kernel that forms it, so the learned and Taylor warm starts
+// agree bit for bit when the network's output is zero).
+__device__ __forceinline__ float taylor_increment(double dt, double v, double a) {
+  return (float)__fma_rn(dt, v, __dmul_rn(__dmul_rn(0.5 * dt, dt), a));
+}
+
+// Network input features and, into delta (when given), the Taylor increment on free DOFs
+// (0 on Gamma), to which the last layer's epilogue adds the scaled network output.
+__global__ void __launch_bounds__(256) k_warm_features(WarmArgs w, const float* scale, bf16* X, float* delta) {
   const float inv = scale[1];
   const double dt = w.dt, h2 = 0.5 * w.dt * w.dt;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < w.V;
@@ -405,6 +410,7 @@ __global__ void __launch_bounds__(256) k_warm_features(WarmArgs w, const float* 
       f[k] = (float)dv * inv;
       f[3 + k] = (float)da * inv;
       if ((mk >> k) & 1) f[6 + k] = (float)(w.Ug[k] - (w.u[gi] + dv + da)) * inv;
+      if (delta) delta[gi] = ((mk >> k) & 1) ? 0.f : taylor_increment(dt, w.v[gi], w.a[gi]);
     }
     f[9] = mk ? 1.f : 0.f;
     const long long row = w.phase ? (long long)w.phase[i] : i;
@@ -441,7 +447,7 @@ __global__ void __launch_bounds__(256) k_warm_taylor(WarmArgs w, float* delta) {
     const int k = (int)(gi / w.V);
     const long long i = gi - (long long)k * w.V;
     const uint8_t mk = w.mask ? w.mask[i] : (uint8_t)0;
-    delta[gi] = ((mk >> k) & 1) ? 0.f : (float)(w.dt * w.v[gi] + 0.5 * w.dt * w.dt * w.a[gi]);
+    delta[gi] = ((mk >> k) & 1) ? 0.f : taylor_increment(w.dt, w.v[gi], w.a[gi]);
   }
 }
 
@@ -567,7 +573,7 @@ void launch_conv(const ConvArgs& p, cudaStream_t st) {
   const long long grid = std::min<long long>(p.ntiles, 2LL * num_sms());
   const int cout_alg = EPI == EPI_WARM || EPI == EPI_LINEAR ? kNetOut : COUT;
   const double fl = 2.0 * 27 * CIN * cout_alg * (double)p.V;
-  const double by = (double)p.V * (2.0 * CIN + (EPI == EPI_WARM ? 4.0 * p.c + 16.0 * p.c : 2.0 * COUT)) +
+  const double by = (double)p.V * (2.0 * CIN + (EPI == EPI_WARM ? 8.0 * p.c : 2.0 * COUT)) +
                     (EPI == EPI_GRAD ? 2.0 * COUT * p.V : 0.0);
   prof_launch(1, KK_NET_CONV, by, fl, st, [&] { k_conv<CIN, COUT, EPI><<<(int)grid, kThreads, sm, st>>>(p); });
 }
@@ -801,15 +807,16 @@ void net_work_free(NetWork* w) {
   *w = NetWork{};
 }
 
-static void warm_scale_features(NetWork* w, const WarmArgs& a, bool features, cudaStream_t st) {
+static void warm_scale_features(NetWork* w, const WarmArgs& a, bool features, cudaStream_t st,
+                                float* delta = nullptr) {
   const int nb = aux_blocks(a.V);
   prof_launch(1, KK_NET_AUX, (double)a.V * (a.c * 24.0 + 1.0), (double)a.V * a.c * 8.0, st,
               [&] { k_warm_scale<<<nb, 256, 0, st>>>(a, w->part); });
   prof_launch(1, KK_NET_AUX, 8.0 * nb, 0.0, st,
               [&] { k_warm_scale_fin<<<1, 256, 0, st>>>(w->part, nb, (double)a.c * a.V, w->scale); });
   if (features)
-    prof_launch(1, KK_NET_AUX, (double)a.V * (a.c * 24.0 + 4.0 + 32.0), (double)a.V * 40.0, st,
-                [&] { k_warm_features<<<nb, 256, 0, st>>>(a, w->scale, w->x); });
+    prof_launch(1, KK_NET_AUX, (double)a.V * (a.c * 28.0 + 4.0 + 32.0), (double)a.V * 40.0, st,
+                [&] { k_warm_features<<<nb, 256, 0, st>>>(a, w->scale, w->x, delta); });
 }
 
 void net_warm(const NetDev* n, NetWork* w, const WarmArgs& a, float* delta, cudaStream_t st) {
@@ -819,7 +826,7 @@ void net_warm(const NetDev* n, NetWork* w, const WarmArgs& a, float* delta, cuda
                 [&] { k_warm_taylor<<<nb, 256, 0, st>>>(a, delta); });
     return;
   }
-  warm_scale_features(w, a, true, st);
+  warm_scale_features(w, a, true, st, delta);
   ConvArgs p = conv_base(a.n1, a.n2, a.n3);
   p.c = a.c;
   p.v = a.v;
