@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
   const double U0 = sc->Ug[0], U1 = sc->Ug[1], U2 = sc->Ug[2];
   const int warm = sc->warm;
   const bool use_au = sc->use_au != 0;
+  const double dU0 = use_au ? sc->dU[0] : 0.0, dU1 = use_au ? sc->dU[1] : 0.0, dU2 = use_au ? sc->dU[2] : 0.0;
   const double* au = reinterpret_cast<const double*>(D.slot[SL_AU]);
   double* r64 = reinterpret_cast<double*>(D.slot[SL_R64]);
   double acc = 0.0, accr = 0.0;
@@ -62,19 +63,24 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
     if (isg) x0 = Uk;
     b[gi] = bv;
     x[gi] = x0;
+    // lifting field w_j enters only where U_j (or its increment) is nonzero: a zero
+    // component's field is not read (the same result: 0 * w_j subtracts nothing)
+    const double w0 = (U0 != 0.0 || dU0 != 0.0) ? w[gi] : 0.0;
+    const double w1 = (nd > 1 && (U1 != 0.0 || dU1 != 0.0)) ? w[tot + gi] : 0.0;
+    const double w2 = (nd > 2 && (U2 != 0.0 || dU2 != 0.0)) ? w[2 * tot + gi] : 0.0;
     if (!isg) {
-      double t = bv - U0 * w[gi];
-      if (nd > 1) t -= U1 * w[tot + gi];
-      if (nd > 2) t -= U2 * w[2 * tot + gi];
+      double t = bv - U0 * w0;
+      if (nd > 1) t -= U1 * w1;
+      if (nd > 2) t -= U2 * w2;
       acc += t * t;
     }
     if (use_au) {
       // x0 = u_{n-1} + sum_j dU_j E e_j, so P(b - A x0) = P(b - A u_{n-1}) - sum_j dU_j w_j,
       // with A u_{n-1} kept from the previous step's last FP64 residual evaluation
       double rv = bv - au[gi];
-      rv -= sc->dU[0] * w[gi];
-      if (nd > 1) rv -= sc->dU[1] * w[tot + gi];
-      if (nd > 2) rv -= sc->dU[2] * w[2 * tot + gi];
+      rv -= dU0 * w0;
+      if (nd > 1) rv -= dU1 * w1;
+      if (nd > 2) rv -= dU2 * w2;
       if (isg) rv = 0.0;
       r64[gi] = rv;
       accr += rv * rv;
