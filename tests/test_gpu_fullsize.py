@@ -14,14 +14,28 @@ from tests.gpu_util import rel, solver_lib, to_dev, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def test_fullsize_polycrystal_steps_satisfy_the_oracle_equation():
+def _random_model(wfft, hidden, seed):
+    """A 4-layer network with a random (not zero) output layer: the warm start is then
+    the Taylor increment plus a network correction, as in the bench's headline mode."""
+    rng = np.random.default_rng(seed)
+    _, params = wfft.blob_params(wfft.model_init(hidden, seed))
+    W4 = 0.5 * rng.standard_normal(params[3][0].shape) / np.sqrt(27 * hidden)
+    params[3] = (W4.astype(np.float32), params[3][1])
+    return wfft.params_blob(hidden, params)
+
+
+@pytest.mark.parametrize("warm", ["prev", "learned"])
+def test_fullsize_polycrystal_steps_satisfy_the_oracle_equation(warm):
     from oracle import newmark, spectral
     from oracle.medium import field_to_oracle
     torch = torch_cuda()
     wfft = solver_lib()
     prob = inputs.config_c3(nsteps=5, n=256)
-    opts = wfft.default_options(precision=wfft.MIXED, tol=1e-10, maxit=500, check_every=4)
+    opts = wfft.default_options(precision=wfft.MIXED, tol=1e-10, maxit=500, check_every=4,
+                                warm_start=wfft.WARM_LEARNED if warm == "learned" else wfft.WARM_PREV)
     s = wfft.Solver.from_problem(prob, options=opts)
+    if warm == "learned":
+        s.set_model(_random_model(wfft, 32, 9))
     s.autotune(3)
     nm = newmark.oracle_from_problem(prob, tol=1e-10)
     checked = []
