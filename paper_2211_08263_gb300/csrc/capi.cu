@@ -1139,7 +1139,15 @@ struct BatchCtx {
   Scalars* const* dsrc = nullptr;  // device: sc64 pointers then sc32 pointers
   Scalars* dgather = nullptr;      // device: gathered copies
   std::vector<BeginJob> hb64, hb32;
+  // CUDA graphs of one block of grouped PCG iterations per precision (captured lazily)
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+  int chunk_iters[2] = {0, 0};
+  long long chunk_launches[2] = {0, 0};
   ~BatchCtx() {
+    for (int k = 0; k < 2; ++k)
+      if (chunk[k]) cudaGraphExecDestroy(chunk[k]);
+    if (cap_st) cudaStreamDestroy(cap_st);
     for (void* p : dev) cudaFree(p);
     if (host) cudaFreeHost(host);
   }
@@ -1286,15 +1294,52 @@ template <typename T>
 int batch_pcg(BatchCtx& B, const BatchLaunch<T>& bl, const Plan<T>& P0, int which, int fa, int fb, int budget,
               int check_every, cudaStream_t st) {
   const int n = (int)B.hs.size();
+  wfft_handle* h0 = B.hs[0];
+  auto block = [&](cudaStream_t s) {
+    for (int i = 0; i < check_every; ++i) {
+      launch_apply<T>(P0, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, s, &bl);
+      launch_fin_batch(B.fin[fa], n, FIN_ALPHA, s);
+      launch_precond<T>(P0, PRE_RUPD, SL_R, SL_Z, 1, s, &bl);
+      launch_fin_batch(B.fin[fb], n, FIN_BETA, s);
+    }
+  };
+  // as for single solves: the block is captured once per context and precision on an
+  // internal stream and replayed (every argument points at device-resident descriptors,
+  // job tables and scalars); not while profiling
+  const bool graphs = h0->opt.use_graphs && !h0->prof.on;
   int launched = 0;
   for (;;) {
-    for (int i = 0; i < check_every; ++i) {
-      launch_apply<T>(P0, PRE_PUPD, SL_P, POST_APPLY, SL_Q, 1, 1, st, &bl);
-      launch_fin_batch(B.fin[fa], n, FIN_ALPHA, st);
-      launch_precond<T>(P0, PRE_RUPD, SL_R, SL_Z, 1, st, &bl);
-      launch_fin_batch(B.fin[fb], n, FIN_BETA, st);
-      ++launched;
+    if (graphs) {
+      if (!B.chunk[which] || B.chunk_iters[which] != check_every) {
+        if (B.chunk[which]) cudaGraphExecDestroy(B.chunk[which]);
+        B.chunk[which] = nullptr;
+        if (!B.cap_st && cudaStreamCreateWithFlags(&B.cap_st, cudaStreamNonBlocking) != cudaSuccess)
+          return WFFT_ECUDA;
+        const long long before = h0->prof.lifetime;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(B.cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WFFT_ECUDA;
+        block(B.cap_st);
+        const cudaError_t ec = cudaStreamEndCapture(B.cap_st, &g);
+        if (ec != cudaSuccess || !g) {
+          if (g) cudaGraphDestroy(g);
+          return WFFT_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&B.chunk[which], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+          B.chunk[which] = nullptr;
+          return WFFT_ECUDA;
+        }
+        B.chunk_iters[which] = check_every;
+        B.chunk_launches[which] = h0->prof.lifetime - before;
+        h0->prof.lifetime = before;
+      }
+      if (cudaGraphLaunch(B.chunk[which], st) != cudaSuccess) return WFFT_ECUDA;
+      h0->prof.lifetime += B.chunk_launches[which];
+    } else {
+      block(st);
     }
+    launched += check_every;
     if (cudaGetLastError() != cudaSuccess) return WFFT_ECUDA;
     if (batch_read(B, st)) return WFFT_ECUDA;
     if (all_done(B, which)) return WFFT_OK;

@@ -76,3 +76,26 @@ def test_mixed_structure_falls_back_to_one_by_one():
     U = np.stack([p2.U[0], p3.U[0]])
     rc, infos = wfft.batch_step(s, U)
     assert rc == wfft.OK and all(i["status"] == wfft.OK for i in infos)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_graph_blocks_match_plain_launches_bitwise(precision):
+    """Grouped PCG blocks replayed as CUDA graphs compute exactly what direct launches do."""
+    torch_cuda()
+    wfft = solver_lib()
+    probs = _problems(9, nsteps=3)
+    states = {}
+    for graphs in (1, 0):
+        hs = [wfft.Solver.from_problem(p, options=wfft.default_options(precision=precision, tol=1e-10,
+                                                                       use_graphs=graphs)) for p in probs]
+        iters = []
+        for k in range(probs[0].nsteps):
+            rc, infos = wfft.batch_step(hs, np.stack([p.U[k] for p in probs]))
+            assert rc == wfft.OK, infos
+            iters.append([i["iters"] for i in infos])
+        states[graphs] = ([h.get_state()[0] for h in hs], iters)
+        for h in hs:
+            h.close()
+    assert states[1][1] == states[0][1]
+    for a, b in zip(states[1][0], states[0][0]):
+        assert np.array_equal(a, b)
