@@ -76,6 +76,25 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_over_ranks(ms, iters, world, device):
+    """Whole-job figures of the replicas: the slowest rank's timed milliseconds (max over
+    ranks) and the Krylov iterations all ranks ran (sum).  device: "cuda" under NCCL,
+    "cpu" under gloo."""
+    if world <= 1:
+        return float(ms), float(iters)
+    import torch
+    mx = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    sm = torch.tensor([float(iters)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx.item()), float(sm.item())
+
+
+def whole_job_value(V, iters, ms):
+    """voxel x Krylov iterations of all ranks per second of the slowest rank."""
+    return V * iters / (ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -504,17 +523,8 @@ def main():
         if m == modes[0]:
             clk = clocks.stop()
     head = results[modes[0]]
-    # max over ranks
-    ms = head["ms_total"]
-    iters = head["iters"]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        it = torch.tensor([float(iters)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(it, op=torch.distributed.ReduceOp.SUM)
-        iters = float(it.item())
-    value = V * iters / (ms * 1e-3)
+    ms, iters = aggregate_over_ranks(head["ms_total"], head["iters"], world, "cuda")
+    value = whole_job_value(V, iters, ms)
     modes_out = {}
     for m, r in results.items():
         modes_out[MODES[m][0]] = {"ms_per_step": r["ms_total"] / K, "s_per_step": r["ms_total"] / K / 1e3,
