@@ -15,9 +15,9 @@ solve, the mixed solve from u_{n-1} and the mixed solve from the Taylor
 extrapolation alone are measured beside it.  Timed with CUDA events on the solver's stream after `--warmup` untimed
 steps; every field is >= 64 MB, so the working set of each pass exceeds L2.
 
-`--impl reference` times the FP64 CPU oracle (the reference implementation
-of this build) on the host cores: one oracle PCG iteration of the same
-256^3 workload per step.
+`--impl reference` times the FP64 CPU oracle (the plain NumPy/SciPy restatement of
+the method that the tests check the GPU path against) on the host cores: one oracle
+PCG iteration of the same 256^3 workload per step.
 """
 from __future__ import annotations
 
