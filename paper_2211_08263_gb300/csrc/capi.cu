@@ -201,6 +201,9 @@ static int build_plan(wfft_handle* h, Plan<T>& P, const std::vector<double>& cta
   // spectral buffer and Krylov vectors in T
   cplx<T>* spec;
   CKH(h, dalloc(h, &spec, (size_t)D.s * D.Vh * sizeof(cplx<T>)));
+  // the pitch padding of the rows is never written by the passes: zero it once, so that
+  // copies of whole rows (wfft_rfft3) carry zeros there
+  CKH(h, cudaMemset(spec, 0, (size_t)D.s * D.Vh * sizeof(cplx<T>)));
   D.spec = spec;
   const size_t vec = (size_t)h->c * h->V;
   for (int sl : {(int)SL_R, (int)SL_Z, (int)SL_P, (int)SL_Q}) {
@@ -1123,7 +1126,7 @@ namespace {
 
 enum FinSlot {
   FJ_REF = 0, FJ_RES0, FJ_RZ0, FJ_ALPHA, FJ_BETA, FJ_OUTER_STORED, FJ_OUTER_RESID, FJ_REACT,
-  FJ_RZ0_32, FJ_ALPHA_32, FJ_BETA_32, FJ_N
+  FJ_RZ0_32, FJ_ALPHA_32, FJ_BETA_32, FJ_DNORM, FJ_OUTER_INCR, FJ_N
 };
 
 struct BatchCtx {
@@ -1138,6 +1141,9 @@ struct BatchCtx {
   Scalars* host = nullptr;  // pinned mirror: [i] = sc64 of instance i, [n + i] = sc32
   Scalars* const* dsrc = nullptr;  // device: sc64 pointers then sc32 pointers
   Scalars* dgather = nullptr;      // device: gathered copies
+  const float* const* q32s = nullptr;  // device: FP32 operator output (SL_Q) of each instance
+  double* rb_dev = nullptr;            // device / pinned host: rounding estimates of an
+  double* rb_host = nullptr;           //   incremental residual, per instance
   std::vector<BeginJob> hb64, hb32;
   // CUDA graphs of one block of grouped PCG iterations per precision (captured lazily)
   cudaStream_t cap_st = nullptr;
@@ -1150,6 +1156,7 @@ struct BatchCtx {
     if (cap_st) cudaStreamDestroy(cap_st);
     for (void* p : dev) cudaFree(p);
     if (host) cudaFreeHost(host);
+    if (rb_host) cudaFreeHost(rb_host);
   }
 };
 BatchCtx* g_batch = nullptr;
@@ -1233,6 +1240,8 @@ int build_batch(std::vector<wfft_handle*>& hs, BatchCtx*& out, std::string& err)
     J(FJ_RZ0_32) = {h->sc32, nullptr, 0, F.part[PT_B], pr32, nullptr, 0, nullptr};
     J(FJ_ALPHA_32) = {h->sc32, F.part[PT_A], bx32, nullptr, 0, nullptr, 0, nullptr};
     J(FJ_BETA_32) = {h->sc32, F.part[PT_A], bx32, F.part[PT_B], pr32, nullptr, 0, nullptr};
+    J(FJ_DNORM) = {h->sc64, nullptr, 0, nullptr, 0, D.part[PT_C], ew, nullptr};
+    J(FJ_OUTER_INCR) = {h->sc64, D.part[PT_A], ew, nullptr, 0, nullptr, 0, h->sc32};
   }
   if (e == cudaSuccess) {
     std::vector<Scalars*> ptrs(2 * n);
@@ -1263,6 +1272,19 @@ int build_batch(std::vector<wfft_handle*>& hs, BatchCtx*& out, std::string& err)
     B->begin32 = B->begin64 + n;
   }
   if (e == cudaSuccess) e = cudaMallocHost(&B->host, 2 * n * sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&B->rb_host, n * sizeof(double));
+  if (e == cudaSuccess) {
+    std::vector<const float*> q(n);
+    for (int i = 0; i < n; ++i) q[i] = reinterpret_cast<const float*>(hs[i]->P32.h.slot[SL_Q]);
+    void* dq = nullptr;
+    e = cudaMalloc(&dq, n * sizeof(const float*) + n * sizeof(double));
+    if (e == cudaSuccess) {
+      B->dev.push_back(dq);
+      e = cudaMemcpy(dq, q.data(), n * sizeof(const float*), cudaMemcpyHostToDevice);
+      B->q32s = reinterpret_cast<const float* const*>(dq);
+      B->rb_dev = reinterpret_cast<double*>(reinterpret_cast<char*>(dq) + n * sizeof(const float*));
+    }
+  }
   if (e != cudaSuccess) {
     err = std::string("batch context: ") + cudaGetErrorString(e);
     delete B;
@@ -1401,10 +1423,12 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
     b.tol2 = h->opt.tol * h->opt.tol;
     b.maxit = h->opt.maxit;
     b.use_au = use_au ? 1 : 0;
+    b.rb = use_au ? h->au_bound : 0.0;
     B.hb32[i] = b;
     B.hb32[i].sc = h->sc32;
     B.hb32[i].tol2 = h->opt.inner_tol * h->opt.inner_tol;
     B.hb32[i].use_au = 0;
+    B.hb32[i].rb = 0.0;
   }
   CKH(h0, cudaEventRecord(h0->ev0, st));
   CKH(h0, cudaMemcpyAsync(B.begin64, B.hb64.data(), n * sizeof(BeginJob), cudaMemcpyHostToDevice, st));
@@ -1416,7 +1440,8 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
   launch_predict(P0, st, &B.bl64);
   launch_fin_batch(B.fin[FJ_REF], n, FIN_REF, st);
   const int watchdog = h0->opt.watchdog_iters > 0 ? h0->opt.watchdog_iters : 4 * h0->opt.maxit;
-  std::vector<int> iters(n, 0), outer(n, 0), sweeps(n, 0);
+  std::vector<int> iters(n, 0), outer(n, 0), sweeps(n, 0), incrs(n, 0);
+  std::vector<double> last_rb(n, 0.0);
   int status_all = WFFT_OK;
   bool last_resid_on_x = false;
   if (!mixed) {
@@ -1433,15 +1458,52 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
     }
   } else {
     bool stored = use_au;
+    bool after_full = false;  // the latest residual was a full FP64 evaluation
     int sweep = 0, total_inner = 0;
     std::vector<char> active(n, 1);
     for (;;) {
+      // incremental residual (as for single solves), taken only when every unfinished
+      // instance's rounding estimate is within a quarter of its target
+      bool incr = false;
+      if (!stored && after_full && h0->opt.incr_resid) {
+        launch_dnorm2(P0, st, &B.bl64);
+        launch_fin_batch(B.fin[FJ_DNORM], n, FIN_DNORM, st);
+        if (cudaGetLastError() != cudaSuccess || batch_read(B, st)) return fail(h0, WFFT_ECUDA, "batch solve failed");
+        incr = true;
+        for (int i = 0; i < n; ++i) {
+          const Scalars& s64 = B.host[i];
+          B.rb_host[i] = 0.0;
+          if (s64.done) continue;
+          const double rb =
+              kIncrC * std::ldexp(1.0, -24) * hs[i]->lam_max * B.host[n + i].xcoef * std::sqrt(s64.dnorm2);
+          B.rb_host[i] = rb;
+          if (!(hs[i]->lam_max > 0) || !std::isfinite(rb) || !(rb <= 0.25 * std::sqrt(s64.tol2 * s64.ref2)))
+            incr = false;
+        }
+      }
       if (stored) {
         launch_fin_batch(B.fin[FJ_OUTER_STORED], n, FIN_OUTER, st);
+        after_full = false;
+      } else if (incr) {
+        CKH(h0, cudaMemcpyAsync(B.rb_dev, B.rb_host, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        launch_incr_begin_batch(B.dsrc, n, B.rb_dev, st);
+        launch_apply<float>(F0, PRE_PLAIN, SL_D, POST_APPLY, SL_Q, 0, 0, st, &B.bl32);
+        launch_resid_incr(P0, nullptr, 1, st, &B.bl64, B.q32s);
+        launch_fin_batch(B.fin[FJ_OUTER_INCR], n, FIN_OUTER, st);
+        for (int i = 0; i < n; ++i)
+          if (active[i]) {
+            ++incrs[i];
+            last_rb[i] = B.rb_host[i];
+          }
+        after_full = false;
       } else {
         launch_apply<double>(P0, sweep > 0 ? PRE_XUPD : PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, st, &B.bl64);
         launch_fin_batch(B.fin[FJ_OUTER_RESID], n, FIN_OUTER, st);
-        for (int i = 0; i < n; ++i) outer[i] += active[i];
+        for (int i = 0; i < n; ++i) {
+          outer[i] += active[i];
+          if (active[i]) last_rb[i] = 0.0;
+        }
+        after_full = true;
       }
       last_resid_on_x = !stored;
       stored = false;
@@ -1501,7 +1563,7 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
       for (int k = 0; k < 3; ++k) h->U_prev[k] = B.hb64[i].U[k];
     }
     h->au_valid = st_i == WFFT_OK && mixed && last_resid_on_x && !s64.zero_free;
-    h->au_bound = 0.0;
+    h->au_bound = last_rb[i];
     if (infos) {
       wfft_step_info& in = infos[i];
       memset(&in, 0, sizeof(in));
@@ -1509,6 +1571,7 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
       in.iters = iters[i];
       in.outer_applies = outer[i];
       in.sweeps = sweeps[i];
+      in.incr_resids = incrs[i];
       in.ref = std::sqrt(s64.ref2);
       in.rel_res = s64.ref2 > 0 ? std::sqrt(s64.rr / s64.ref2) : 0.0;
       for (int k = 0; k < 3; ++k) in.reaction[k] = st_i == WFFT_OK ? s64.react[k] : 0.0;

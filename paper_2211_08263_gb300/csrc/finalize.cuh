@@ -26,6 +26,7 @@ struct BeginJob {
   Scalars* sc;
   double U[3];
   double dU[3];
+  double rb;  // rounding estimate carried by the stored A u (incremental last residual)
   int warm;
   double tol2;
   int maxit;
@@ -53,8 +54,13 @@ int ew_block_count(const Plan<double>& P);
 //   launch_resid_incr: with q32 = A d in FP32 and xc = ||r|| of the sweep's start,
 //     x += xc d, A x += xc q32 (SL_AU), r = [P](b - A x) (SL_R64), partial sums of
 //     ||r||^2 into PT_A (ew_block_count(P) blocks).
-void launch_dnorm2(const Plan<double>& P, cudaStream_t st);
+//   Grouped forms: the BatchLaunch of the instances (their elementwise geometry),
+//   q32s[i] the FP32 product of instance i, launch_incr_begin_batch over the sc64 / sc32
+//   pointer table with per-instance estimates rb[i] (finished instances untouched).
+void launch_dnorm2(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl = nullptr);
 void launch_incr_begin(Scalars* sc64, Scalars* sc32, double rb, cudaStream_t st);
-void launch_resid_incr(const Plan<double>& P, const float* q32, int masked, cudaStream_t st);
+void launch_incr_begin_batch(Scalars* const* src, int n, const double* rb, cudaStream_t st);
+void launch_resid_incr(const Plan<double>& P, const float* q32, int masked, cudaStream_t st,
+                       const BatchLaunch<double>* bl = nullptr, const float* const* q32s = nullptr);
 
 }  // namespace wfft

@@ -380,17 +380,20 @@ void launch_explicit_update(const Plan<double>& P, const double Udot[3], cudaStr
 // incremental residual of a mixed solve
 // ---------------------------------------------------------------------------
 // Partial sums of ||d||^2 over the FP32 correction: FP32 squares summed in FP32 per
-// thread (a relative error far below the 1 % the rounding bound needs), FP64 across.
-__global__ void __launch_bounds__(256) k_dnorm2(const Desc<double>* __restrict__ dd) {
-  const Desc<double>& D = *dd;
+// thread (a relative error far below the 1 % the rounding estimate needs), FP64 across.
+// BatchArgs as for the predictor (n = 0: one instance).
+__global__ void __launch_bounds__(256) k_dnorm2(const Desc<double>* __restrict__ dd, BatchArgs<double> ba) {
+  int blk;
+  const Desc<double>* __restrict__ Dp = pick_ptr<double, 1>(dd, ba, blk);
+  const Desc<double>& D = *Dp;
   const int nblk = ew_blocks_dev(D);
   const float* d = reinterpret_cast<const float*>(D.slot[SL_D]);
   const long long tot = (long long)D.c * D.V;
   float acc = 0.f;
-  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x)
+  for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x)
     acc = fmaf(d[gi], d[gi], acc);
   const double s = block_sum((double)acc);
-  if (threadIdx.x == 0) D.part[PT_C][blockIdx.x] = s;
+  if (threadIdx.x == 0) D.part[PT_C][blk] = s;
 }
 
 __global__ void k_incr_begin(Scalars* sc64, Scalars* sc32, double rb) {
@@ -400,12 +403,37 @@ __global__ void k_incr_begin(Scalars* sc64, Scalars* sc32, double rb) {
   sc32->status = 0;
 }
 
+// Grouped form: src = sc64 pointers then sc32 pointers of n instances; unfinished
+// instances get their rounding estimate rb[i] and their FP32 scalars re-opened.
+__global__ void k_incr_begin_batch(Scalars* const* src, int n, const double* rb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || src[i]->done) return;
+  src[i]->rbound = rb[i];
+  src[n + i]->done = 0;
+  src[n + i]->status = 0;
+}
+
 // x += xc d, A x += xc q32, r = [P](b - A x): the residual of x + xc d from the stored
 // FP64 product A x and the FP32 product of the correction (the same fold of d into x
-// as the x pass of a full FP64 residual evaluation).
-__global__ void __launch_bounds__(256) k_resid_incr(const Desc<double>* __restrict__ dd, const float* __restrict__ q32,
+// as the x pass of a full FP64 residual evaluation).  q32s[i]: instance i's FP32
+// product (grouped launches); q32: the single instance's.
+__global__ void __launch_bounds__(256) k_resid_incr(const Desc<double>* __restrict__ dd, BatchArgs<double> ba,
+                                                    const float* __restrict__ q32, const float* const* q32s,
                                                     int masked) {
-  const Desc<double>& D = *dd;
+  int blk = blockIdx.x;
+  const Desc<double>* Dp = dd;
+  if (ba.n > 0) {  // instance index by binary search over the block prefix sums (as pick_ptr)
+    int lo = 0, hi = ba.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(ba.start + mid) <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    blk = blockIdx.x - __ldg(ba.start + lo);
+    Dp = ba.descs[lo];
+    q32 = q32s[lo];
+  }
+  const Desc<double>& D = *Dp;
   if (D.sc->done) return;
   const int nblk = ew_blocks_dev(D);
   const double xc = D.sc_inner->xcoef;
@@ -417,7 +445,7 @@ __global__ void __launch_bounds__(256) k_resid_incr(const Desc<double>* __restri
   double* r = reinterpret_cast<double*>(D.slot[SL_R64]);
   double acc = 0.0;
   const long long tot = (long long)D.c * V;
-  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
+  for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
     const int k = (int)(gi / V);
     const long long vox = gi - (long long)k * V;
     x[gi] = x[gi] + xc * (double)d[gi];
@@ -429,20 +457,28 @@ __global__ void __launch_bounds__(256) k_resid_incr(const Desc<double>* __restri
     acc = fma(rv, rv, acc);
   }
   const double s = block_sum(acc);
-  if (threadIdx.x == 0) D.part[PT_A][blockIdx.x] = s;
+  if (threadIdx.x == 0) D.part[PT_A][blk] = s;
 }
 
-void launch_dnorm2(const Plan<double>& P, cudaStream_t st) {
-  const double cv = (double)P.h.c * P.h.V;
-  prof_launch(0, KK_NEWMARK, 4.0 * cv, 2.0 * cv, st, [&] { k_dnorm2<<<ew_blocks(P), 256, 0, st>>>(P.d); });
+void launch_dnorm2(const Plan<double>& P, cudaStream_t st, const BatchLaunch<double>* bl) {
+  const double cv = ew_cv(P, bl);
+  const int nb = bl ? bl->total[GEO_EW] : ew_blocks(P);
+  const BatchArgs<double> ba = ew_args(bl);
+  prof_launch(0, KK_NEWMARK, 4.0 * cv, 2.0 * cv, st, [&] { k_dnorm2<<<nb, 256, 0, st>>>(P.d, ba); });
 }
 void launch_incr_begin(Scalars* sc64, Scalars* sc32, double rb, cudaStream_t st) {
   prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_incr_begin<<<1, 32, 0, st>>>(sc64, sc32, rb); });
 }
-void launch_resid_incr(const Plan<double>& P, const float* q32, int masked, cudaStream_t st) {
-  const double cv = (double)P.h.c * P.h.V;
-  prof_launch(0, KK_NEWMARK, cv * (8 * 6 + 4 * 2) + P.h.V, cv * 6, st,
-              [&] { k_resid_incr<<<ew_blocks(P), 256, 0, st>>>(P.d, q32, masked); });
+void launch_incr_begin_batch(Scalars* const* src, int n, const double* rb, cudaStream_t st) {
+  prof_launch(0, KK_SCALAR, 0.0, 0.0, st, [&] { k_incr_begin_batch<<<(n + 63) / 64, 64, 0, st>>>(src, n, rb); });
+}
+void launch_resid_incr(const Plan<double>& P, const float* q32, int masked, cudaStream_t st,
+                       const BatchLaunch<double>* bl, const float* const* q32s) {
+  const double cv = ew_cv(P, bl);
+  const int nb = bl ? bl->total[GEO_EW] : ew_blocks(P);
+  const BatchArgs<double> ba = ew_args(bl);
+  prof_launch(0, KK_NEWMARK, cv * (8 * 6 + 4 * 2) + cv / P.h.c, cv * 6, st,
+              [&] { k_resid_incr<<<nb, 256, 0, st>>>(P.d, ba, q32, q32s, masked); });
 }
 
 // ---------------------------------------------------------------------------
@@ -631,7 +667,7 @@ __global__ void k_begin_batch(const BeginJob* jobs, int n) {
   sc->tol2 = j.tol2;
   sc->tol2_base = j.tol2;
   sc->floor_fac = 0.0;
-  sc->rbound = 0.0;
+  sc->rbound = j.rb;
   sc->dnorm2 = 0.0;
   sc->maxit = j.maxit;
   sc->done = 0;

@@ -32,6 +32,7 @@ def test_batched_steps_match_single_steps_and_oracle(precision, tol, bar):
     opt = lambda: wfft.default_options(precision=precision, tol=tol)
     grouped = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
     single = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
+    n_incr = 0
     for k in range(probs[0].nsteps):
         U = np.stack([p.U[k] for p in probs])
         rc, infos = wfft.batch_step(grouped, U)
@@ -40,6 +41,9 @@ def test_batched_steps_match_single_steps_and_oracle(precision, tol, bar):
             s.step(p.U[k])
         for inf in infos:
             assert inf["status"] == wfft.OK and inf["rel_res"] <= tol * 1.0001
+            n_incr += inf["incr_resids"]
+    if precision == 0:
+        assert n_incr == 0
     for g, s, p in zip(grouped, single, probs):
         ug, vg, ag, ng = g.get_state()
         us, vs, as_, ns = s.get_state()
@@ -99,3 +103,34 @@ def test_batched_graph_blocks_match_plain_launches_bitwise(precision):
     assert states[1][1] == states[0][1]
     for a, b in zip(states[1][0], states[0][0]):
         assert np.array_equal(a, b)
+
+
+def test_batched_mixed_steps_take_the_incremental_residual():
+    """Polycrystal pulses of uneven sizes: the grouped mixed solve replaces its last FP64
+    residual by the incremental one when every instance's rounding estimate allows it,
+    and the grouped states equal the single solves' within the solver tolerance."""
+    torch_cuda()
+    wfft = solver_lib()
+    probs = []
+    for n, seed in (((24, 24, 24), 31), ((32, 24, 20), 32), ((20, 28, 24), 33)):
+        ids, Cv, rho = inputs.polycrystal(n, 12, seed)
+        dt = 2e-7
+        U = inputs._U_series(6, dt, lambda t: inputs.gaussian_pulse(t, 1e-6, 5 * dt, 15 * dt))
+        probs.append(inputs.Problem(f"pulse{n}", 3, n, (1e-3,) * 3, dt, 0.25, 0.5, Cv, rho, ids,
+                                    inputs.slab_mask(3, n, 4), U, tol=1e-10))
+    opt = lambda: wfft.default_options(precision=wfft.MIXED, tol=1e-10)
+    grouped = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
+    single = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
+    n_incr, outer = 0, 0
+    for k in range(probs[0].nsteps):
+        rc, infos = wfft.batch_step(grouped, np.stack([p.U[k] for p in probs]))
+        assert rc == wfft.OK, infos
+        for s, p in zip(single, probs):
+            s.step(p.U[k])
+        n_incr += sum(i["incr_resids"] for i in infos)
+        outer += sum(i["outer_applies"] for i in infos)
+        assert all(i["rel_res"] <= 1e-10 for i in infos)
+    print(n_incr, outer)
+    assert n_incr > 0
+    for g, s in zip(grouped, single):
+        assert rel(g.get_state()[0], s.get_state()[0]) < 1e-8
