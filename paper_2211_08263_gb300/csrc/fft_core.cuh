@@ -274,12 +274,15 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
 // keeps each stage's registers apart.  ES = 1: row tiles with line stride
 // `lstride` (nlines at run time), NL = 0; NL > 0: column tiles (line stride 1,
 // element stride ES, NL lines).  Must be called by every thread of the block (barriers).
-template <typename T, int ES, int NL = 0>
+// ONLY16: the caller guarantees a pure radix-16 schedule, and the other stage kinds are
+// not compiled in (a smaller instruction footprint for kernels with several FFT calls).
+template <typename T, int ES, int NL = 0, bool ONLY16 = false>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int nlines, int lstride, const cplx<T>* tw,
                                           int sgn) {
   const int N = pl.n;
   int Ns = 1;
   for (int s = 0; s < pl.cnt[6]; ++s, Ns *= 16) fft_stage<T, 16, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
+  if constexpr (ONLY16) return;
   for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[1]; ++s, Ns *= 4) fft_stage<T, 4, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   for (int s = 0; s < pl.cnt[2]; ++s, Ns *= 2) fft_stage<T, 2, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);

@@ -692,7 +692,8 @@ __global__ void __launch_bounds__(kColThreadsPlain, sizeof(T) == 8 ? 2 : 4)
 //   OP_DIV : s stresses sig^ -> c tractions t^ = (-theta/V) i B(xi)^T sig^
 //   OP_PREC: c residuals r^ -> z^ = (1/V) (theta K(xi) + rho_bar I)^-1 r^, with the
 //            Parseval partial sum of (r, z) over the half spectrum
-template <typename T, int OP, int BX, int NS, int BATCH>
+// R16: the axis' schedule is pure radix 16 (only that stage kind is compiled in).
+template <typename T, int OP, int BX, int NS, int BATCH, bool R16 = false>
 __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 4)
     k_colop(const Desc<T>* __restrict__ dd, BatchArgs<T> ba, int axis) {
   constexpr int ES = col_es(NS, BX, (int)sizeof(T));
@@ -720,10 +721,10 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 4)
   col_load_all<T, BX, ES, NIN>(D, g, tl);
   __syncthreads();
   if (kSplit && NIN == 6) {
-    fft_lines<T, ES, 3 * BX>(tl, pl, 3 * BX, 1, tw, -1);
-    fft_lines<T, ES, 3 * BX>(tl + 3 * BX, pl, 3 * BX, 1, tw, -1);
+    fft_lines<T, ES, 3 * BX, R16>(tl, pl, 3 * BX, 1, tw, -1);
+    fft_lines<T, ES, 3 * BX, R16>(tl + 3 * BX, pl, 3 * BX, 1, tw, -1);
   } else {
-    fft_lines<T, ES, NIN * BX>(tl, pl, NIN * BX, 1, tw, -1);
+    fft_lines<T, ES, NIN * BX, R16>(tl, pl, NIN * BX, 1, tw, -1);
   }
   DotAcc<T> acc;
   for (int e = threadIdx.x; e < N * BX; e += blockDim.x) {
@@ -818,10 +819,10 @@ __global__ void __launch_bounds__(kColThreadsOp, sizeof(T) == 8 ? 2 : 4)
   }
   __syncthreads();
   if (kSplit && NOUT == 6) {
-    fft_lines<T, ES, 3 * BX>(tl, pl, 3 * BX, 1, tw, +1);
-    fft_lines<T, ES, 3 * BX>(tl + 3 * BX, pl, 3 * BX, 1, tw, +1);
+    fft_lines<T, ES, 3 * BX, R16>(tl, pl, 3 * BX, 1, tw, +1);
+    fft_lines<T, ES, 3 * BX, R16>(tl + 3 * BX, pl, 3 * BX, 1, tw, +1);
   } else {
-    fft_lines<T, ES, NOUT * BX>(tl, pl, NOUT * BX, 1, tw, +1);
+    fft_lines<T, ES, NOUT * BX, R16>(tl, pl, NOUT * BX, 1, tw, +1);
   }
   for (int k = 0; k < NOUT; ++k) col_store<T, BX, ES>(D, g, k, tl, k);
 }

@@ -313,11 +313,22 @@ static void launch_colop_bx(const Launch<T, B>& L, int axis, cudaStream_t st) {
   // slots: c (2 or 3) for the preconditioner, s (3 or 6) for gradient / divergence
   constexpr int kSmall = OP == OP_PREC ? 2 : 3;
   constexpr int kLarge = OP == OP_PREC ? 3 : 6;
+  // 3-D single-instance FP32 passes over a pure radix-16 axis: the variant without the
+  // other stage kinds
+  const AxisPlan& ap = L.P.h.ax[axis];
+  const bool only16 = ap.cnt[6] > 0 && !ap.cnt[0] && !ap.cnt[1] && !ap.cnt[2] && !ap.cnt[3] && !ap.cnt[4] &&
+                      !ap.cnt[5];
   prof_launch(prec_index(sizeof(T)), kind, by, fl, st, [&] {
     if (!d3)
       k_colop<T, OP, BX, kSmall, B><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);
-    else
+    else if constexpr (B == 0 && sizeof(T) == 4) {
+      if (only16)
+        k_colop<T, OP, BX, kLarge, B, true><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);
+      else
+        k_colop<T, OP, BX, kLarge, B><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);
+    } else {
       k_colop<T, OP, BX, kLarge, B><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);
+    }
   });
 }
 
@@ -572,6 +583,15 @@ cudaError_t init_kernel_attributes_impl() {
   WFFT_SETATTR_BX(1)
   WFFT_SETATTR_BX(2)
   WFFT_SETATTR_BX(4)
+  if constexpr (B == 0 && sizeof(T) == 4) {
+#define WFFT_SETATTR_R16(BXV)                             \
+  WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 6, B, true>)); \
+  WFFT_SETATTR((k_colop<T, OP_DIV, BXV, 6, B, true>));  \
+  WFFT_SETATTR((k_colop<T, OP_PREC, BXV, 3, B, true>));
+    WFFT_SETATTR_R16(1)
+    WFFT_SETATTR_R16(2)
+    WFFT_SETATTR_R16(4)
+  }
   WFFT_SETATTR((k_colplain<T, OP_FWD, 1, B>));
   WFFT_SETATTR((k_colplain<T, OP_INV, 1, B>));
   WFFT_SETATTR((k_colplain<T, OP_FWD, 2, B>));
