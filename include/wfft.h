@@ -52,7 +52,7 @@ extern "C" {
 #define WFFT_ENOTCONV 4      /* Krylov solve hit maxit; the step is not committed, state unchanged */
 #define WFFT_ENUMERIC 5      /* NaN/Inf or a non-positive curvature p.Ap in the solve; step not committed */
 #define WFFT_ETIMEOUT 6      /* iteration watchdog fired; step not committed */
-#define WFFT_EUNSUPPORTED 7  /* axis length with a prime factor > 7, or > 512, or N2 = 1 */
+#define WFFT_EUNSUPPORTED 7  /* axis with a prime factor > 7 or too long for the tiles, or N2 = N3 = 1 */
 
 /* arithmetic of the Krylov solve */
 #define WFFT_FP64 0   /* everything FP64 */

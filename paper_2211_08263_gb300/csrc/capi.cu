@@ -165,7 +165,8 @@ static int build_plan(wfft_handle* h, Plan<T>& P, const std::vector<double>& cta
   for (int a = 0; a < 6; ++a)
     for (int b = 0; b < 6; ++b) D.kq[a][b] = (T)kq[a][b];
   for (int ax = 0; ax < 3; ++ax) {
-    if (!factorize(h->n[ax], D.ax[ax])) return fail(h, WFFT_EUNSUPPORTED, "axis length not supported");
+    if (!initial_schedule(h->n[ax], D.ax[ax], [](const AxisPlan& c) { return axis_tile_capacity<T>(c); }))
+      return fail(h, WFFT_EUNSUPPORTED, "axis length not supported");
     // per-stage twiddles of the axis' radix schedule (rewritten by upload_desc when the
     // schedule changes)
     cplx<T>* dtw;
@@ -198,6 +199,8 @@ static int build_plan(wfft_handle* h, Plan<T>& P, const std::vector<double>& cta
   D.beta = h->beta;
   D.gamma = h->gamma;
   plan_geometry<T>(P);
+  if (!P.g.fits)
+    return fail(h, WFFT_EUNSUPPORTED, "an axis is too long for the passes' tiles (register batch or shared memory)");
   // spectral buffer and Krylov vectors in T
   cplx<T>* spec;
   CKH(h, dalloc(h, &spec, (size_t)D.s * D.Vh * sizeof(cplx<T>)));
@@ -287,7 +290,7 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   for (int i = 0; i < 3; ++i) {
     AxisPlan pl;
     if (!factorize(grid->n[i], pl))
-      return fail(nullptr, WFFT_EUNSUPPORTED, "axis lengths must be <= 512 with prime factors 2, 3, 5, 7");
+      return fail(nullptr, WFFT_EUNSUPPORTED, "axis lengths must have prime factors 2, 3, 5, 7 only");
   }
   wfft_handle* h = new (std::nothrow) wfft_handle();
   if (!h) return fail(nullptr, WFFT_ENOMEM, "host allocation failed");
@@ -1095,6 +1098,8 @@ extern "C" int wfft_precond(wfft_handle* h, int precision, const void* r_dev, vo
 template <typename T>
 static int rfft3_impl(wfft_handle* h, Plan<T>& P, Scalars* sc, int dir, int ncomp, const void* in, void* out) {
   const size_t sbytes = (size_t)ncomp * P.h.Vh * sizeof(cplx<T>);
+  if (!rfft3_fits<T>(P, ncomp))
+    return fail(h, WFFT_EUNSUPPORTED, "this many components on this x axis do not fit the transform's tiles");
   launch_set_done(sc, 0, h->st);
   if (dir < 0) {
     CKH(h, set_ext(P, in, out, h->st));
@@ -1686,7 +1691,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
       for (const AxisPlan& c : cands) {
         D.ax[a] = c;
         plan_geometry<T>(P);
-        if (P.g.max_blocks > h->nparts) continue;  // partial-sum arrays are sized at creation
+        if (!P.g.fits || P.g.max_blocks > h->nparts) continue;  // partial-sum arrays are sized at creation
         CKH(h, upload_desc(P));
         const float t = time_iteration<T>(h, P, reps);
         if (t < tbest) {
@@ -1707,7 +1712,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
       for (int xe : {1024, 2048, 4096}) {
         P.g.xelems = xe;
         plan_geometry<T>(P);
-        if (P.g.max_blocks > h->nparts) continue;
+        if (!P.g.fits || P.g.max_blocks > h->nparts) continue;
         CKH(h, upload_desc(P));
         const float t = time_iteration<T>(h, P, reps);
         if (t < tbest) {
@@ -1747,7 +1752,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
     for (int a = 0; a < 3; ++a) D.ax[a] = best.ax[a];
     P.g.xelems = best.xelems;
     plan_geometry<T>(P);
-    if (P.g.max_blocks > h->nparts) {
+    if (!P.g.fits || P.g.max_blocks > h->nparts) {
       for (int a = 0; a < 3; ++a) D.ax[a] = before.ax[a];
       P.g.xelems = before.xelems;
       plan_geometry<T>(P);
@@ -1869,10 +1874,12 @@ int set_radix_plan(wfft_handle* h, Plan<T>& P, int axis, const AxisPlan& pl) {
   const AxisPlan old = D.ax[axis];
   D.ax[axis] = pl;
   plan_geometry<T>(P);
-  if (P.g.max_blocks > h->nparts) {
+  if (!P.g.fits || P.g.max_blocks > h->nparts) {
+    const bool fits = P.g.fits;
     D.ax[axis] = old;
     plan_geometry<T>(P);
-    return fail(h, WFFT_EINVAL, "this decomposition needs more partial-sum slots than the handle has");
+    return fail(h, WFFT_EINVAL, fits ? "this decomposition needs more partial-sum slots than the handle has"
+                                     : "this decomposition's stages do not fit the passes' tiles");
   }
   CKH(h, cudaStreamSynchronize(h->st));
   CKH(h, upload_desc(P));
@@ -2079,6 +2086,11 @@ int set_plan(wfft_handle* h, Plan<T>& P, const wfft_plan_choice* in) {
   for (int a = 0; a < 3; ++a) D.ax[a] = ax[a];
   P.g.xelems = in->xelems;
   plan_geometry<T>(P);
+  if (!P.g.fits) {
+    D = saved;
+    P.g = gsaved;
+    return fail(h, WFFT_EINVAL, "this plan's stages do not fit the passes' tiles");
+  }
   for (int a = 1; a <= 2; ++a)
     for (int op = 0; op < 5; ++op) {
       if (!ops_of_axis(D, a, op)) continue;

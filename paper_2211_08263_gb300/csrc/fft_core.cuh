@@ -15,12 +15,14 @@
 
 namespace wfft {
 
-// Butterflies a thread holds per stage for radix R: at most 16 complex values
-// in FP32 and 8 in FP64 (register budget).  The host sizes every tile so that
-// ceil(elements / R) <= NbOf * threads for each radix of the plan.
+// Butterflies a thread holds per stage for radix R: up to 16 complex values (14 and 15
+// for radices 7, 3 and 5) in both precisions.  A stage transforms at most NbOf * threads
+// butterflies, so the host accepts only plans whose every tile satisfies
+// ceil(elements / R) <= NbOf * threads for each radix of its axis; with 256 threads a
+// tile of three line pairs holds axes of up to 1194-1365 points.  Iterations past a
+// tile's butterflies are predicated off, so small tiles pay only their index arithmetic.
 template <typename T, int R> struct NbOf {
-  static constexpr int cap = sizeof(T) == 8 ? 8 : 16;
-  static constexpr int v = (cap / R) > 0 ? cap / R : 1;
+  static constexpr int v = (16 / R) > 0 ? 16 / R : 1;
 };
 
 // Radix-5 constants: cos(2 pi/5) = (sqrt5 - 1)/4, cos(4 pi/5) = -(sqrt5 + 1)/4,

@@ -10,12 +10,17 @@
 
 namespace wfft {
 
+// Longest axis a radix schedule is made for.  Whether an axis is supported is decided
+// by the tiles of the passes (every stage's register batch and the shared memory):
+// up to 1365 points in FP32 and 597-1365 in FP64, depending on the radices.
+constexpr int kMaxAxis = 2048;
+
 // radix schedule: as many 8s as possible, the rest of the power of two as 4s / a 2
 // (4*4 rather than 8*2), then the odd radices 3, 5, 7
 static inline bool factorize(int n, AxisPlan& pl) {
   pl.n = n;
   for (int i = 0; i < 7; ++i) pl.cnt[i] = 0;
-  if (n < 1 || n > 512) return false;
+  if (n < 1 || n > kMaxAxis) return false;
   int m = n, e2 = 0;
   while (m % 2 == 0) {
     m /= 2;
@@ -58,6 +63,19 @@ static inline std::vector<AxisPlan> factor_candidates(int n, bool allow16) {
         out.push_back(c);
       }
   return out;
+}
+
+// Radix schedule of an axis at plan creation: the built-in one (factorize), unless a
+// tile of three line pairs or three slots (3 n elements) would exceed what its stages
+// hold per block (cap(schedule), the register batch of each radix x 256 threads); a
+// long axis then takes the decomposition whose stages hold the most.
+template <typename Cap>
+static inline bool initial_schedule(int n, AxisPlan& pl, Cap cap) {
+  if (!factorize(n, pl)) return false;
+  if (cap(pl) < 3 * n)
+    for (const AxisPlan& c : factor_candidates(n, true))
+      if (cap(c) > cap(pl)) pl = c;
+  return true;
 }
 
 // W_n^m = exp(-2 pi i m / n), m = 0..n-1, evaluated in long double on the host

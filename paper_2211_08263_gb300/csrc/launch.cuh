@@ -19,6 +19,7 @@ struct PassGeo {
   size_t sm_col[3][5];  // [axis][op] dynamic shared memory
   int max_blocks;
   int xelems = 0;       // complex elements per x-pass tile (0: the default 2048; capped by the register batch)
+  bool fits = true;     // every tile within its stages' register batch and the opt-in shared memory
 };
 
 template <typename T>
@@ -101,6 +102,11 @@ size_t geo_smem(const Plan<T>& P, int cls, int bx);
 // a real slot and the spectral buffer (testing entry point).
 template <typename T>
 void launch_rfft3(const Plan<T>& P, int dir, int ncomp, int real_slot, cudaStream_t st);
+template <typename T>
+bool rfft3_fits(const Plan<T>& P, int ncomp);
+// Complex elements one tile of 256 threads may hold under the radix schedule pl.
+template <typename T>
+int axis_tile_capacity(const AxisPlan& pl);
 
 // Set the max dynamic shared memory attribute of every kernel (once per process).
 template <typename T, int B>

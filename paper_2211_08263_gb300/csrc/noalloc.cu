@@ -78,8 +78,8 @@ extern "C" int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21]
   D.n2 = grid->n[1];
   D.n3 = grid->n[2];
   for (int ax = 0; ax < 3; ++ax)
-    if (!factorize(grid->n[ax], D.ax[ax]))
-      return na_fail(WFFT_EUNSUPPORTED, "axis lengths must be <= 512 with prime factors 2, 3, 5, 7");
+    if (!initial_schedule(grid->n[ax], D.ax[ax], [](const AxisPlan& c) { return axis_tile_capacity<double>(c); }))
+      return na_fail(WFFT_EUNSUPPORTED, "axis lengths must have prime factors 2, 3, 5, 7 only");
   D.nh = D.n1 / 2 + 1;
   D.pitch = ((D.nh + 7) / 8) * 8;
   D.opAxis = D.n3 > 1 ? 2 : 1;
@@ -91,6 +91,8 @@ extern "C" int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21]
     return na_fail(WFFT_EINVAL, "grid too large for the allocation-free scratch (c*N3*N2*pitch complex "
                                 "doubles must fit 16 MiB, e.g. 64^3)");
   plan_geometry<double>(P);
+  if (!P.g.fits)
+    return na_fail(WFFT_EUNSUPPORTED, "an axis is too long for the passes' tiles (register batch or shared memory)");
   // scratch layout: descriptor | scalars | 3 twiddle tables | partial sums | spectral buffer
   const size_t off_sc = align256(sizeof(Desc<double>));
   const size_t off_tw = off_sc + align256(sizeof(Scalars));
@@ -133,7 +135,7 @@ extern "C" int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21]
   precond_coeffs(cbar, theta, kq);
   for (int a = 0; a < 6; ++a)
     for (int b = 0; b < 6; ++b) D.kq[a][b] = kq[a][b];
-  double2 tw[512];
+  double2 tw[kMaxAxis];
   size_t off = off_tw;
   for (int ax = 0; ax < 3; ++ax) {
     fill_stage_twiddles<double>(tw, D.ax[ax]);

@@ -15,15 +15,35 @@ namespace wfft {
 template <typename T>
 static int max_tile_elems(const AxisPlan& pl, int thr) {
   int cap = 1 << 30;
-  const int rad[7] = {8, 4, 2, 3, 5, 7, 16};
-  for (int i = 0; i < 7; ++i) {
-    if (!pl.cnt[i]) continue;
-    const int R = rad[i];
-    const int capR = sizeof(T) == 8 ? 8 : 16;
-    const int nb = std::max(1, capR / R);
-    cap = std::min(cap, nb * R * thr);
-  }
+  // elements per thread of one stage, radix order 8, 4, 2, 3, 5, 7, 16 (the stage's own rule)
+  const int per[7] = {8 * NbOf<T, 8>::v, 4 * NbOf<T, 4>::v, 2 * NbOf<T, 2>::v, 3 * NbOf<T, 3>::v,
+                      5 * NbOf<T, 5>::v, 7 * NbOf<T, 7>::v, 16 * NbOf<T, 16>::v};
+  for (int i = 0; i < 7; ++i)
+    if (pl.cnt[i]) cap = std::min(cap, per[i] * thr);
   return cap;
+}
+
+// Dynamic shared memory a pass may request (the kernels' opt-in attribute).
+constexpr size_t kMaxDynSmem = 200 * 1024;
+
+// x lines per block of an x pass over nc components with at most `ex` complex
+// elements per tile: lines are transformed in pairs (two real lines as one complex
+// line), so lx * nc is even; a single line of an odd nc takes two lines (nc pairs).
+static inline int x_tile_lines(int n1, long long nsp, int ex, int nc) {
+  int lx = std::max(1, (2 * ex) / (nc * n1));
+  if (lx > nsp) lx = (int)std::max<long long>(1, nsp);
+  while (lx > 1 && ((lx * nc) & 1)) --lx;
+  if ((lx * nc) & 1) lx = 2;
+  return lx;
+}
+
+// Whether an x pass over nc components fits: its tile of lx * nc / 2 line pairs within
+// the register batch of every stage, and its shared memory within the opt-in limit.
+template <typename T>
+static bool x_tile_fits(const Desc<T>& D, int thr, int lx, int nc) {
+  const long long elems = (long long)(lx * nc / 2) * D.n1;
+  const size_t sm = (size_t)(D.n1 + (lx * nc / 2) * row_stride(D.n1)) * sizeof(cplx<T>);
+  return elems <= max_tile_elems<T>(D.ax[0], thr) && sm <= kMaxDynSmem;
 }
 
 // Slots transformed by one batched FFT call of a column pass: the 3-D gradient and
@@ -41,15 +61,9 @@ void plan_geometry(Plan<T>& P) {
   const long long nsp = (long long)D.n2 * D.n3;
   // x passes: npairs * N1 <= elems, LX * nc even
   const int ex = std::min(budget, max_tile_elems<T>(D.ax[0], g.thr));
-  auto pick_lx = [&](int nc) {
-    int lx = std::max(1, (2 * ex) / (nc * D.n1));
-    if (lx > nsp) lx = (int)std::max<long long>(1, nsp);
-    while (lx > 1 && ((lx * nc) & 1)) --lx;
-    if ((lx * nc) & 1) lx = 2;  // odd nc with a single line: pair two lines
-    return lx;
-  };
-  g.LX = pick_lx(D.c);
-  g.LXm = pick_lx(D.s);
+  g.LX = x_tile_lines(D.n1, nsp, ex, D.c);
+  g.LXm = x_tile_lines(D.n1, nsp, ex, D.s);
+  g.fits = x_tile_fits(D, g.thr, g.LX, D.c) && x_tile_fits(D, g.thr, g.LXm, D.s);
   P.h.lx = g.LX;
   P.h.lxm = g.LXm;
   g.blk_x = (int)((nsp + g.LX - 1) / g.LX);
@@ -83,6 +97,7 @@ void plan_geometry(Plan<T>& P) {
       g.blk_col[ax][op] = ((D.nh + bx - 1) / bx) * nouter;
       g.sm_col[ax][op] = (size_t)(N + col_es(ns, bx, sizeof(T)) * N) * cs;
       g.max_blocks = std::max(g.max_blocks, g.blk_col[ax][op]);
+      if (N > 1 && ((long long)nb * bx * N > maxe || g.sm_col[ax][op] > kMaxDynSmem)) g.fits = false;
     }
   }
 }
@@ -99,8 +114,9 @@ bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx) {
   const int thr = plain ? kColThreadsPlain : kColThreadsOp;
   const int maxbx = plain && sizeof(T) == 4 ? 16 : 4;  // 16-wide plain tiles: FP32 only (tuned, not default)
   if (bx < 1 || bx > maxbx || (bx & (bx - 1))) return false;
+  const size_t sm = (size_t)(N + col_es(ns, bx, sizeof(T)) * N) * sizeof(cplx<T>);
   return (long long)col_batch_slots(op, ns) * bx * N <= max_tile_elems<T>(D.ax[axis], thr) &&
-         (size_t)col_es(ns, bx, sizeof(T)) * N * sizeof(cplx<T>) <= 64 * 1024;
+         ((size_t)col_es(ns, bx, sizeof(T)) * N * sizeof(cplx<T>) <= 64 * 1024 || (bx == 1 && sm <= kMaxDynSmem));
 }
 
 template <typename T>
@@ -525,16 +541,29 @@ __global__ void __launch_bounds__(256) k_xplain(const Desc<T>* __restrict__ dd, 
   }
 }
 
+// x lines per block of the standalone transform of ncomp components, and whether its
+// tile fits (ncomp = 5 in 3-D takes five line pairs per tile on long x axes).
+template <typename T>
+int rfft3_lines(const Plan<T>& P, int ncomp) {
+  const Desc<T>& D = P.h;
+  const int ex = std::min(2048, max_tile_elems<T>(D.ax[0], P.g.thr));
+  return x_tile_lines(D.n1, (long long)D.n2 * D.n3, ex, ncomp);
+}
+template <typename T>
+bool rfft3_fits(const Plan<T>& P, int ncomp) {
+  return x_tile_fits(P.h, P.g.thr, rfft3_lines(P, ncomp), ncomp);
+}
+template <typename T>
+int axis_tile_capacity(const AxisPlan& pl) {
+  return max_tile_elems<T>(pl, 256);
+}
+
 template <typename T>
 void launch_rfft3(const Plan<T>& P, int dir, int ncomp, int real_slot, cudaStream_t st) {
   const Desc<T>& D = P.h;
   const PassGeo& g = P.g;
   const long long nsp = (long long)D.n2 * D.n3;
-  const int ex = std::min(2048, max_tile_elems<T>(D.ax[0], g.thr));
-  int lx = std::max(1, (2 * ex) / (ncomp * D.n1));
-  if (lx > nsp) lx = (int)std::max<long long>(1, nsp);
-  while (lx > 1 && ((lx * ncomp) & 1)) --lx;
-  if ((lx * ncomp) & 1) lx = 2;
+  const int lx = rfft3_lines(P, ncomp);
   const int nb = (int)((nsp + lx - 1) / lx);
   const size_t sm = (size_t)(D.n1 + (lx * ncomp / 2) * row_stride(D.n1)) * sizeof(cplx<T>);
   const int axes[2] = {1, 2};
@@ -622,6 +651,8 @@ cudaError_t init_kernel_attributes_impl() {
   template int geo_blocks<T>(const Plan<T>&, int, int);                                                     \
   template size_t geo_smem<T>(const Plan<T>&, int, int);                                                    \
   template void launch_rfft3<T>(const Plan<T>&, int, int, int, cudaStream_t);                               \
+  template bool rfft3_fits<T>(const Plan<T>&, int);                                                         \
+  template int axis_tile_capacity<T>(const AxisPlan&);                                                      \
   template cudaError_t init_kernel_attributes_impl<T, 0>();
 
 // Grouped (batched) kernels.

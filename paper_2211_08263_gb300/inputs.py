@@ -375,6 +375,44 @@ def config_c3(nsteps: int = 400, n: int = 256, ngrains: int = 500, seed: int = 3
                    slab_mask(3, shape, 4), U, tol=1e-10, extra={"seed": seed, "ngrains": ngrains})
 
 
+# nickel single crystal of the polycrystalline bar (Sec. 4.3)
+NI_BAR_CUBIC = (249e9, 155e9, 114e9)
+NI_BAR_RHO = 8908.0
+
+
+def config_bar567(nsteps: int = 60, pulse_grains: float = 20.0, seed: int = 567,
+                  dt_cfl: float = 10.0) -> Problem:
+    """The polycrystalline bar of Sec. 4.3: 35 x 35 x 567 voxels of 10 um (0.35 x 0.35 x
+    5.67 mm), nickel grains (C11 = 249, C12 = 155, C44 = 114 GPa, rho = 8908) with random
+    orientations; bell pulse (Eq. prescribed_displacement, alpha = 4, A = 5.67e-6 m,
+    omega = pi c / (pulse_grains d_g), c = sqrt(C11 / rho), d_g = 100 um) on u_3 of the
+    plane x_3 = 0, u_1 = u_2 = 0 there.  Synthetic stand-in for the paper's microstructure:
+    a periodic Voronoi map with as many grains as spheres of 100 um fill the bar (the
+    paper's weighted, log-normal tessellation is not reproduced).  dt = dt_cfl * CFL with
+    CFL = h / c (Sec. 3.1); pulse_grains = 3 is the paper's short pulse, 20 its long one."""
+    n = (35, 35, 567)
+    h = 1e-5
+    dg = 1e-4
+    V = n[0] * n[1] * n[2]
+    ngrains = int(round(V * h ** 3 / (np.pi / 6.0 * dg ** 3)))
+    rng = np.random.default_rng(seed)
+    ids, _ = periodic_voronoi(n, ngrains, rng)
+    Rs = random_rotations(rng, ngrains)
+    base = cubic_voigt(*NI_BAR_CUBIC)
+    Cv = np.stack([voigt21_from_matrix(rotate_voigt(base, R)) for R in Rs])
+    rho = np.full(ngrains, NI_BAR_RHO)
+    c0 = np.sqrt(NI_BAR_CUBIC[0] / NI_BAR_RHO)
+    dt = dt_cfl * h / c0
+    omega = np.pi * c0 / (pulse_grains * dg)
+    t = dt * np.arange(1, nsteps + 1)
+    U = np.zeros((nsteps, 3))
+    U[:, 2] = bell_pulse(t, 5.67e-6, omega, 4.0)
+    mask = np.zeros((3, n[2], n[1], n[0]), dtype=np.uint8)
+    mask[:, 0, :, :] = 1
+    return Problem("bar_polycrystal_35x35x567", 3, n, (h,) * 3, dt, 0.25, 0.5, Cv, rho, ids, mask, U,
+                   tol=1e-10, extra={"seed": seed, "ngrains": ngrains, "pulse_grains": pulse_grains})
+
+
 BATCH_SIZES = (64, 80, 96, 128, 144, 160, 192)
 
 

@@ -36,7 +36,8 @@ def test_default_options(lib):
     assert o.precision == wfft.FP64 and o.tol == 1e-10 and o.maxit == 1000 and o.check_every >= 1
 
 
-@pytest.mark.parametrize("case", ["ndim", "n2d", "dt", "rho", "spd", "nphase", "allmasked", "prime", "1d"])
+@pytest.mark.parametrize("case", ["ndim", "n2d", "dt", "rho", "spd", "nphase", "allmasked", "prime", "1d",
+                                  "long"])
 def test_create_rejects_bad_inputs_before_device_work(lib, case):
     from paper_2211_08263_gb300 import wfft
     p = inputs.config_c1(2)
@@ -63,6 +64,12 @@ def test_create_rejects_bad_inputs_before_device_work(lib, case):
     elif case == "prime":
         kw["n"] = (11, 64, 1)
         kw["phase"] = np.zeros((1, 64, 11), np.uint16)
+        kw["mask"] = None
+        expect = wfft.EUNSUPPORTED
+    elif case == "long":
+        # 3^7: 7-smooth, but longer than any radix schedule is made for
+        kw["n"] = (2187, 64, 1)
+        kw["phase"] = np.zeros((1, 64, 2187), np.uint16)
         kw["mask"] = None
         expect = wfft.EUNSUPPORTED
     elif case == "1d":
