@@ -52,7 +52,7 @@ extern "C" {
 #define WFFT_ENOTCONV 4      /* Krylov solve hit maxit; the step is not committed, state unchanged */
 #define WFFT_ENUMERIC 5      /* NaN/Inf or a non-positive curvature p.Ap in the solve; step not committed */
 #define WFFT_ETIMEOUT 6      /* iteration watchdog fired; step not committed */
-#define WFFT_EUNSUPPORTED 7  /* axis with a prime factor > 7 or too long for the tiles, or N2 = N3 = 1 */
+#define WFFT_EUNSUPPORTED 7  /* axis with two prime factors > 7 (or one > 127) or too long for the tiles, or N2 = N3 = 1 */
 
 /* arithmetic of the Krylov solve */
 #define WFFT_FP64 0   /* everything FP64 */
@@ -134,6 +134,10 @@ WFFT_API int wfft_default_options(wfft_options* opt);
  * The volume averages Cbar and rho_bar of the preconditioner (Eq. precond,
  * Eq. acous) and the lifting fields used by the stopping test are computed
  * here.  Returns WFFT_EINVAL / WFFT_EUNSUPPORTED / WFFT_ENOMEM / WFFT_ECUDA.
+ * Axis lengths: prime factors 2, 3, 5, 7 and at most one other prime P <= 127 (the
+ * paper's odd grids, e.g. 129 = 3 x 43 and 1025 = 5^2 x 41, Sec. 4.1); P is taken by a
+ * direct P-point DFT stage (P products per element) ahead of the radix stages; each axis
+ * must also fit the tiles of the passes (EUNSUPPORTED otherwise).
  * The state starts at rest (u = v = a = 0).
  */
 WFFT_API int wfft_create(const wfft_grid* grid, const double* C, const uint16_t* phase, int nphase,
@@ -315,8 +319,9 @@ WFFT_API int wfft_net_loss_grad(const void* blob, size_t bytes, const int n[3], 
 WFFT_API int wfft_autotune(wfft_handle* h, int reps, int* changed);
 /*
  * Radix schedule of one axis of one precision's plan, set by hand: cnt[r] stages of
- * radix 8, 4, 2, 3, 5, 7, 16 (r = 0..6; their product must be the axis length).  The
- * stages run in the order 16s, 8s, 4s,
+ * radix 8, 4, 2, 3, 5, 7, 16 (r = 0..6; their product, times the axis's prime factor
+ * above 7 if it has one, must be the axis length).  The stages run in the order: the
+ * prime factor's direct DFT stage (implied, not a choice), then 16s, 8s, 4s,
  * 2s, 3s, 5s, 7s.  The tile geometry follows; a schedule that would need more
  * partial-sum slots than the handle allocated is refused (EINVAL, plan unchanged).
  * Synchronises the stream.

@@ -290,7 +290,8 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   for (int i = 0; i < 3; ++i) {
     AxisPlan pl;
     if (!factorize(grid->n[i], pl))
-      return fail(nullptr, WFFT_EUNSUPPORTED, "axis lengths must have prime factors 2, 3, 5, 7 only");
+      return fail(nullptr, WFFT_EUNSUPPORTED,
+                  "axis lengths must have prime factors 2, 3, 5, 7 and at most one other prime, up to 127");
   }
   wfft_handle* h = new (std::nothrow) wfft_handle();
   if (!h) return fail(nullptr, WFFT_ENOMEM, "host allocation failed");
@@ -1900,13 +1901,16 @@ extern "C" int wfft_set_radix(wfft_handle* h, int precision, int axis, const int
   static const int rad[7] = {8, 4, 2, 3, 5, 7, 16};
   AxisPlan pl;
   pl.n = h->n[axis];
-  long long prod = 1;
+  pl.prime = axis_prime(h->n[axis]);  // the general prime stage is implied by the axis length
+  long long prod = pl.prime > 0 ? pl.prime : 1;
   for (int r = 0; r < 7; ++r) {
     if (cnt[r] < 0 || cnt[r] > 16) return fail(h, WFFT_EINVAL, "stage counts must be 0..16");
     pl.cnt[r] = cnt[r];
     for (int k = 0; k < cnt[r]; ++k) prod *= rad[r];
   }
-  if (prod != h->n[axis]) return fail(h, WFFT_EINVAL, "the stages' radices must multiply to the axis length");
+  if (prod != h->n[axis])
+    return fail(h, WFFT_EINVAL,
+                "the stages' radices (times the prime factor above 7, if any) must multiply to the axis length");
   ProfScope ps_(h);
   return precision == WFFT_FP64 ? set_radix_plan<double>(h, h->P64, axis, pl)
                                 : set_radix_plan<float>(h, h->P32, axis, pl);
@@ -2069,15 +2073,18 @@ int set_plan(wfft_handle* h, Plan<T>& P, const wfft_plan_choice* in) {
   Desc<T>& D = P.h;
   AxisPlan ax[3];
   for (int a = 0; a < 3; ++a) {
-    long long prod = 1;
     ax[a].n = h->n[a];
+    ax[a].prime = axis_prime(h->n[a]);  // implied by the axis length
+    long long prod = ax[a].prime > 0 ? ax[a].prime : 1;
     for (int r = 0; r < 7; ++r) {
       const int c = in->radix[a][r];
       if (c < 0 || c > 16) return fail(h, WFFT_EINVAL, "stage counts must be 0..16");
       ax[a].cnt[r] = c;
       for (int k = 0; k < c; ++k) prod *= rad[r];
     }
-    if (prod != h->n[a]) return fail(h, WFFT_EINVAL, "a radix schedule does not multiply to its axis length");
+    if (prod != h->n[a])
+      return fail(h, WFFT_EINVAL,
+                  "a radix schedule (times the prime factor above 7, if any) does not multiply to its axis length");
   }
   if (in->xelems != 0 && (in->xelems < 256 || in->xelems > 8192))
     return fail(h, WFFT_EINVAL, "the x-pass tile size must be 0 or 256..8192 elements");

@@ -21,10 +21,14 @@ constexpr int kMaxStages = 12;
 constexpr int kCtabStride3 = 24;  // 21 Voigt values padded for vector loads
 constexpr int kCtabStride2 = 8;   // 6 in-plane values padded
 
-// Radix schedule of one axis: cnt[] = number of stages of radix 8, 4, 2, 3, 5, 7.
+// Radix schedule of one axis: cnt[] = number of stages of radix 8, 4, 2, 3, 5, 7, 16,
+// prime = the one prime factor above 7 (11..kMaxPrime) the axis may have, taken by a
+// general prime-length DFT stage that runs first (0: none).
+constexpr int kMaxPrime = 127;
 struct AxisPlan {
   int n;
   int cnt[7];  // stages of radix 8, 4, 2, 3, 5, 7, 16 (16: FP32 plans only)
+  int prime;
 };
 
 // Scalars of one Krylov solve, updated only by the single-block finalize kernels.

@@ -270,19 +270,89 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
   __syncthreads();
 }
 
+// Outputs a thread computes per general prime stage (fft_stage_prime); the host
+// accepts only tiles of at most kPrimeBatch * threads elements on such axes.
+constexpr int kPrimeBatch = 16;
+
+// General prime-length stage for the one prime factor P > 7 of an axis, run first
+// (Ns = 1, no inter-stage twiddles): with n = N / P butterflies per line, output q of
+// butterfly j is y[j P + q] = sum_r x[j + r n] W_P^{(r q) mod P} (conjugate roots for
+// the inverse), a direct P-point DFT.  Each output is one P-term sum read from shared
+// memory, its roots from the stage's table block (W_P^m at m - 1); a thread keeps up to
+// kPrimeBatch outputs between the two barriers, so the stage runs in place like the
+// others.  The loops over a thread's outputs are not unrolled: the outputs then live in
+// local memory (L1) on this path only, and the stage takes no registers from the
+// kernels it is compiled into (their other paths keep their register allocation).
+// Cost: P complex products per element, against about R per radix-R element
+// elsewhere: meant for the odd grid sizes of the paper (41, 43), not for speed.
+template <typename T, int ES, int NL>
+__device__ __forceinline__ void fft_stage_prime(cplx<T>* buf, int N, int P, int nlines, int lstride,
+                                                const cplx<T>* tw, int sgn) {
+  constexpr bool LF = NL > 0;
+  const int nb = N / P;
+  const int total = N * (LF ? NL : nlines);
+  const int nthr = blockDim.x;
+  int tid;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+  cplx<T> acc[kPrimeBatch];
+#pragma unroll 1
+  for (int i = 0; i < kPrimeBatch; ++i) {
+    const int id = tid + i * nthr;
+    acc[i] = cmake<T>((T)0, (T)0);
+    if (id < total) {
+      const int line = LF ? id % NL : id / N;
+      const int e = LF ? id / NL : id - line * N;
+      const int j = e / P, q = e - j * P;
+      const cplx<T>* src = LF ? buf + line : buf + (size_t)line * lstride;
+      cplx<T> sum = src[LF ? j * ES : rowpad(j)];
+      int m = q;  // (r q) mod P for r = 1
+      for (int r = 1; r < P; ++r) {
+        const cplx<T> x = src[LF ? (j + r * nb) * ES : rowpad(j + r * nb)];
+        cplx<T> w = cmake<T>((T)1, (T)0);
+        if (m) w = tw[m - 1];
+        if (sgn > 0) w.y = -w.y;
+        sum = cadd<T>(sum, cmul<T>(x, w));
+        m += q;
+        if (m >= P) m -= P;
+      }
+      acc[i] = sum;
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int i = 0; i < kPrimeBatch; ++i) {
+    const int id = tid + i * nthr;
+    if (id < total) {
+      const int line = LF ? id % NL : id / N;
+      const int e = LF ? id / NL : id - line * N;
+      cplx<T>* dst = LF ? buf + line : buf + (size_t)line * lstride;
+      dst[LF ? e * ES : rowpad(e)] = acc[i];
+    }
+  }
+  __syncthreads();
+}
+
 // Full transform of `nlines` lines.  sgn = -1 forward, +1 inverse (unnormalised).
-// Stages are applied radix by radix (16s, 8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
+// Stages are applied radix by radix (the general prime stage, if the axis has a prime
+// factor above 7, then 16s, 8s, 4s, 2s, 3s, 5s, 7s): the self-sorting
 // formulation is valid for any order of the radices, and one loop per radix
 // keeps each stage's registers apart.  ES = 1: row tiles with line stride
 // `lstride` (nlines at run time), NL = 0; NL > 0: column tiles (line stride 1,
 // element stride ES, NL lines).  Must be called by every thread of the block (barriers).
-// ONLY16: the caller guarantees a pure radix-16 schedule, and the other stage kinds are
-// not compiled in (a smaller instruction footprint for kernels with several FFT calls).
+// ONLY16: the caller guarantees a pure radix-16 schedule (no prime stage either), and
+// the other stage kinds are not compiled in (a smaller instruction footprint for
+// kernels with several FFT calls).
 template <typename T, int ES, int NL = 0, bool ONLY16 = false>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const AxisPlan& pl, int nlines, int lstride, const cplx<T>* tw,
                                           int sgn) {
   const int N = pl.n;
   int Ns = 1;
+  if constexpr (!ONLY16) {
+    if (pl.prime) {
+      fft_stage_prime<T, ES, NL>(buf, N, pl.prime, nlines, lstride, tw, sgn);
+      Ns = pl.prime;
+    }
+  }
   for (int s = 0; s < pl.cnt[6]; ++s, Ns *= 16) fft_stage<T, 16, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);
   if constexpr (ONLY16) return;
   for (int s = 0; s < pl.cnt[0]; ++s, Ns *= 8) fft_stage<T, 8, ES, NL>(buf, N, nlines, lstride, Ns, tw, sgn);

@@ -15,13 +15,34 @@ namespace wfft {
 // up to 1365 points in FP32 and 597-1365 in FP64, depending on the radices.
 constexpr int kMaxAxis = 2048;
 
+// The prime factor of n above 7 that a general prime-length stage takes: 0 if n is
+// 7-smooth, -1 if what is left after dividing out 2, 3, 5 and 7 is not one prime of
+// 11..kMaxPrime (two such primes, a square of one, or a larger prime).
+static inline int axis_prime(int n) {
+  if (n < 1) return -1;
+  int m = n;
+  const int small[4] = {2, 3, 5, 7};
+  for (int q = 0; q < 4; ++q)
+    while (m % small[q] == 0) m /= small[q];
+  if (m == 1) return 0;
+  if (m > kMaxPrime) return -1;
+  for (int d = 2; d * d <= m; ++d)
+    if (m % d == 0) return -1;
+  return m;
+}
+
 // radix schedule: as many 8s as possible, the rest of the power of two as 4s / a 2
-// (4*4 rather than 8*2), then the odd radices 3, 5, 7
+// (4*4 rather than 8*2), then the odd radices 3, 5, 7, and the prime factor above 7
+// (if any) as one general stage
 static inline bool factorize(int n, AxisPlan& pl) {
   pl.n = n;
   for (int i = 0; i < 7; ++i) pl.cnt[i] = 0;
+  pl.prime = 0;
   if (n < 1 || n > kMaxAxis) return false;
-  int m = n, e2 = 0;
+  const int prime = axis_prime(n);
+  if (prime < 0) return false;
+  pl.prime = prime;
+  int m = prime ? n / prime : n, e2 = 0;
   while (m % 2 == 0) {
     m /= 2;
     ++e2;
@@ -44,7 +65,8 @@ static inline bool factorize(int n, AxisPlan& pl) {
 
 // Every decomposition of n the FFT stages support: the power-of-two part as radix-16
 // (when allow16), radix-8, radix-4 and at most one radix-2 stage in any
-// mix, the odd part as 3s, 5s and 7s.  Empty if n is not supported.
+// mix, the odd part as 3s, 5s and 7s (and the general prime stage, if any).  Empty if
+// n is not supported.
 static inline std::vector<AxisPlan> factor_candidates(int n, bool allow16) {
   std::vector<AxisPlan> out;
   AxisPlan base;
@@ -96,12 +118,14 @@ static inline std::vector<cplx<T>> twiddles(int n) {
 }
 
 // Per-stage twiddle table of a radix schedule (the stages in the order the FFT runs
-// them: 16s, 8s, 4s, 2s, 3s, 5s, 7s).  The stage of radix R after Ns points have
-// been combined uses W_{Ns R}^{r k} (r = 1..R-1, k = 0..Ns-1), kept at
-// (Ns - 1) + (r - 1) Ns + k: consecutive butterflies of a stage read consecutive
-// entries (no shared-memory bank conflicts), and since the blocks of successive stages
-// have Ns (R - 1) = Ns' - Ns entries the table has exactly n - 1 entries (n entries
-// are written, the last one unused).
+// them: the general prime stage P, then 16s, 8s, 4s, 2s, 3s, 5s, 7s).  The stage of
+// radix R after Ns points have been combined uses W_{Ns R}^{r k} (r = 1..R-1,
+// k = 0..Ns-1), kept at (Ns - 1) + (r - 1) Ns + k: consecutive butterflies of a stage
+// read consecutive entries (no shared-memory bank conflicts), and since the blocks of
+// successive stages have Ns (R - 1) = Ns' - Ns entries the table has exactly n - 1
+// entries (n entries are written, the last one unused).  The prime stage runs at
+// Ns = 1, where those twiddles are all 1; its block of P - 1 entries holds the roots
+// of its own DFT instead: W_P^m at m - 1 (m = 1..P-1).
 template <typename T>
 static inline void fill_stage_twiddles(cplx<T>* w, const AxisPlan& pl) {
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -112,6 +136,15 @@ static inline void fill_stage_twiddles(cplx<T>* w, const AxisPlan& pl) {
     w[i].y = (T)0;
   }
   int Ns = 1;
+  if (pl.prime) {
+    const int P = pl.prime;
+    for (int m = 1; m < P; ++m) {
+      const long double a = -2.0L * pi * (long double)m / (long double)P;
+      w[m - 1].x = (T)cosl(a);
+      w[m - 1].y = (T)sinl(a);
+    }
+    Ns = P;
+  }
   for (int q = 0; q < 7; ++q)
     for (int s = 0; s < cnt[q]; ++s) {
       const int R = rad[q];

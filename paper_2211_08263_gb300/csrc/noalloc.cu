@@ -79,7 +79,8 @@ extern "C" int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21]
   D.n3 = grid->n[2];
   for (int ax = 0; ax < 3; ++ax)
     if (!initial_schedule(grid->n[ax], D.ax[ax], [](const AxisPlan& c) { return axis_tile_capacity<double>(c); }))
-      return na_fail(WFFT_EUNSUPPORTED, "axis lengths must have prime factors 2, 3, 5, 7 only");
+      return na_fail(WFFT_EUNSUPPORTED,
+                     "axis lengths must have prime factors 2, 3, 5, 7 and at most one other prime, up to 127");
   D.nh = D.n1 / 2 + 1;
   D.pitch = ((D.nh + 7) / 8) * 8;
   D.opAxis = D.n3 > 1 ? 2 : 1;

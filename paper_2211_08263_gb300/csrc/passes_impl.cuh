@@ -20,6 +20,8 @@ static int max_tile_elems(const AxisPlan& pl, int thr) {
                       5 * NbOf<T, 5>::v, 7 * NbOf<T, 7>::v, 16 * NbOf<T, 16>::v};
   for (int i = 0; i < 7; ++i)
     if (pl.cnt[i]) cap = std::min(cap, per[i] * thr);
+  // the general prime stage: kPrimeBatch outputs per thread
+  if (pl.prime) cap = std::min(cap, kPrimeBatch * thr);
   return cap;
 }
 
@@ -333,7 +335,7 @@ static void launch_colop_bx(const Launch<T, B>& L, int axis, cudaStream_t st) {
   // other stage kinds
   const AxisPlan& ap = L.P.h.ax[axis];
   const bool only16 = ap.cnt[6] > 0 && !ap.cnt[0] && !ap.cnt[1] && !ap.cnt[2] && !ap.cnt[3] && !ap.cnt[4] &&
-                      !ap.cnt[5];
+                      !ap.cnt[5] && !ap.prime;
   prof_launch(prec_index(sizeof(T)), kind, by, fl, st, [&] {
     if (!d3)
       k_colop<T, OP, BX, kSmall, B><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);

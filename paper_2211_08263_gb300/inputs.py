@@ -413,6 +413,34 @@ def config_bar567(nsteps: int = 60, pulse_grains: float = 20.0, seed: int = 567,
                    tol=1e-10, extra={"seed": seed, "ngrains": ngrains, "pulse_grains": pulse_grains})
 
 
+# Aluminium of the paper's material table (Sec. 3.1): E, nu, rho
+AL_E_NU_RHO = (70.3e9, 0.345, 2700.0)
+
+
+def config_sphere129(nsteps: int = 6, pulse_steps: float = 12.0) -> Problem:
+    """Spherical waves in a homogeneous solid (Sec. 4.1): a 1 m aluminium cube of
+    129^3 voxels (129 = 3 x 43), dt = 1.52e-6 s, the bell pulse (Eq.
+    prescribed_displacement, alpha = 4, amplitude 1 mm) on u_1 of the voxels whose
+    centres lie within R = 1 cm of the centre of the cube (the centre voxel and its six
+    face neighbours at h = 7.75 mm), u_2 = u_3 = 0 there.  The pulse frequency is not
+    printed for this case: omega = pi / (pulse_steps dt), a pulse of pulse_steps steps."""
+    n = (129, 129, 129)
+    h = 1.0 / 129
+    E, nu, rho = AL_E_NU_RHO
+    Cv = voigt21_from_matrix(isotropic_voigt(E, nu))[None, :]
+    dt = 1.52e-6
+    x = (np.arange(129) + 0.5) * h - 0.5
+    r2 = x[:, None, None] ** 2 + x[None, :, None] ** 2 + x[None, None, :] ** 2
+    mask = np.zeros((3, 129, 129, 129), dtype=np.uint8)
+    mask[:, r2 <= 0.01 ** 2] = 1
+    t = dt * np.arange(1, nsteps + 1)
+    U = np.zeros((nsteps, 3))
+    U[:, 0] = bell_pulse(t, 1e-3, np.pi / (pulse_steps * dt), 4.0)
+    phase = np.zeros((129, 129, 129), dtype=np.uint16)
+    return Problem("sphere_al_129", 3, n, (h,) * 3, dt, 0.25, 0.5, Cv, np.array([rho]), phase, mask, U,
+                   tol=1e-10, extra={"pulse_steps": pulse_steps})
+
+
 BATCH_SIZES = (64, 80, 96, 128, 144, 160, 192)
 
 

@@ -36,8 +36,8 @@ def test_default_options(lib):
     assert o.precision == wfft.FP64 and o.tol == 1e-10 and o.maxit == 1000 and o.check_every >= 1
 
 
-@pytest.mark.parametrize("case", ["ndim", "n2d", "dt", "rho", "spd", "nphase", "allmasked", "prime", "1d",
-                                  "long"])
+@pytest.mark.parametrize("case", ["ndim", "n2d", "dt", "rho", "spd", "nphase", "allmasked", "prime", "bigprime",
+                                  "1d", "long"])
 def test_create_rejects_bad_inputs_before_device_work(lib, case):
     from paper_2211_08263_gb300 import wfft
     p = inputs.config_c1(2)
@@ -62,8 +62,15 @@ def test_create_rejects_bad_inputs_before_device_work(lib, case):
     elif case == "allmasked":
         kw["mask"] = np.ones_like(p.mask)
     elif case == "prime":
-        kw["n"] = (11, 64, 1)
-        kw["phase"] = np.zeros((1, 64, 11), np.uint16)
+        # 143 = 11 x 13: two prime factors above 7 (one general prime stage per axis)
+        kw["n"] = (143, 64, 1)
+        kw["phase"] = np.zeros((1, 64, 143), np.uint16)
+        kw["mask"] = None
+        expect = wfft.EUNSUPPORTED
+    elif case == "bigprime":
+        # 2 x 131: a prime factor above the largest direct DFT stage (127)
+        kw["n"] = (262, 64, 1)
+        kw["phase"] = np.zeros((1, 64, 262), np.uint16)
         kw["mask"] = None
         expect = wfft.EUNSUPPORTED
     elif case == "long":

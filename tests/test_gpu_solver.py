@@ -161,7 +161,8 @@ def test_failure_statuses_leave_state_unchanged():
         wfft.Solver(3, (8, 8, 8), (1e-3,) * 3, prob.C, -np.abs(prob.rho), prob.phase[:8, :8, :8], None, 1e-7)
     assert e.value.code == wfft.EINVAL
     with pytest.raises(wfft.WfftError) as e:
-        wfft.Solver(3, (11, 8, 8), (1e-3,) * 3, prob.C, prob.rho, np.zeros((8, 8, 11), np.uint16), None, 1e-7)
+        # 143 = 11 x 13: two prime factors above 7 (one direct prime stage per axis)
+        wfft.Solver(3, (143, 8, 8), (1e-3,) * 3, prob.C, prob.rho, np.zeros((8, 8, 143), np.uint16), None, 1e-7)
     assert e.value.code == wfft.EUNSUPPORTED
 
 
