@@ -1,11 +1,30 @@
 """Pins of the FP64 oracle against closed forms, the paper's printed numbers,
 invariants and a brute-force dense solve -- nothing here compares the oracle
 with itself.  CPU only."""
+import os
+
 import numpy as np
 import pytest
 
 from paper_2211_08263_gb300 import inputs
 from oracle import analytic, dense, green, medium, newmark, pcg, spectral
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    """Rows of a fixture of values printed by the paper (tests/golden, '#' lines cite them)."""
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+TABLE2 = {int(r[0]): float(r[1]) for r in _golden("table2_bar_implicit_fft.txt")}
+TABLE4 = {r[0]: (float(r[1]), float(r[2])) for r in _golden("table4_plane_wave_speeds.txt")}
 
 rel = lambda a, b: float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
@@ -288,31 +307,52 @@ def _bar_run(ratio):
     return rel(s.u[0], ua)
 
 
-@pytest.mark.parametrize("ratio,paper", [(5, 2.09e-3), (10, 5.36e-3)])
-def test_1d_aluminium_bar_reproduces_table_2(ratio, paper):
+@pytest.mark.parametrize("ratio", [5, 10])
+def test_1d_aluminium_bar_reproduces_table_2(ratio):
     """Sec. 3.1, Table 2 (implicit FFT column): Al bar, N = 6561, bell pulse at
     x0 = 0 (Eq. prescribed_displacement), error of Eq. normL2 at the final time
     against the d'Alembert solution (App. C), within a factor 1.5."""
     err = _bar_run(ratio)
+    paper = TABLE2[ratio]
     assert paper / 1.5 < err < paper * 1.5, err
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("ratio,paper", [(1, 2.59e-3), (2, 2.48e-3)])
-def test_1d_aluminium_bar_reproduces_table_2_small_dt(ratio, paper):
+@pytest.mark.parametrize("ratio", [1, 2])
+def test_1d_aluminium_bar_reproduces_table_2_small_dt(ratio):
+    paper = TABLE2[ratio]
     err = _bar_run(ratio)
     assert paper / 1.5 < err < paper * 1.5, err
+
+
+def test_material_table_follows_the_isotropic_closed_forms():
+    """Sec. 3.1, material table: lambda and mu from E and nu (the relations the oracle
+    uses to build isotropic stiffnesses) and the 1-D speed c0 = sqrt(E / rho) reproduce the
+    printed values; lambda and mu within 0.2 % (iron's printed nu = 0.293 is rounded: its
+    printed mu = 81.6 GPa needs nu = 0.295), c0 within 0.1 m/s."""
+    rows = _golden("table1_materials.txt")
+    assert [r[0] for r in rows] == ["Aluminium", "Iron", "Uranium"]
+    for name, E, rho, lam_p, mu_p, nu, c0_p in rows:
+        E, rho, lam_p, mu_p, nu, c0_p = (float(v) for v in (E, rho, lam_p, mu_p, nu, c0_p))
+        lam, mu = analytic.lame(E * 1e9, nu)
+        assert abs(lam / 1e9 - lam_p) <= 2e-3 * lam_p, (name, lam / 1e9)
+        assert abs(mu / 1e9 - mu_p) <= 2e-3 * mu_p, (name, mu / 1e9)
+        assert abs(np.sqrt(E * 1e9 / rho) - c0_p) <= 0.1, name
+        # the 1-D speed is the longitudinal speed of a material with nu = 0
+        lam0, mu0 = analytic.lame(E * 1e9, 0.0)
+        assert abs(analytic.isotropic_speeds(lam0, mu0, rho)[0] - c0_p) <= 0.1
 
 
 def test_3d_plane_wave_speeds_match_table_4():
     """Sec. 3.2 / Table 4 analogue: homogeneous Al (E = 70.3 GPa, nu = 0.345),
     a plane source on the x_1 = 0 voxel plane, dt = 10 CFL; the pulse centroid
-    moves at c_L = 6395.5 m/s (P) and c_S = 3111.1 m/s (S), within 1e-2."""
+    moves at c_L = 6395.5 m/s (P) and c_S = 3111.1 m/s (S), within 1e-2, as do the
+    paper's measured 6398.4 and 3105.4 m/s (tests/golden/table4_plane_wave_speeds.txt)."""
     E, rho = AL
     nu = 0.345
     lam, mu = analytic.lame(E, nu)
     cL, cS = analytic.isotropic_speeds(lam, mu, rho)
-    assert abs(cL - 6395.5) < 1.0 and abs(cS - 3111.1) < 1.0
+    assert abs(cL - TABLE4["P"][0]) < 1.0 and abs(cS - TABLE4["S"][0]) < 1.0
     C = medium.tensor_from_voigt21(inputs.voigt21_from_matrix(inputs.isotropic_voigt(E, nu)))
     N1, h = 2187, 1e-3  # as Table 4 (the pulse then spans ~44 steps at 10 CFL)
     shape = (1, 3, N1)
@@ -340,6 +380,9 @@ def test_3d_plane_wave_speeds_match_table_4():
         n1, n2 = int(0.25 * N1 * h / c / dt), nsteps
         speed = (cents[n2] - cents[n1]) / ((n2 - n1) * dt)
         assert abs(speed - c) / c < 1e-2, (comp, speed, c)
+        # and the speed the paper measured on its own implicit FFT solution
+        fft = TABLE4["P" if comp == 0 else "S"][1]
+        assert abs(speed - fft) / fft < 1e-2, (comp, speed, fft)
 
 
 # --------------------------------------------------------------------------
