@@ -283,8 +283,9 @@ constexpr int kPrimeBatch = 16;
 // others.  The loops over a thread's outputs are not unrolled: the outputs then live in
 // local memory (L1) on this path only, and the stage takes no registers from the
 // kernels it is compiled into (their other paths keep their register allocation).
-// Cost: P complex products per element, against about R per radix-R element
-// elsewhere: meant for the odd grid sizes of the paper (41, 43), not for speed.
+// Cost: (P - 1) / 2 paired terms per element (4 real products each), against about
+// R per radix-R element elsewhere: meant for the odd grid sizes of the paper (41, 43),
+// not for speed.
 template <typename T, int ES, int NL>
 __device__ __forceinline__ void fft_stage_prime(cplx<T>* buf, int N, int P, int nlines, int lstride,
                                                 const cplx<T>* tw, int sgn) {
@@ -305,13 +306,19 @@ __device__ __forceinline__ void fft_stage_prime(cplx<T>* buf, int N, int P, int 
       const int j = e / P, q = e - j * P;
       const cplx<T>* src = LF ? buf + line : buf + (size_t)line * lstride;
       cplx<T> sum = src[LF ? j * ES : rowpad(j)];
+      // terms r and P - r share the root's cosine and negate its sine (P is odd):
+      // x_r W^{rq} + x_{P-r} W^{-rq} = (x_r + x_{P-r}) cos + i t (x_r - x_{P-r}),
+      // t = -sin (forward) or +sin (inverse) of 2 pi r q / P
       int m = q;  // (r q) mod P for r = 1
-      for (int r = 1; r < P; ++r) {
-        const cplx<T> x = src[LF ? (j + r * nb) * ES : rowpad(j + r * nb)];
+      for (int r = 1; r <= (P - 1) / 2; ++r) {
+        const cplx<T> a = src[LF ? (j + r * nb) * ES : rowpad(j + r * nb)];
+        const cplx<T> b = src[LF ? (j + (P - r) * nb) * ES : rowpad(j + (P - r) * nb)];
         cplx<T> w = cmake<T>((T)1, (T)0);
         if (m) w = tw[m - 1];
-        if (sgn > 0) w.y = -w.y;
-        sum = cadd<T>(sum, cmul<T>(x, w));
+        const T t = sgn > 0 ? -w.y : w.y;
+        const cplx<T> sm = cadd<T>(a, b), df = csub<T>(a, b);
+        sum.x += sm.x * w.x - t * df.y;
+        sum.y += sm.y * w.x + t * df.x;
         m += q;
         if (m >= P) m -= P;
       }
