@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the launch-bound C1 (64^2) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT plans (no wfft_autotune)")
     ap.add_argument("--no-explicit", action="store_true", help="skip the explicit-scheme measurement")
+    ap.add_argument("--no-sphere", action="store_true", help="skip the 129^3 sphere (prime-length stage) measurement")
     ap.add_argument("--plan", default=None,
                     help="plan choices to apply instead of autotuning: a JSON file, or the JSON text itself")
     ap.add_argument("--save-plan", default=None, help="write the plan choices of the timed handles (JSON)")
@@ -404,6 +405,34 @@ def small_grid(wfft, torch, steps=50):
     return out
 
 
+def sphere129(wfft, torch, W=3, K=10):
+    """The paper's spherical waves in a homogeneous aluminium cube (Sec. 4.1): 129^3 voxels,
+    129 = 3 x 43, so every axis runs the direct 43-point DFT stage ahead of its radix-3
+    stage; central u_1 bell pulse, dt 1.52e-6 s.  Milliseconds per Newmark step (CUDA events
+    on the solver's stream) and Krylov iterations per step, FP64 and mixed, tol 1e-10."""
+    from paper_2211_08263_gb300 import inputs
+    prob = inputs.config_sphere129(nsteps=W + K)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"workload": "129^3 Al cube (E 70.3 GPa, nu 0.345, rho 2700), u_1 bell pulse within 1 cm of the "
+                       "centre, dt 1.52e-6 s, tol 1e-10; axes 3 x 43 (direct 43-point DFT stage)",
+           "steps": K, "warmup": W}
+    for name, prec in (("fp64", wfft.FP64), ("mixed", wfft.MIXED)):
+        s = wfft.Solver.from_problem(prob, options=wfft.default_options(precision=prec, tol=1e-10, maxit=400),
+                                     stream=stream.cuda_stream)
+        for k in range(W):
+            s.step(prob.U[k])
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        its = sum(s.step(prob.U[k])["iters"] for k in range(W, W + K))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_step": ev0.elapsed_time(ev1) / K, "krylov_iters_per_step": its / K}
+        s.close()
+    return out
+
+
 def explicit_scheme(wfft, torch, prob, W, K):
     """The paper's explicit central-difference variant (Sec. 2.3) on the same 256^3 medium:
     one FP64 operator application per step at 0.9 of the CFL increment."""
@@ -572,6 +601,8 @@ def main():
         line["small_grid"] = small_grid(wfft, torch)
     if not args.no_explicit:
         line["explicit"] = explicit_scheme(wfft, torch, prob, W, K)
+    if not args.no_sphere:
+        line["sphere129"] = sphere129(wfft, torch)
     if "e2e_s" in head:
         line["e2e"] = {"value": V * head["e2e_iters"] * world / head["e2e_s"], "unit": UNIT,
                        "h2d_bytes_per_step": 24, "d2h_bytes_per_step": head["d2h_bytes"],
