@@ -270,70 +270,86 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
   __syncthreads();
 }
 
-// Outputs a thread computes per general prime stage (fft_stage_prime); the host
-// accepts only tiles of at most kPrimeBatch * threads elements on such axes.
+// Elements a tile on an axis with a prime stage may hold per thread (the host accepts
+// only tiles of at most kPrimeBatch * threads elements on such axes), and the output
+// pairs (q, P - q) a thread then computes per prime stage: ceil(16 (P + 1) / (2 P)) = 9
+// for P >= 11.
 constexpr int kPrimeBatch = 16;
+constexpr int kPrimeTasks = 9;
 
 // General prime-length stage for the one prime factor P > 7 of an axis, run first
 // (Ns = 1, no inter-stage twiddles): with n = N / P butterflies per line, output q of
 // butterfly j is y[j P + q] = sum_r x[j + r n] W_P^{(r q) mod P} (conjugate roots for
-// the inverse), a direct P-point DFT.  Each output is one P-term sum read from shared
-// memory, its roots from the stage's table block (W_P^m at m - 1); a thread keeps up to
-// kPrimeBatch outputs between the two barriers, so the stage runs in place like the
-// others.  The loops over a thread's outputs are not unrolled: the outputs then live in
+// the inverse), a direct P-point DFT.  P is odd, so terms r and P - r share the root's
+// cosine and negate its sine: with S_r = x_r + x_{P-r}, D_r = x_r - x_{P-r},
+// A = sum_r S_r cos(2 pi r q / P) and B = sum_r i t_r D_r (t_r = -sin forward, +sin
+// inverse), r = 1..(P-1)/2, the outputs q and P - q are x_0 + A + B and x_0 + A - B.
+// One task computes such a pair from (P - 1) / 2 paired terms read from shared memory,
+// the roots from the stage's table block (W_P^m at m - 1); a thread keeps up to
+// kPrimeTasks pairs between the two barriers, so the stage runs in place like the
+// others.  The loops over a thread's tasks are not unrolled: the pairs then live in
 // local memory (L1) on this path only, and the stage takes no registers from the
 // kernels it is compiled into (their other paths keep their register allocation).
-// Cost: (P - 1) / 2 paired terms per element (4 real products each), against about
-// R per radix-R element elsewhere: meant for the odd grid sizes of the paper (41, 43),
-// not for speed.
+// Cost: (P - 1) / 2 paired terms per two outputs, against about R products per
+// radix-R element elsewhere: meant for the odd grid sizes of the paper (41, 43), not
+// for speed.
 template <typename T, int ES, int NL>
 __device__ __forceinline__ void fft_stage_prime(cplx<T>* buf, int N, int P, int nlines, int lstride,
                                                 const cplx<T>* tw, int sgn) {
   constexpr bool LF = NL > 0;
   const int nb = N / P;
-  const int total = N * (LF ? NL : nlines);
+  const int H = (P + 1) / 2;  // q = 0 .. (P - 1) / 2
+  const int per_line = nb * H;
+  const int tasks = per_line * (LF ? NL : nlines);
   const int nthr = blockDim.x;
   int tid;
   asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
-  cplx<T> acc[kPrimeBatch];
+  cplx<T> yq[kPrimeTasks], ym[kPrimeTasks];
 #pragma unroll 1
-  for (int i = 0; i < kPrimeBatch; ++i) {
+  for (int i = 0; i < kPrimeTasks; ++i) {
     const int id = tid + i * nthr;
-    acc[i] = cmake<T>((T)0, (T)0);
-    if (id < total) {
-      const int line = LF ? id % NL : id / N;
-      const int e = LF ? id / NL : id - line * N;
-      const int j = e / P, q = e - j * P;
+    if (id < tasks) {
+      const int line = LF ? id % NL : id / per_line;
+      const int t = LF ? id / NL : id - line * per_line;
+      const int j = t / H, q = t - j * H;
       const cplx<T>* src = LF ? buf + line : buf + (size_t)line * lstride;
-      cplx<T> sum = src[LF ? j * ES : rowpad(j)];
-      // terms r and P - r share the root's cosine and negate its sine (P is odd):
-      // x_r W^{rq} + x_{P-r} W^{-rq} = (x_r + x_{P-r}) cos + i t (x_r - x_{P-r}),
-      // t = -sin (forward) or +sin (inverse) of 2 pi r q / P
+      const cplx<T> x0 = src[LF ? j * ES : rowpad(j)];
+      cplx<T> A = cmake<T>((T)0, (T)0), B = cmake<T>((T)0, (T)0);
       int m = q;  // (r q) mod P for r = 1
       for (int r = 1; r <= (P - 1) / 2; ++r) {
         const cplx<T> a = src[LF ? (j + r * nb) * ES : rowpad(j + r * nb)];
         const cplx<T> b = src[LF ? (j + (P - r) * nb) * ES : rowpad(j + (P - r) * nb)];
         cplx<T> w = cmake<T>((T)1, (T)0);
         if (m) w = tw[m - 1];
-        const T t = sgn > 0 ? -w.y : w.y;
-        const cplx<T> sm = cadd<T>(a, b), df = csub<T>(a, b);
-        sum.x += sm.x * w.x - t * df.y;
-        sum.y += sm.y * w.x + t * df.x;
+        const T tr = sgn > 0 ? -w.y : w.y;
+        const cplx<T> S = cadd<T>(a, b), D = csub<T>(a, b);
+        A.x += S.x * w.x;
+        A.y += S.y * w.x;
+        B.x -= tr * D.y;
+        B.y += tr * D.x;
         m += q;
         if (m >= P) m -= P;
       }
-      acc[i] = sum;
+      const cplx<T> c = cadd<T>(x0, A);
+      yq[i] = cadd<T>(c, B);
+      ym[i] = csub<T>(c, B);
     }
   }
   __syncthreads();
 #pragma unroll 1
-  for (int i = 0; i < kPrimeBatch; ++i) {
+  for (int i = 0; i < kPrimeTasks; ++i) {
     const int id = tid + i * nthr;
-    if (id < total) {
-      const int line = LF ? id % NL : id / N;
-      const int e = LF ? id / NL : id - line * N;
+    if (id < tasks) {
+      const int line = LF ? id % NL : id / per_line;
+      const int t = LF ? id / NL : id - line * per_line;
+      const int j = t / H, q = t - j * H;
       cplx<T>* dst = LF ? buf + line : buf + (size_t)line * lstride;
-      dst[LF ? e * ES : rowpad(e)] = acc[i];
+      const int e = j * P + q;
+      dst[LF ? e * ES : rowpad(e)] = yq[i];
+      if (q) {
+        const int e2 = j * P + P - q;
+        dst[LF ? e2 * ES : rowpad(e2)] = ym[i];
+      }
     }
   }
   __syncthreads();
