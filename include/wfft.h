@@ -136,8 +136,8 @@ WFFT_API int wfft_default_options(wfft_options* opt);
  * here.  Returns WFFT_EINVAL / WFFT_EUNSUPPORTED / WFFT_ENOMEM / WFFT_ECUDA.
  * Axis lengths: prime factors 2, 3, 5, 7 and at most one other prime P <= 127 (the
  * paper's odd grids, e.g. 129 = 3 x 43 and 1025 = 5^2 x 41, Sec. 4.1); P is taken by a
- * direct P-point DFT stage ((P - 1) / 2 paired terms per element) ahead of the radix stages; each axis
- * must also fit the tiles of the passes (EUNSUPPORTED otherwise).
+ * direct P-point DFT stage ((P - 1) / 2 paired terms per two outputs) ahead of the radix
+ * stages; each axis must also fit the tiles of the passes (EUNSUPPORTED otherwise).
  * The state starts at rest (u = v = a = 0).
  */
 WFFT_API int wfft_create(const wfft_grid* grid, const double* C, const uint16_t* phase, int nphase,
