@@ -384,6 +384,19 @@ WFFT_API int wfft_operator_bound(int ndim, const int n[3], const double h[3], co
                                  long long nrows, double theta, double* lam_max);
 
 /*
+ * Built-in FFT decomposition of an axis of n points (Sec. 2.1.3, Eq. Fourier_derivatives:
+ * the DFT the transforms compute): cnt[r] stages of radix 8, 4, 2, 3, 5, 7, 16 (r = 0..6,
+ * the layout of wfft_set_radix; the built-in schedule uses no radix-16 stage) and *prime =
+ * the axis's prime factor above 7, taken by a direct prime-length DFT stage ahead of the
+ * others (0: none).  This is the schedule a new handle starts from, unless the axis is
+ * too long for the tiles of its passes (a handle then takes the decomposition whose
+ * stages hold the most).  cnt and prime: caller-owned host arrays, written on success.
+ * Returns WFFT_EINVAL (null pointers) or WFFT_EUNSUPPORTED (n outside 1..2048, two prime
+ * factors above 7, or one above 127).  Host computation only.
+ */
+WFFT_API int wfft_axis_plan(int n, int cnt[7], int* prime);
+
+/*
  * The paper's own treatment of the prescribed region (Sec. 2.2.3, Eqs. f_discrete,
  * solve_green, G, Vt, L-determination_ND; Alg. 2), for small regions; FP64 implicit
  * handles only.  wfft_green_setup solves A g = e_(p,j) without the projection P for a

@@ -1868,6 +1868,17 @@ extern "C" int wfft_operator_bound(int ndim, const int n[3], const double h[3], 
   return WFFT_OK;
 }
 
+extern "C" int wfft_axis_plan(int n, int cnt[7], int* prime) {
+  if (!cnt || !prime) return fail(nullptr, WFFT_EINVAL, "cnt and prime are required");
+  AxisPlan pl;
+  if (!factorize(n, pl))
+    return fail(nullptr, WFFT_EUNSUPPORTED,
+                "axis lengths must be 1..2048 with prime factors 2, 3, 5, 7 and at most one other prime, up to 127");
+  for (int r = 0; r < 7; ++r) cnt[r] = pl.cnt[r];
+  *prime = pl.prime;
+  return WFFT_OK;
+}
+
 namespace {
 template <typename T>
 int set_radix_plan(wfft_handle* h, Plan<T>& P, int axis, const AxisPlan& pl) {

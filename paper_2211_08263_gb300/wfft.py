@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
     lib.wfft_download_async.argtypes = [vp, vp, vp, vp]
     lib.wfft_download_wait.argtypes = [vp]
     lib.wfft_operator_bound.argtypes = [i, P(i), P(d), vp, vp, C.c_longlong, d, P(d)]
+    lib.wfft_axis_plan.argtypes = [i, P(i), P(i)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
     lib.wfft_model_bytes.argtypes = [i]
     lib.wfft_model_bytes.restype = C.c_size_t
@@ -543,6 +544,15 @@ def operator_bound(ndim: int, n, h, C_table: np.ndarray, rho: np.ndarray, theta:
     _raise_global(load().wfft_operator_bound(int(ndim), nn, hh, _ptr(Ct), _ptr(r), Ct.shape[0], float(theta),
                                              C.byref(out)))
     return out.value
+
+
+def axis_plan(n: int):
+    """Built-in FFT decomposition of an axis of n points (wfft_axis_plan): (stage counts of
+    radix 8, 4, 2, 3, 5, 7, 16, prime factor above 7 taken by the direct stage or 0)."""
+    cnt = (C.c_int * 7)()
+    prime = C.c_int()
+    _raise_global(load().wfft_axis_plan(int(n), cnt, C.byref(prime)))
+    return list(cnt), prime.value
 
 
 def explicit_dt(ndim: int, h, C_table: np.ndarray, rho: np.ndarray) -> float:

@@ -179,3 +179,32 @@ def test_operator_bound_homogeneous_isotropic_closed_form(lib):
     expect = rho + th * (3 * lam_ + 2 * mu) * xi2
     got = wfft.operator_bound(3, n, h, Cv, np.array([rho]), th)
     assert abs(got - expect) <= 1e-12 * expect, (got, expect)
+
+
+@pytest.mark.parametrize("n,cnt,prime", [
+    (256, [2, 1, 0, 0, 0, 0, 0], 0),    # 8 8 4
+    (129, [0, 0, 0, 1, 0, 0, 0], 43),   # 3 x 43: the paper's spherical-wave grid
+    (1025, [0, 0, 0, 0, 2, 0, 0], 41),  # 5^2 x 41: the paper's plate grid
+    (176, [0, 2, 0, 0, 0, 0, 0], 11),   # 2^4 (as 4 x 4) x 11
+    (127, [0, 0, 0, 0, 0, 0, 0], 127),  # the largest direct stage
+    (567, [0, 0, 0, 4, 0, 1, 0], 0),    # 3^4 x 7: the paper's polycrystal bar
+    (1, [0, 0, 0, 0, 0, 0, 0], 0)])
+def test_axis_plan_factorizes_with_one_prime_stage(lib, n, cnt, prime):
+    """wfft_axis_plan (host only): the built-in decomposition multiplies back to n, with at
+    most one prime factor above 7 as the direct stage."""
+    from paper_2211_08263_gb300 import wfft
+    got, p = wfft.axis_plan(n)
+    assert (got, p) == (cnt, prime)
+    rad = [8, 4, 2, 3, 5, 7, 16]
+    assert int(np.prod([r ** c for r, c in zip(rad, got)])) * max(p, 1) == n
+
+
+@pytest.mark.parametrize("n", [143, 262, 11 * 11, 2049, 0, 6561])
+def test_axis_plan_refuses_unsupported_lengths(lib, n):
+    """Two prime factors above 7 (143 = 11 x 13, 121 = 11^2), one above 127 (262 = 2 x 131),
+    and lengths outside 1..2048 (6561 = 3^8, the paper's 1-D bar) are refused."""
+    from paper_2211_08263_gb300 import wfft
+    with pytest.raises(wfft.WfftError) as e:
+        wfft.axis_plan(n)
+    assert e.value.code == wfft.EUNSUPPORTED
+
