@@ -1,7 +1,8 @@
 """Grouped steps of uneven grids (wfft_batch_step): one launch per pass over
 all unconverged instances must give the same states as stepping each handle on
-its own (and as the FP64 oracle), in FP64 and mixed precision; an instance that
-fails does not commit while the others do."""
+its own (and as the FP64 oracle), in FP64 and mixed precision, also with axes that
+have a prime factor above 7; an instance that fails does not commit while the
+others do."""
 import numpy as np
 import pytest
 
@@ -11,6 +12,8 @@ from tests.gpu_util import oracle_field, rel, solver_lib, torch_cuda
 pytestmark = pytest.mark.gpu
 
 SIZES = [(16, 16, 16), (24, 20, 12), (20, 16, 24), (32, 24, 16)]
+# axes with a prime factor above 7 (direct prime-length stage), per instance
+PRIME_SIZES = [(22, 13, 12), (43, 16, 6), (16, 11, 26)]
 
 
 def _problems(seed, nsteps=4, sizes=SIZES):
@@ -23,12 +26,13 @@ def _problems(seed, nsteps=4, sizes=SIZES):
     return probs
 
 
+@pytest.mark.parametrize("sizes", [SIZES, PRIME_SIZES], ids=["smooth", "prime"])
 @pytest.mark.parametrize("precision,tol,bar", [(0, 1e-12, 1e-10), (1, 1e-10, 1e-6)])
-def test_batched_steps_match_single_steps_and_oracle(precision, tol, bar):
+def test_batched_steps_match_single_steps_and_oracle(precision, tol, bar, sizes):
     from oracle import newmark
     torch_cuda()
     wfft = solver_lib()
-    probs = _problems(5)
+    probs = _problems(5, sizes=sizes)
     opt = lambda: wfft.default_options(precision=precision, tol=tol)
     grouped = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
     single = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
