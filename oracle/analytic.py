@@ -57,6 +57,39 @@ def dalembert_periodic(x: np.ndarray, t: float, x0: float, c0: float, L: float, 
     return Ufun(t - s / c0) + Ufun(t - (L - s) / c0)
 
 
+def layered_dalembert_periodic(x: np.ndarray, t: float, bounds, c, Z, Ufun) -> np.ndarray:
+    """Displacement of a periodic layered bar [bounds[0], bounds[-1]) driven at x = bounds[0]
+    (= bounds[-1]) by u(0, t) = U(t), by superposing d'Alembert waves (App. C, Eq.
+    soL_wave_eq) ray by ray: layer k spans [bounds[k], bounds[k+1]) with speed c[k] and
+    impedance Z[k].  A wave leaves the source both ways; at an interface it splits into a
+    reflected and a transmitted wave with the amplitude ratios of App. C (Eq.
+    wave_transmission_reflection); at the source point, held at U(t) = 0 once the pulse has
+    passed, it reflects with ratio -1.  Waves whose front reaches a boundary after t are not
+    split further.  U must vanish for negative arguments."""
+    x = np.asarray(x, dtype=np.float64)
+    nl = len(c)
+    L = bounds[-1]
+    u = np.zeros_like(x)
+    # each wave: amplitude, direction (+1 right), layer, the point and time its front leaves
+    waves = [(1.0, +1, 0, bounds[0], 0.0), (1.0, -1, nl - 1, L, 0.0)]
+    while waves:
+        a, d, k, xs, ts = waves.pop()
+        lo, hi = bounds[k], bounds[k + 1]
+        ahead = (x >= lo) & (x < hi) & ((x - xs) * d >= 0)
+        u[ahead] += a * Ufun(t - ts - np.abs(x[ahead] - xs) / c[k])
+        xe = hi if d > 0 else lo
+        th = ts + abs(xe - xs) / c[k]
+        if th > t:
+            continue
+        if (d > 0 and k == nl - 1) or (d < 0 and k == 0):
+            waves.append((-a, -d, k, xe, th))  # the source point
+            continue
+        r, tr = reflection_transmission(Z[k], Z[k + d])
+        waves.append((a * r, -d, k, xe, th))
+        waves.append((a * tr, d, k + d, xe, th))
+    return u
+
+
 def reflection_transmission(Z1: float, Z2: float):
     """Amplitude ratios of a displacement wave from medium 1 into medium 2 (App. C):
     A_T / A_I = 2 / (1 + Z2/Z1),  A_R / A_I = (1 - Z2/Z1) / (1 + Z2/Z1)."""
