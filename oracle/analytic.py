@@ -12,7 +12,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   (Eq. wave_velocity-nd).
 * Cubic-crystal speeds along [100], [110], [111] (textbook).
 * 1-D d'Alembert solution with periodic images and reflection /
-  transmission coefficients at an interface (App. C).
+  transmission coefficients at an interface (App. C), and the layered bar's
+  solution built from them wave by wave (pinned by the homogeneous closed form
+  and by the interface conditions of Eq. wave_boundary).
 """
 from __future__ import annotations
 
