@@ -1,0 +1,113 @@
+"""Mistakes planted in the FP64 oracle, on the CPU, must fail its pins.
+
+Each case replaces one function of the oracle's spectral operator (Eq. Fourier_ND_A) or
+preconditioner (Eq. precond) by a copy with one plausible slip -- a dropped factor or
+term, a wrong sign, a wrong index -- and runs a few fast pins of tests/test_oracle_pins.py
+against it: at least one must fail.  The pins compare the oracle with things outside it
+(the dense operator assembled from the closed-form differentiation matrix, the exact
+inverse of a homogeneous medium, the discrete Newmark phase of a plane wave), so this
+checks that they would notice.  CPU only."""
+import numpy as np
+import pytest
+
+from oracle import spectral
+from tests import test_oracle_pins as pins
+
+
+def _strain_no_half(sp, u):
+    d = sp.d
+    uh = [sp.fwd(u[l]) for l in range(d)]
+    eps = np.empty((d, d) + sp.shape)
+    for l in range(d):
+        for m in range(d):
+            eps[l, m] = sp.inv(1j * (uh[l] * sp.xi[m] + uh[m] * sp.xi[l]))  # the 1/2 dropped
+    return eps
+
+
+def _divergence_sign(sp, sig):
+    d = sp.d
+    t = np.empty((d,) + sp.shape)
+    for j in range(d):
+        acc = np.zeros(sp.hshape, dtype=np.complex128)
+        for k in range(d):
+            acc -= 1j * sp.xi[k] * sp.fwd(sig[j, k])  # sign flipped
+        t[j] = sp.inv(acc)
+    return t
+
+
+def _divergence_index(sp, sig):
+    d = sp.d
+    t = np.empty((d,) + sp.shape)
+    for j in range(d):
+        acc = np.zeros(sp.hshape, dtype=np.complex128)
+        for k in range(d):
+            acc += 1j * sp.xi[j] * sp.fwd(sig[j, k])  # xi_j instead of xi_k
+        t[j] = sp.inv(acc)
+    return t
+
+
+def _hooke_swapped(med, eps):
+    d = med.d
+    e = eps.reshape(d, d, -1)
+    C = med.Ctab[med.phase.reshape(-1)]
+    return np.einsum("vikjl,klv->ijv", C, e).reshape(eps.shape)  # C_ikjl instead of C_ijkl
+
+
+def _apply_A_no_mass(med, sp, u, theta):
+    return -theta * spectral.divergence(sp, spectral.hooke(med, spectral.strain(sp, u)))  # rho u dropped
+
+
+def _acoustic_transposed(sp, Cbar):
+    d = sp.d
+    xi = [np.broadcast_to(sp.xi[k], sp.hshape) for k in range(d)]
+    K = np.zeros(sp.hshape + (d, d))
+    for i in range(d):
+        for j in range(d):
+            for k in range(d):
+                for m in range(d):
+                    K[..., i, j] += Cbar[i, j, k, m] * xi[k] * xi[m]  # C_ijkm instead of C_ikjm
+    return K
+
+
+_ORIG_APPLY_M = spectral.apply_M
+
+
+def _apply_M_no_theta(med, sp, r, theta, Cbar=None, rhobar=None):
+    # theta folded away: (K + rho_bar I)^-1, i.e. theta = 1
+    return _ORIG_APPLY_M(med, sp, r, 1.0, Cbar, rhobar)
+
+
+MUTATIONS = {
+    "strain without 1/2": ("strain", _strain_no_half),
+    "divergence sign": ("divergence", _divergence_sign),
+    "divergence index": ("divergence", _divergence_index),
+    "Hooke indices swapped": ("hooke", _hooke_swapped),
+    "mass term dropped": ("apply_A", _apply_A_no_mass),
+    "acoustic tensor transposed": ("acoustic_tensor", _acoustic_transposed),
+    "preconditioner without theta": ("apply_M", _apply_M_no_theta),
+}
+
+PINS = [
+    lambda: pins.test_fft_operator_equals_dense_operator(*pins.CASES[0]),
+    lambda: pins.test_fft_operator_equals_dense_operator(*pins.CASES[-1]),
+    lambda: pins.test_preconditioner_is_exact_inverse_for_homogeneous_medium(3, True),
+    lambda: pins.test_plane_wave_follows_discrete_newmark_closed_form(3, True, 0),
+]
+
+
+def test_pins_pass_on_the_unchanged_oracle():
+    for pin in PINS:
+        pin()
+
+
+@pytest.mark.parametrize("name", list(MUTATIONS))
+def test_planted_mistake_fails_a_pin(monkeypatch, name):
+    attr, bad = MUTATIONS[name]
+    monkeypatch.setattr(spectral, attr, bad)
+    failed = 0
+    for pin in PINS:
+        try:
+            pin()
+        except (AssertionError, np.linalg.LinAlgError, ValueError, FloatingPointError):
+            failed += 1
+    assert failed >= 1, f"no pin noticed: {name}"
