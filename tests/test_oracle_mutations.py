@@ -1,16 +1,16 @@
 """Mistakes planted in the FP64 oracle, on the CPU, must fail its pins.
 
-Each case replaces one function of the oracle's spectral operator (Eq. Fourier_ND_A) or
-preconditioner (Eq. precond) by a copy with one plausible slip -- a dropped factor or
-term, a wrong sign, a wrong index -- and runs a few fast pins of tests/test_oracle_pins.py
-against it: at least one must fail.  The pins compare the oracle with things outside it
+Each case replaces one function of the oracle's spectral operator (Eq. Fourier_ND_A),
+preconditioner (Eq. precond) or Newmark update (Eq. Newmark) by a copy with one plausible
+slip -- a dropped factor or term, a wrong sign, a wrong index -- and runs a few fast pins
+of tests/test_oracle_pins.py against it: at least one must fail.  The pins compare the oracle with things outside it
 (the dense operator assembled from the closed-form differentiation matrix, the exact
 inverse of a homogeneous medium, the discrete Newmark phase of a plane wave), so this
 checks that they would notice.  CPU only."""
 import numpy as np
 import pytest
 
-from oracle import spectral
+from oracle import newmark, spectral
 from tests import test_oracle_pins as pins
 
 
@@ -77,6 +77,29 @@ def _apply_M_no_theta(med, sp, r, theta, Cbar=None, rhobar=None):
     return _ORIG_APPLY_M(med, sp, r, 1.0, Cbar, rhobar)
 
 
+def _predictor_sign(self, s):
+    ut = s.u + self.dt * s.v + self.dt * self.dt * (0.5 + self.beta) * s.a  # + beta instead of - beta
+    return ut, self.med.rho[None] * ut
+
+
+def _corrector_no_old_acceleration(self, s, x, ut):
+    a_new = (x - ut) / self.theta
+    v_new = s.v + self.dt * self.gamma * a_new  # the (1 - gamma) a_{n-1} term dropped
+    return newmark.State(x, v_new, a_new)
+
+
+def _corrector_without_beta(self, s, x, ut):
+    a_new = (x - ut) / (self.dt * self.dt)  # dt^2 instead of beta dt^2
+    v_new = s.v + self.dt * ((1.0 - self.gamma) * s.a + self.gamma * a_new)
+    return newmark.State(x, v_new, a_new)
+
+
+NEWMARK_MUTATIONS = {
+    "predictor sign": ("predictor", _predictor_sign),
+    "corrector drops the old acceleration": ("corrector", _corrector_no_old_acceleration),
+    "corrector without beta": ("corrector", _corrector_without_beta),
+}
+
 MUTATIONS = {
     "strain without 1/2": ("strain", _strain_no_half),
     "divergence sign": ("divergence", _divergence_sign),
@@ -95,19 +118,37 @@ PINS = [
 ]
 
 
+NEWMARK_PINS = [
+    lambda: pins.test_plane_wave_follows_discrete_newmark_closed_form(3, True, 0),
+    lambda: pins.test_plane_wave_follows_discrete_newmark_closed_form(2, False, 1),
+    pins.test_energy_conserved_in_free_vibration,
+]
+
+
+def _failures(pins_):
+    failed = 0
+    for pin in pins_:
+        try:
+            pin()
+        except (AssertionError, np.linalg.LinAlgError, ValueError, FloatingPointError):
+            failed += 1
+    return failed
+
+
 def test_pins_pass_on_the_unchanged_oracle():
-    for pin in PINS:
+    for pin in PINS + NEWMARK_PINS:
         pin()
+
+
+@pytest.mark.parametrize("name", list(NEWMARK_MUTATIONS))
+def test_planted_newmark_mistake_fails_a_pin(monkeypatch, name):
+    attr, bad = NEWMARK_MUTATIONS[name]
+    monkeypatch.setattr(newmark.NewmarkOracle, attr, bad)
+    assert _failures(NEWMARK_PINS) >= 1, f"no pin noticed: {name}"
 
 
 @pytest.mark.parametrize("name", list(MUTATIONS))
 def test_planted_mistake_fails_a_pin(monkeypatch, name):
     attr, bad = MUTATIONS[name]
     monkeypatch.setattr(spectral, attr, bad)
-    failed = 0
-    for pin in PINS:
-        try:
-            pin()
-        except (AssertionError, np.linalg.LinAlgError, ValueError, FloatingPointError):
-            failed += 1
-    assert failed >= 1, f"no pin noticed: {name}"
+    assert _failures(PINS) >= 1, f"no pin noticed: {name}"
