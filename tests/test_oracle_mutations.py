@@ -1,7 +1,8 @@
 """Mistakes planted in the FP64 oracle, on the CPU, must fail its pins.
 
 Each case replaces one function of the oracle's spectral operator (Eq. Fourier_ND_A),
-preconditioner (Eq. precond) or Newmark update (Eq. Newmark) by a copy with one plausible
+preconditioner (Eq. precond), Newmark update (Eq. Newmark) or masked conjugate gradient
+(Sec. 2.2.3) by a copy with one plausible
 slip -- a dropped factor or term, a wrong sign, a wrong index -- and runs a few fast pins
 of tests/test_oracle_pins.py against it: at least one must fail.  The pins compare the oracle with things outside it
 (the dense operator assembled from the closed-form differentiation matrix, the exact
@@ -10,7 +11,7 @@ checks that they would notice.  CPU only."""
 import numpy as np
 import pytest
 
-from oracle import newmark, spectral
+from oracle import newmark, pcg, spectral
 from tests import test_oracle_pins as pins
 
 
@@ -94,6 +95,40 @@ def _corrector_without_beta(self, s, x, ut):
     return newmark.State(x, v_new, a_new)
 
 
+def _pcg(project_q=True, beta_inverted=False):
+    """The masked PCG with one slip switched on (else the same steps as oracle.pcg)."""
+    def run(Aop, Mop, b, x0, mask, xgam, tol, maxit=1000):
+        P = lambda v: np.where(mask, 0.0, v)
+        x = np.where(mask, xgam, x0)
+        x_g = np.where(mask, xgam, 0.0)
+        ref = np.sqrt(pcg.dot(P(b - Aop(x_g)), P(b - Aop(x_g))))
+        if ref == 0.0:
+            return x_g, {"iters": 0, "ref": 0.0, "rel_res": 0.0, "converged": True}
+        r = P(b - Aop(x))
+        z = P(Mop(r))
+        p = z.copy()
+        rz = pcg.dot(r, z)
+        it, rn = 0, np.sqrt(pcg.dot(r, r))
+        while it < maxit and rn > tol * ref:
+            q = P(Aop(p)) if project_q else Aop(p)
+            alpha = rz / pcg.dot(p, q)
+            x = x + alpha * p
+            r = r - alpha * q
+            it += 1
+            rn = np.sqrt(pcg.dot(r, r))
+            z = P(Mop(r))
+            rz_new = pcg.dot(r, z)
+            p = z + (rz / rz_new if beta_inverted else rz_new / rz) * p
+            rz = rz_new
+        return x, {"iters": it, "ref": ref, "rel_res": rn / ref, "converged": rn <= tol * ref}
+    return run
+
+
+PCG_MUTATIONS = {
+    "A p not projected": _pcg(project_q=False),
+    "beta inverted": _pcg(beta_inverted=True),
+}
+
 NEWMARK_MUTATIONS = {
     "predictor sign": ("predictor", _predictor_sign),
     "corrector drops the old acceleration": ("corrector", _corrector_no_old_acceleration),
@@ -135,9 +170,27 @@ def _failures(pins_):
     return failed
 
 
+PCG_PINS = [
+    lambda: pins.test_green_matrix_masked_pcg_and_dense_agree(2, (8, 8, 1), 2),
+    lambda: pins.test_green_matrix_masked_pcg_and_dense_agree(3, (6, 6, 6), 1),
+]
+
+
 def test_pins_pass_on_the_unchanged_oracle():
-    for pin in PINS + NEWMARK_PINS:
+    for pin in PINS + NEWMARK_PINS + PCG_PINS:
         pin()
+
+
+def test_unchanged_copy_of_the_pcg_passes_the_pins(monkeypatch):
+    """The copy used for the PCG mutations, with no slip, is the oracle's algorithm."""
+    monkeypatch.setattr(newmark, "masked_pcg", _pcg())
+    assert _failures(PCG_PINS) == 0
+
+
+@pytest.mark.parametrize("name", list(PCG_MUTATIONS))
+def test_planted_pcg_mistake_fails_a_pin(monkeypatch, name):
+    monkeypatch.setattr(newmark, "masked_pcg", PCG_MUTATIONS[name])
+    assert _failures(PCG_PINS) >= 1, f"no pin noticed: {name}"
 
 
 @pytest.mark.parametrize("name", list(NEWMARK_MUTATIONS))
