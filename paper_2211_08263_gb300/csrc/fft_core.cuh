@@ -276,6 +276,9 @@ __device__ __forceinline__ void fft_stage(cplx<T>* buf, int N, int nlines, int l
 // for P >= 11.
 constexpr int kPrimeBatch = 16;
 constexpr int kPrimeTasks = 9;
+// a tile of kPrimeBatch * threads elements holds kPrimeBatch (P + 1) / (2 P) pairs per
+// thread, largest for the smallest prime P = 11
+static_assert(kPrimeTasks * 2 * 11 >= kPrimeBatch * (11 + 1), "prime-stage task batch too small for its tiles");
 
 // General prime-length stage for the one prime factor P > 7 of an axis, run first
 // (Ns = 1, no inter-stage twiddles): with n = N / P butterflies per line, output q of
