@@ -345,6 +345,36 @@ def test_material_table_follows_the_isotropic_closed_forms():
         assert abs(analytic.isotropic_speeds(lam0, mu0, rho)[0] - c0_p) <= 0.1
 
 
+def test_plane_strain_strip_with_nu_zero_equals_the_1d_bar():
+    """A 2-D plane-strain strip of N x 2 voxels with nu = 0 (lambda = 0, C11 = E), loaded
+    uniformly across its width on the x_idx = 0 column, takes the same Newmark steps as the
+    1-D bar of Sec. 3.1: for y-uniform fields the spectral y derivative vanishes, so the
+    strip's operator reduces to the bar's -E theta D_x^2 + rho.  (The GPU runs Table 2's bar
+    in this form.)"""
+    E, rho = MATERIALS["Aluminium"]
+    L, N = 2.0, 243
+    c0 = np.sqrt(E / rho)
+    dt = 10 * (L / N) / c0
+    nsteps = 40
+    Uf = lambda t: inputs.bell_pulse(t, 1e-3, 5 * np.pi * c0 / L, 4)
+    U = np.zeros((nsteps, 3))
+    U[:, 0] = Uf(dt * np.arange(1, nsteps + 1))
+    med1 = medium.Medium(1, (N,), (L,), np.full((1, 1, 1, 1, 1), E), np.zeros(N, np.int64), np.full(N, rho))
+    mask1 = np.zeros((1, N), bool)
+    mask1[0, 0] = True
+    s1, _ = newmark.NewmarkOracle(med1, mask1, dt, tol=1e-13).run(U)
+    h = L / N
+    C = inputs.voigt21_from_matrix(inputs.isotropic_voigt(E, 0.0))[None, :]
+    mask = np.zeros((2, 1, 2, N), np.uint8)
+    mask[:, :, :, 0] = 1
+    strip = inputs.Problem("strip", 2, (N, 2, 1), (h, h, h), dt, 0.25, 0.5, C, np.array([rho]),
+                           np.zeros((1, 2, N), np.uint16), mask, U, tol=1e-13)
+    s2, _ = newmark.oracle_from_problem(strip, tol=1e-13).run(U)
+    # oracle 2-D fields are [c][N2][N1]
+    assert rel(s2.u[0, 0], s1.u[0]) < 1e-11 and rel(s2.u[0, 1], s1.u[0]) < 1e-11
+    assert np.abs(s2.u[1]).max() <= 1e-14 * np.abs(s1.u[0]).max()
+
+
 def _layers(middle, bounds):
     E = [MATERIALS[m][0] for m in ("Aluminium", middle, "Aluminium")]
     rho = [MATERIALS[m][1] for m in ("Aluminium", middle, "Aluminium")]
