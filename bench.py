@@ -12,8 +12,13 @@ FP64 true-residual refinement, FP64 state; warm start = Taylor extrapolation
 plus the BF16 network's correction, trained on the GPU beforehand -- untimed --
 on 2000 step pairs of new-seed polycrystal runs at 48^3); the plain FP64
 solve, the mixed solve from u_{n-1} and the mixed solve from the Taylor
-extrapolation alone are measured beside it.  Timed with CUDA events on the solver's stream after `--warmup` untimed
-steps; every field is >= 64 MB, so the working set of each pass exceeds L2.
+extrapolation alone are measured beside it.  The mixed forms run every step of the
+400-step pulse; the timed region (`--steps` K steps, CUDA events on the solver's stream,
+a device synchronisation on both sides) is the window centred on the pulse's peak
+(step 200), after `--warmup` untimed steps; per-window figures (onset, peak, tail) and
+whole-run iterations per step are reported beside it.  Plain FP64 runs the same three
+windows from states the first form kept.  Every field is >= 64 MB, so the working set
+of each pass exceeds L2.
 
 `--impl reference` times the FP64 CPU oracle (the plain NumPy/SciPy restatement of
 the method that the tests check the GPU path against) on the host cores: one oracle
@@ -50,6 +55,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid edge (the workload is 256)")
+    ap.add_argument("--nsteps", type=int, default=400, help="steps of the pulse (the workload is 400)")
+    ap.add_argument("--fp64-whole", action="store_true",
+                    help="run every step of the pulse in FP64 too (default: its three windows only)")
     ap.add_argument("--modes", default="learned,mixed,taylor,fp64",
                     help="learned = mixed + learned warm start, taylor = mixed + Taylor warm start, "
                          "mixed = mixed from u_{n-1}, fp64 = plain FP64 from u_{n-1}")
@@ -63,6 +71,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default FFT plans (no wfft_autotune)")
     ap.add_argument("--no-explicit", action="store_true", help="skip the explicit-scheme measurement")
     ap.add_argument("--no-sphere", action="store_true", help="skip the 129^3 sphere (prime-length stage) measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 48-instance uneven batch")
+    ap.add_argument("--batch-inst", type=int, default=48, help="instances of the uneven batch")
     ap.add_argument("--plan", default=None,
                     help="plan choices to apply instead of autotuning: a JSON file, or the JSON text itself")
     ap.add_argument("--save-plan", default=None, help="write the plan choices of the timed handles (JSON)")
@@ -241,7 +251,27 @@ NO_INCR = False     # --no-incr-resid: full FP64 residuals only
 XELEMS = None       # --xelems: x-pass tile size set after tuning
 
 
-def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None, autotune=True):
+def windows(nsteps, W, K):
+    """Timed windows of K steps, each after W untimed warm-up steps: the pulse's onset
+    (right after the first W steps), its peak (centred on the Gaussian's centre, step 200 of
+    400) and its tail (the last K steps).  Steps are numbered from 1."""
+    peak0 = max(W + 1, min(nsteps - K + 1, nsteps // 2 - K // 2 + 1))
+    return {"onset": (W + 1, W + K), "peak": (peak0, peak0 + K - 1), "tail": (nsteps - K + 1, nsteps)}
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=None, autotune=True,
+             whole=True, states=None):
+    """One solver form on the pulse.  whole=True: every step of the pulse is run, each timed with
+    CUDA events on the solver's stream; the headline region is the K steps of the peak window
+    after its W warm-up steps, bracketed by a device synchronisation (and a barrier across
+    ranks) on both sides; the per-launch profile is taken on the PROF_STEPS steps after it
+    (their times are left out of the per-window figures).  States at the start of each
+    window's warm-up are kept in `states` (device copies) for forms that run windows only.
+    whole=False: each window runs from the kept state, W warm-up steps then K timed steps."""
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     _, prec, warm = MODES[mode]
@@ -275,61 +305,145 @@ def run_mode(wfft, torch, prob, mode, blob, W, K, world, e2e: bool, inner_tol=No
             s.set_plan(pr, pl)
     for pr in precs:
         PLANS_USED["fp64" if pr == wfft.FP64 else "fp32"] = s.get_plan(pr)
-    for n in range(W):
-        s.step(prob.U[n])
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    l0 = s.launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    infos = []
-    ev0.record(stream)
-    for n in range(W, W + K):
-        infos.append(s.step(prob.U[n]))
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches = s.launch_count() - l0
-    # per-kernel CUDA-event times (for the kernel table and the roofline) on the steps
-    # after the timed ones: event pairs around every launch would perturb the timed region
-    s.profile(True)
-    for n in range(W + K, W + K + PROF_STEPS):
-        s.step(prob.U[n])
-    prof = s.profile_read()
-    s.profile(False)
-    res = {"ms_total": ms, "iters": sum(i["iters"] for i in infos),
-           "outer_applies": sum(i["outer_applies"] for i in infos),
-           "sweeps": sum(i["sweeps"] for i in infos), "rel_res_max": max(i["rel_res"] for i in infos),
-           "incr_resids": sum(i["incr_resids"] for i in infos),
-           "launches": launches, "profile": prof, "iters_per_step": [i["iters"] for i in infos],
-           "autotune_changed": tuned}
+    nsteps = prob.nsteps
+    wins = windows(nsteps, W, K)
+    t0, t1 = wins["peak"]
+    shape = s.shape
+    per_ms, per_it, infos_all = {}, {}, {}
+    res = {"autotune_changed": tuned}
+
+    def timed_region(first, last):
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = s.launch_count()
+        ev0, ev1 = _events(torch)
+        infos = []
+        ev0.record(stream)
+        for n in range(first, last + 1):
+            infos.append(s.step(prob.U[n - 1]))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return ev0.elapsed_time(ev1), infos, s.launch_count() - l0
+
+    def keep_state(n):
+        if states is not None and n not in states:
+            u = torch.empty(shape, dtype=torch.float64, device="cuda")
+            v, a = torch.empty_like(u), torch.empty_like(u)
+            s.get_state_dev(u, v, a)
+            states[n] = (u, v, a)
+
+    prof_steps = set(range(t1 + 1, min(nsteps, t1 + PROF_STEPS) + 1))
+    if whole:
+        starts = {w[0] - W - 1 for w in wins.values()}
+        n = 1
+        evs = {}
+        while n <= nsteps:
+            if n - 1 in starts:
+                keep_state(n - 1)
+            if n == t0 - W:
+                # warm-up of the headline window, then the timed region
+                for k in range(n, t0):
+                    e0, e1 = _events(torch)
+                    e0.record(stream)
+                    infos_all[k] = s.step(prob.U[k - 1])
+                    e1.record(stream)
+                    evs[k] = (e0, e1)
+                ms, infos, launches = timed_region(t0, t1)
+                for k, inf in zip(range(t0, t1 + 1), infos):
+                    infos_all[k] = inf
+                    per_ms[k] = ms / K
+                res.update({"ms_total": ms, "iters": sum(i["iters"] for i in infos), "launches": launches,
+                            "outer_applies": sum(i["outer_applies"] for i in infos),
+                            "sweeps": sum(i["sweeps"] for i in infos),
+                            "rel_res_max": max(i["rel_res"] for i in infos),
+                            "incr_resids": sum(i["incr_resids"] for i in infos),
+                            "iters_per_step": [i["iters"] for i in infos]})
+                n = t1 + 1
+                # per-kernel CUDA-event times (kernel table, roofline) on the steps after the
+                # timed ones: event pairs around every launch would perturb the timed region
+                s.profile(True)
+                for k in sorted(prof_steps):
+                    infos_all[k] = s.step(prob.U[k - 1])
+                res["profile"] = s.profile_read()
+                s.profile(False)
+                n = max(prof_steps) + 1 if prof_steps else n
+                continue
+            e0, e1 = _events(torch)
+            e0.record(stream)
+            infos_all[n] = s.step(prob.U[n - 1])
+            e1.record(stream)
+            evs[n] = (e0, e1)
+            n += 1
+        torch.cuda.synchronize()
+        for k, (e0, e1) in evs.items():
+            per_ms[k] = e0.elapsed_time(e1)
+        for k, inf in infos_all.items():
+            per_it[k] = inf["iters"]
+        out_w = {}
+        for name, (a, b) in wins.items():
+            ks = [k for k in range(a, b + 1) if k in per_ms]
+            out_w[name] = {"steps": [a, b], "ms_per_step": sum(per_ms[k] for k in ks) / len(ks) if ks else None,
+                           "krylov_iters_per_step": sum(per_it[k] for k in range(a, b + 1)) / (b - a + 1)}
+        ks = [k for k in per_ms if k not in prof_steps]
+        res["windows"] = out_w
+        res["whole_run"] = {"steps": nsteps, "ms_per_step": sum(per_ms[k] for k in ks) / len(ks),
+                            "krylov_iters_per_step": sum(per_it.values()) / len(per_it),
+                            "fp64_applies_per_step": sum(i["outer_applies"] for i in infos_all.values()) / nsteps,
+                            "max_rel_res": max(i["rel_res"] for i in infos_all.values()),
+                            "note": "every step of the pulse; the profiled steps' times left out"}
+    else:
+        out_w = {}
+        for name, (a, b) in wins.items():
+            u, v, a_ = states[a - W - 1]
+            s.set_state_dev(u, v, a_, a - W - 1)
+            for k in range(a - W, a):
+                s.step(prob.U[k - 1])
+            ms, infos, launches = timed_region(a, b)
+            out_w[name] = {"steps": [a, b], "ms_per_step": ms / K,
+                           "krylov_iters_per_step": sum(i["iters"] for i in infos) / K}
+            if name == "peak":
+                res.update({"ms_total": ms, "iters": sum(i["iters"] for i in infos), "launches": launches,
+                            "outer_applies": sum(i["outer_applies"] for i in infos),
+                            "sweeps": sum(i["sweeps"] for i in infos),
+                            "rel_res_max": max(i["rel_res"] for i in infos),
+                            "incr_resids": sum(i["incr_resids"] for i in infos),
+                            "iters_per_step": [i["iters"] for i in infos]})
+                s.profile(True)
+                for k in range(b + 1, min(nsteps, b + PROF_STEPS) + 1):
+                    s.step(prob.U[k - 1])
+                res["profile"] = s.profile_read()
+                s.profile(False)
+        res["windows"] = out_w
     if e2e:
-        # end to end through the C ABI: U(t_n) from host memory in, the displacement
-        # field u_n copied back to pinned host memory after every step
+        # end to end through the C ABI over the headline window: U(t_n) from host memory in,
+        # the displacement field u_n copied back to pinned host memory after every step
         host_u = torch.empty((2,) + tuple(s.shape), dtype=torch.float64, pin_memory=True).numpy()
         s2 = make()
         for pr in precs:
             s2.set_plan(pr, PLANS_USED["fp64" if pr == wfft.FP64 else "fp32"])
-        for n in range(W):
-            s2.step(prob.U[n])
+        u, v, a_ = states[t0 - W - 1]
+        s2.set_state_dev(u, v, a_, t0 - W - 1)
+        for n in range(t0 - W, t0):
+            s2.step(prob.U[n - 1])
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        t0 = time.perf_counter()
+        h0 = time.perf_counter()
         it2 = 0
-        for n in range(W, W + K):
-            it2 += s2.step(prob.U[n])["iters"]
+        for n in range(t0, t1 + 1):
+            it2 += s2.step(prob.U[n - 1])["iters"]
             # u_n to pinned host memory on the library's copy stream, overlapping the next
             # step's solve (the next corrector waits for the copy); one buffer per step in
             # flight, so the host reads u_n only after the wait below
-            s2.download_async(host_u[(n - W) % 2])
+            s2.download_async(host_u[(n - t0) % 2])
         s2.download_wait()
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        res["e2e_s"] = t1 - t0
+        h1 = time.perf_counter()
+        res["e2e_s"] = h1 - h0
         res["e2e_iters"] = it2
         res["d2h_bytes"] = int(host_u[0].nbytes)
         s2.close()
@@ -463,6 +577,88 @@ def explicit_scheme(wfft, torch, prob, W, K):
             "note": "explicit central difference (beta 0, gamma 1/2), FP64, prescribed u_x velocity on the slab"}
 
 
+def batch_leg(wfft, torch, rank, world, W, K, ninst=48, nsteps=100):
+    """The batched workload of uneven grids: 48 polycrystal instances of 64^3 ... 192^3 (seeded
+    sizes, 50-800 grains, the 256^3 workload's cubic nickel), Gaussian pulse of sigma 10 dt
+    centred at step 40 on each x-face slab, mixed precision to 1e-10.  Instances are
+    partitioned across ranks by their FFT work (no collective on the data path); each rank
+    steps its instances together (wfft_batch_step: one grouped launch per pass, each
+    instance with its own autotuned radix schedule and column-tile widths, grouped PCG
+    blocks replayed as CUDA graphs).  Timed: K grouped steps centred on the pulse's peak,
+    after the steps before them (untimed), CUDA events on the solvers' stream; value =
+    voxel x Krylov iterations of all instances / slowest rank's time."""
+    import numpy as np
+    from paper_2211_08263_gb300 import batch, inputs
+    specs = inputs.config_c4_specs(ninst)
+    costs = [batch.instance_cost((sz, sz, sz)) for sz, _, _ in specs]
+    mine = batch.partition(costs, world)[rank]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    probs, solvers = [], []
+    for i in mine:
+        sz, ng, seed = specs[i]
+        p = inputs.config_c4_instance(sz, ng, seed, nsteps)
+        sv = wfft.Solver.from_problem(p, options=wfft.default_options(precision=wfft.MIXED, tol=1e-10, maxit=500,
+                                                                      check_every=4),
+                                      stream=stream.cuda_stream)
+        sv.autotune(3)  # timed once per grid size and precision, then taken from the cache
+        probs.append(p)
+        solvers.append(sv)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    first = max(W + 1, 40 - K // 2 + 1)
+    last = min(nsteps, first + K - 1)
+    local = {}
+    ms = 0.0
+    vox_it = 0.0
+    if solvers:
+        Ustep = lambda k: np.stack([p.U[k - 1] for p in probs])  # noqa: E731
+        for k in range(1, first):
+            rc, _ = wfft.batch_step(solvers, Ustep(k))
+            if rc != wfft.OK:
+                raise RuntimeError(f"batched step {k} failed: {rc}")
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if solvers:
+        ev0, ev1 = _events(torch)
+        recs = []
+        ev0.record(stream)
+        for k in range(first, last + 1):
+            rc, infos = wfft.batch_step(solvers, Ustep(k))
+            if rc != wfft.OK:
+                raise RuntimeError(f"batched step {k} failed: {rc}")
+            recs.append(infos)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        for j, i in enumerate(mine):
+            its = [r[j]["iters"] for r in recs]
+            V = probs[j].nvox
+            vox_it += V * sum(its)
+            local[i] = {"size": probs[j].n[0], "iters_per_step": sum(its) / len(its),
+                        "max_rel_res": max(r[j]["rel_res"] for r in recs)}
+    if world > 1:
+        torch.distributed.barrier()
+    ms_all, vox_all = aggregate_over_ranks(ms, vox_it, world, "cuda")
+    allrec = batch.gather_records(local, world)
+    for sv in solvers:
+        sv.close()
+    nk = last - first + 1
+    sizes = sorted({r["size"] for r in allrec.values()})
+    return {"workload": f"{ninst} polycrystals of {min(sizes)}^3..{max(sizes)}^3 (seeded sizes from "
+                        "64, 80, 96, 128, 144, 160, 192; 50-800 grains), sigma 10 dt pulse centred at step 40, "
+                        "mixed, tol 1e-10",
+            "instances": len(allrec), "ranks": world, "voxels": int(sum(s ** 3 for s, _, _ in specs)),
+            "timed_steps": [first, last], "ms_per_step": ms_all / nk,
+            "voxel_iters_per_s": vox_all / (ms_all * 1e-3) if ms_all > 0 else None,
+            "krylov_iters_per_step_mean": float(np.mean([r["iters_per_step"] for r in allrec.values()])),
+            "max_rel_res": max(r["max_rel_res"] for r in allrec.values()),
+            "setup_s": round(setup_s, 1), "scaling": "weak (instances partitioned by FFT work)"}
+
+
 def cpu_oracle_iteration(prob, reps=1):
     """One FP64 oracle PCG iteration (operator + preconditioner + updates) on the workload."""
     import numpy as np
@@ -521,7 +717,7 @@ def main():
     rank, world, local = dist_env()
     from paper_2211_08263_gb300 import inputs
     W, K = args.warmup, args.steps
-    prob = inputs.config_c3(nsteps=W + K + PROF_STEPS, n=args.n, nz=args.nz)
+    prob = inputs.config_c3(nsteps=max(args.nsteps, 2 * (W + K + PROF_STEPS) + K), n=args.n, nz=args.nz)
     if args.impl == "reference":
         return run_reference(args, prob, rank, world)
 
@@ -544,25 +740,36 @@ def main():
         blob, learned = train_warm_start(wfft, args, torch.cuda.current_stream())
     clocks = ClockSampler(local)
     results = {}
-    for m in modes:
+    states = {}
+    # forms whose every step is run: the mixed ones (tens of ms per step); plain FP64 runs the
+    # three windows from the states the first form kept, unless --fp64-whole
+    order = [m for m in modes if m != "fp64" or args.fp64_whole] + [m for m in modes if m == "fp64" and
+                                                                       not args.fp64_whole]
+    for m in order:
         if m == modes[0]:
             clocks.start()
+        whole = m != "fp64" or args.fp64_whole
         results[m] = run_mode(wfft, torch, prob, m, blob, W, K, world, e2e=(m == modes[0] and not args.no_e2e),
-                              inner_tol=args.inner_tol, autotune=not args.no_autotune)
+                              inner_tol=args.inner_tol, autotune=not args.no_autotune, whole=whole,
+                              states=states)
         if m == modes[0]:
             clk = clocks.stop()
+    states.clear()
     head = results[modes[0]]
     ms, iters = aggregate_over_ranks(head["ms_total"], head["iters"], world, "cuda")
     value = whole_job_value(V, iters, ms)
     modes_out = {}
-    for m, r in results.items():
+    for m in modes:
+        r = results[m]
         modes_out[MODES[m][0]] = {"ms_per_step": r["ms_total"] / K, "s_per_step": r["ms_total"] / K / 1e3,
                         "voxel_iters_per_s": V * r["iters"] / (r["ms_total"] * 1e-3),
                         "krylov_iters_per_step": r["iters"] / K, "fp64_applies_per_step": r["outer_applies"] / K,
                         "incr_resids_per_step": r["incr_resids"] / K,
                         "sweeps_per_step": r["sweeps"] / K, "max_rel_res": r["rel_res_max"],
                         "autotune_changed": r["autotune_changed"],
-                        "iters_per_step": r["iters_per_step"]}
+                        "iters_per_step": r["iters_per_step"], "windows": r["windows"]}
+        if "whole_run" in r:
+            modes_out[MODES[m][0]]["whole_run"] = r["whole_run"]
     rl = roofline(head["profile"], V, hbm_peak, peak_kind)
     # DRAM bytes per launch from an ncu capture, used only while the kernel's source
     # files still hash to the captured version
@@ -581,9 +788,13 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [prob.n[0], prob.n[1], prob.n[2]],
                        "mode": MODES[modes[0]][0],
-                       "timed_steps": [W + 1, W + K], "tol": 1e-10,
+                       "timed_steps": list(windows(prob.nsteps, W, K)["peak"]), "tol": 1e-10,
+                       "fp64_ms_per_step": round(results["fp64"]["ms_total"] / K, 2) if "fp64" in results else None,
                        "l2": "inputs larger than L2 (every field >= 64 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
+            "fp64_ms_per_step": results["fp64"]["ms_total"] / K if "fp64" in results else None,
+            "fp64_value": (V * results["fp64"]["iters"] / (results["fp64"]["ms_total"] * 1e-3)
+                           if "fp64" in results else None),
             "modes": modes_out, "roofline": rl,
             "kernels": kernel_table(head["profile"], hbm_peak,
                                     sum(d["ms"] for d in head["profile"].values())),
@@ -603,6 +814,8 @@ def main():
         line["explicit"] = explicit_scheme(wfft, torch, prob, W, K)
     if not args.no_sphere:
         line["sphere129"] = sphere129(wfft, torch)
+    if not args.no_batch:
+        line["batch"] = batch_leg(wfft, torch, rank, world, W, K, ninst=args.batch_inst)
     if "e2e_s" in head:
         line["e2e"] = {"value": V * head["e2e_iters"] * world / head["e2e_s"], "unit": UNIT,
                        "h2d_bytes_per_step": 24, "d2h_bytes_per_step": head["d2h_bytes"],

@@ -108,6 +108,12 @@ typedef struct {
   double reaction[3];  /* sum over the grid of rho a_n per component = total force on Gamma */
   double ms;           /* device time of the call (CUDA events) */
   int incr_resids;     /* mixed: incremental residual evaluations (see wfft_options.incr_resid) */
+  double energy;       /* E_n = 1/2 sum_x rho |v_n|^2 + 1/2 sum_x eps_n : C : eps_n of the committed state
+                          (sums over voxels, no cell volume; the energy of the Newmark energy identity,
+                          Eq. Newmark with beta = 1/4, gamma = 1/2).  Implicit steps form the strain part
+                          from the step's own sums, u.K u = sum_j U_j F_j - sum_x rho u_n . a_n with F_j
+                          the reaction (A u_n = b + theta f, f on Gamma), exact up to the solver residual;
+                          explicit steps from K u_n itself.  0 for a step that is not committed. */
 } wfft_step_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-10, maxit 1000, WARM_PREV, inner_tol 1e-5,
@@ -147,7 +153,8 @@ WFFT_API int wfft_create(const wfft_grid* grid, const double* C, const uint16_t*
 /* Free every device and host resource of the handle (NULL is a no-op). */
 WFFT_API void wfft_destroy(wfft_handle* h);
 
-/* Text of the last error on h (static string if h is NULL). */
+/* Text of the last error on h; with h NULL, of the last failed call without a handle
+   made by the calling host thread. */
 WFFT_API const char* wfft_last_error(const wfft_handle* h);
 
 /* Replace the Newmark state (u_{n}, v_{n}, a_{n}) from host arrays [c][N3][N2][N1] and the
@@ -450,29 +457,36 @@ WFFT_API int wfft_profile_read(wfft_handle* h, int precision, int kind, long lon
 WFFT_API int wfft_launch_count(const wfft_handle* h, long long* launches);
 
 /*
- * Preconditioner application z = M r (Eq. precond with Eq. acous, unmasked),
- * FP64, for callers that cannot allocate device memory -- e.g. a framework
- * that owns every device byte through its own arena once it has started, or
- * code that must not change the device allocation state while other work is
- * in flight.  It needs no handle and performs no cudaMalloc / cudaFree or any
- * other allocating call: its scratch (kernel descriptor, scalars, twiddles,
- * partial sums, spectral work buffer) is one fixed __device__ array of
- * 16.25 MiB in the library, held by every GPU that loads the library until
- * the process exits.  The paper has no counterpart of this call.
+ * Allocation-free preconditioner application: z = M r, FP64, unmasked -- the
+ * same reference-medium preconditioner that wfft_precond applies -- for callers
+ * that cannot allocate device memory: e.g. a framework that owns every device
+ * byte through its own arena once it has started, or code that must not change
+ * the device allocation state while other work is in flight.  It needs no
+ * handle and performs no cudaMalloc / cudaFree or any other allocating call:
+ * its scratch (kernel descriptor, scalars, twiddles, partial sums, spectral
+ * work buffer) is one fixed __device__ array of 16.25 MiB in the library.  The
+ * paper has no counterpart of this call.
  *   grid      : sizes as for wfft_create; c * N3 * N2 * pitch complex doubles must
  *               fit 16 MiB (pitch = N1/2+1 rounded up to 8), e.g. up to 64^3 in 3-D;
  *               larger grids return WFFT_EINVAL without touching the device.
  *   cbar      : 21 Voigt values of the reference stiffness (the volume average
  *               of C(x) for the paper's preconditioner); must be SPD.
  *   rho_bar   : reference density (> 0); theta = beta dt^2 (> 0).
- *   r_dev     : device FP64 [c][N3][N2][N1] input;  z_dev: device FP64 output.
+ *   r_dev     : device FP64 [c][N3][N2][N1] input;  z_dev: device FP64 output;
+ *               both must hold c * N1 * N2 * N3 doubles (the call cannot check this).
  *   stream    : cudaStream_t cast to void* (NULL = legacy default stream).
- * Asynchronous on `stream`.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current) and sets the
- * kernels' shared-memory attributes; make that first call before any stream
- * capture.  All calls share the one scratch array and it keeps the last call's
- * contents: calls that overlap on the GPU (other streams, other host threads)
- * race and must be serialised by the caller.  Errors: wfft_last_error(NULL).
+ * Asynchronous on `stream`.  Module loading: under CUDA's default lazy loading the
+ * library's module, and with it the fixed array, is created on a device by the first
+ * use of the library there (this call's first cudaGetSymbolAddress, or any earlier
+ * launch of the library on that device); a caller whose arena will reserve all free
+ * device memory should make a first call (or any other call of the library) before the
+ * arena reserves it, or set CUDA_MODULE_LOADING=EAGER.  Every call looks up the array's
+ * device address in the current context (cudaGetSymbolAddress, allocation-free once
+ * the module is loaded); the first call in a CUDA context also sets the kernels'
+ * shared-memory attributes, so make it before any stream capture.  All calls share
+ * the one scratch array and it keeps the last call's contents: calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  Errors: wfft_last_error(NULL) on the calling host thread.
  */
 WFFT_API int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21], double rho_bar, double theta,
                                   const double* r_dev, double* z_dev, void* stream);

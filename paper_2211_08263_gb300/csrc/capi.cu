@@ -39,6 +39,11 @@ struct wfft_handle {
   int ndim = 0, c = 0, s = 0;
   int n[3] = {1, 1, 1};
   double h[3] = {1, 1, 1};
+  // 3-D grids with one voxel along x_1 run relabeled, (x_2, x_3, x_1) -> (x_1', x_2', x_3'):
+  // internal component k is the caller's component cmap[k]; n_ext is the caller's grid
+  bool relabeled = false;
+  int cmap[3] = {0, 1, 2};
+  int n_ext[3] = {1, 1, 1};
   long long V = 0;
   double dt = 0, beta = 0, gamma = 0, theta = 0;
   wfft_options opt{};
@@ -60,6 +65,7 @@ struct wfft_handle {
   double lam_max = 0;       // upper bound of the largest eigenvalue of A (incremental residuals)
   double au_bound = 0;      // rounding estimate of SL_AU's latest update (0: full FP64)
   double U_prev[3] = {0, 0, 0};
+  int gam_comp[3] = {0, 0, 0};  // 1: component j has prescribed DOFs (Gamma_j nonempty)
   double cbar[21] = {0};
   double rhobar = 0;
   // CUDA graphs of one block of check_every PCG iterations, per precision (captured lazily)
@@ -94,7 +100,7 @@ struct ProfScope {
   ~ProfScope() { g_prof = prev; }
 };
 
-static std::string g_err;
+static thread_local std::string g_err;  // per host thread: calls without a handle may fail concurrently
 
 namespace wfft {
 // Error text of calls that have no handle (wfft_last_error(NULL)).
@@ -107,6 +113,31 @@ static int fail(wfft_handle* h, int code, const std::string& msg) {
   else
     g_err = msg;
   return code;
+}
+
+// Energy of the committed state (a sum over voxels, no cell volume):
+// E_n = 1/2 sum rho |v_n|^2 + 1/2 sum eps_n : C : eps_n.  Implicit steps take the strain
+// part from the step's own sums: the solve gives A u_n = b + theta f with f supported on
+// Gamma, A = rho + theta K and u_n - u~ = theta a_n, so u.K u = -sum rho u_n . a_n +
+// sum_j U_j F_j, where F_j = sum over Gamma_j of f_j equals the reaction sum rho a_n,j
+// (the sum of K u over a periodic grid vanishes); exact up to the solver residual on the
+// free DOFs.  Explicit steps have K u_n itself (esum = u_n . K u_n).
+static double step_energy(const wfft_handle* h, const Scalars& s, const double U[3], bool explicit_step) {
+  if (explicit_step) return 0.5 * s.ekin2 + 0.5 * s.esum;
+  double w = -s.esum;
+  for (int j = 0; j < 3; ++j)
+    if (h->gam_comp[j]) w += U[j] * s.react[j];
+  return 0.5 * s.ekin2 + 0.5 * w;
+}
+
+// Prescribed values in the handle's component order (the caller's U[cmap[k]]).
+static void map_U(const wfft_handle* h, const double* U, double out[3]) {
+  for (int k = 0; k < 3; ++k) out[k] = k < h->ndim ? U[h->cmap[k]] : 0.0;
+}
+// Reaction sums in the caller's component order.
+static void put_reaction(const wfft_handle* h, const double* react, double out[3]) {
+  for (int k = 0; k < 3; ++k) out[k] = 0.0;
+  for (int k = 0; k < h->c; ++k) out[h->cmap[k]] = react[k];
 }
 
 #define CKH(h, x)                                                                                \
@@ -281,6 +312,52 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   }
   if (grid->ndim == 2 && grid->n[2] != 1) return fail(nullptr, WFFT_EINVAL, "2-D grids need n[2] == 1");
   if (grid->n[1] == 1 && grid->n[2] == 1) return fail(nullptr, WFFT_EUNSUPPORTED, "N2 = N3 = 1 is not supported");
+  if (grid->ndim == 3 && grid->n[0] == 1) {
+    // One voxel along x_1 (the paper's 1 x N x N plates, Sec. 4.1): run the same medium on
+    // the cyclically relabeled axes (x_1', x_2', x_3') = (x_2, x_3, x_1), grid (N2, N3, 1).
+    // With N1 = 1 the voxel order [N3][N2][1] is [1][N3][N2]: voxel arrays are unchanged;
+    // component k' is the caller's component cmap[k'] = (1, 2, 0)[k'], and the stiffness is
+    // relabeled index by index (Voigt 11 <- 22, 22 <- 33, 33 <- 11, 23 <- 13, 13 <- 12, 12 <- 23).
+    if (grid->n[2] == 1) return fail(nullptr, WFFT_EUNSUPPORTED, "N1 = N3 = 1 is not supported");
+    const long long Vx = (long long)grid->n[1] * grid->n[2];
+    const int cm[3] = {1, 2, 0};
+    const int vm[6] = {1, 2, 0, 4, 5, 3};
+    const long long rows = phase ? (nphase > 0 ? nphase : 0) : Vx;
+    std::vector<double> C2((size_t)rows * 21);
+    for (long long r = 0; r < rows; ++r) {
+      double m6[36], m2[36];
+      voigt_full(C + (size_t)r * 21, m6);
+      for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) m2[a * 6 + b] = m6[vm[a] * 6 + vm[b]];
+      int k = 0;
+      for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b) C2[(size_t)r * 21 + k++] = m2[a * 6 + b];
+    }
+    std::vector<uint8_t> M2;
+    if (mask) {
+      M2.resize((size_t)3 * Vx);
+      for (int k = 0; k < 3; ++k) memcpy(&M2[(size_t)k * Vx], mask + (size_t)cm[k] * Vx, (size_t)Vx);
+    }
+    wfft_grid g2;
+    g2.ndim = 3;
+    g2.n[0] = grid->n[1];
+    g2.n[1] = grid->n[2];
+    g2.n[2] = 1;
+    g2.h[0] = grid->h[1];
+    g2.h[1] = grid->h[2];
+    g2.h[2] = grid->h[0];
+    const int rc = wfft_create(&g2, C2.data(), phase, nphase, rho, mask ? M2.data() : nullptr, dt, beta, gamma,
+                               opt, stream, out);
+    if (rc == WFFT_OK) {
+      wfft_handle* hr = *out;
+      hr->relabeled = true;
+      for (int k = 0; k < 3; ++k) {
+        hr->cmap[k] = cm[k];
+        hr->n_ext[k] = grid->n[k];
+      }
+    }
+    return rc;
+  }
   const bool explicit_scheme = beta == 0.0 && gamma == 0.5;
   if (!(dt > 0) || !(gamma >= 0) || !(beta > 0 || explicit_scheme))
     return fail(nullptr, WFFT_EINVAL, "need dt > 0, gamma >= 0 and beta > 0 (or beta = 0, gamma = 1/2: explicit scheme)");
@@ -300,6 +377,7 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
   h->s = grid->ndim == 3 ? 6 : 3;
   for (int i = 0; i < 3; ++i) {
     h->n[i] = grid->n[i];
+    h->n_ext[i] = grid->n[i];
     h->h[i] = grid->h[i];
   }
   h->V = (long long)grid->n[0] * grid->n[1] * grid->n[2];
@@ -389,6 +467,11 @@ extern "C" int wfft_create(const wfft_grid* grid, const double* C, const uint16_
         }
   }
   h->has_mask = nfixed > 0;
+  for (int k = 0; k < h->c; ++k) {
+    const uint8_t bit = (uint8_t)(1u << k);
+    for (long long v = 0; v < V && !h->gam_comp[k]; ++v)
+      if (mbits[v] & bit) h->gam_comp[k] = 1;
+  }
   if (nfixed >= (long long)h->c * V) {
     delete h;
     return fail(nullptr, WFFT_EINVAL, "the mask covers every DOF");
@@ -528,7 +611,7 @@ extern "C" int wfft_get_sizes(const wfft_handle* h, int* ndim, int n[3], long lo
   if (!h) return WFFT_EINVAL;
   if (ndim) *ndim = h->ndim;
   if (n)
-    for (int i = 0; i < 3; ++i) n[i] = h->n[i];
+    for (int i = 0; i < 3; ++i) n[i] = h->n_ext[i];
   if (nvox) *nvox = h->V;
   return WFFT_OK;
 }
@@ -564,14 +647,24 @@ static int state_copy(wfft_handle* h, int to_dev, double* u, double* v, double* 
   }
   double* dst[3] = {(double*)h->P64.h.slot[SL_U], (double*)h->P64.h.slot[SL_V], (double*)h->P64.h.slot[SL_A]};
   double* src[3] = {u, v, a};
+  const size_t cb = (size_t)h->V * sizeof(double);  // one component
   for (int i = 0; i < 3; ++i) {
     if (to_dev) {
-      if (src[i])
-        CKH(h, cudaMemcpyAsync(dst[i], src[i], bytes, kind, h->st));
-      else
+      if (!src[i]) {
         CKH(h, cudaMemsetAsync(dst[i], 0, bytes, h->st));
+      } else if (!h->relabeled) {
+        CKH(h, cudaMemcpyAsync(dst[i], src[i], bytes, kind, h->st));
+      } else {
+        for (int k = 0; k < h->c; ++k)
+          CKH(h, cudaMemcpyAsync(dst[i] + (size_t)k * h->V, src[i] + (size_t)h->cmap[k] * h->V, cb, kind, h->st));
+      }
     } else if (src[i]) {
-      CKH(h, cudaMemcpyAsync(src[i], dst[i], bytes, kind, h->st));
+      if (!h->relabeled) {
+        CKH(h, cudaMemcpyAsync(src[i], dst[i], bytes, kind, h->st));
+      } else {
+        for (int k = 0; k < h->c; ++k)
+          CKH(h, cudaMemcpyAsync(src[i] + (size_t)h->cmap[k] * h->V, dst[i] + (size_t)k * h->V, cb, kind, h->st));
+      }
     }
   }
   CKH(h, cudaStreamSynchronize(h->st));
@@ -590,8 +683,17 @@ extern "C" int wfft_download_async(wfft_handle* h, double* u, double* v, double*
   double* dst[3] = {u, v, a};
   CKH(h, cudaEventRecord(h->dl_ready, h->st));
   CKH(h, cudaStreamWaitEvent(h->dl_st, h->dl_ready, 0));
-  for (int i = 0; i < 3; ++i)
-    if (dst[i]) CKH(h, cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToHost, h->dl_st));
+  for (int i = 0; i < 3; ++i) {
+    if (!dst[i]) continue;
+    if (!h->relabeled) {
+      CKH(h, cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToHost, h->dl_st));
+    } else {
+      const size_t cb = (size_t)h->V * sizeof(double);
+      for (int k = 0; k < h->c; ++k)
+        CKH(h, cudaMemcpyAsync(dst[i] + (size_t)h->cmap[k] * h->V, src[i] + (size_t)k * h->V, cb,
+                               cudaMemcpyDeviceToHost, h->dl_st));
+    }
+  }
   CKH(h, cudaEventRecord(h->dl_done, h->dl_st));
   h->dl_pending = true;
   return WFFT_OK;
@@ -625,6 +727,21 @@ extern "C" int wfft_get_state_dev(const wfft_handle* hc, double* u, double* v, d
   wfft_handle* h = const_cast<wfft_handle*>(hc);
   if (!h) return fail(nullptr, WFFT_EINVAL, "null handle");
   return state_copy(h, 0, u, v, a, cudaMemcpyDeviceToDevice);
+}
+
+// Host field [c][V] of the caller <-> device field of the handle (component order cmap).
+static int field_copy(wfft_handle* h, void* dst, const void* src, cudaMemcpyKind kind) {
+  const size_t cb = (size_t)h->V * sizeof(double);
+  if (!h->relabeled) {
+    CKH(h, cudaMemcpyAsync(dst, src, cb * h->c, kind, h->st));
+    return WFFT_OK;
+  }
+  const bool to_dev = kind == cudaMemcpyHostToDevice;
+  for (int k = 0; k < h->c; ++k) {
+    const size_t di = (size_t)(to_dev ? k : h->cmap[k]) * cb, si = (size_t)(to_dev ? h->cmap[k] : k) * cb;
+    CKH(h, cudaMemcpyAsync((char*)dst + di, (const char*)src + si, cb, kind, h->st));
+  }
+  return WFFT_OK;
 }
 
 static int read_scalars(wfft_handle* h) {
@@ -863,7 +980,8 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
   if (warm == WFFT_WARM_LEARNED && !h->net) return fail(h, WFFT_EINVAL, "no warm-start model loaded");
   Plan<double>& P = h->P64;
   const bool mixed = h->opt.precision == WFFT_MIXED;
-  const double Uv[3] = {U[0], h->ndim > 1 ? U[1] : 0.0, h->ndim > 2 ? U[2] : 0.0};
+  double Uv[3];
+  map_U(h, U, Uv);
   // increment warm starts: x0 = u_{n-1} + delta (delta FP32, zero on Gamma); in a
   // mixed solve with the stored A u_{n-1} the increment is the initial guess of the
   // first FP32 inner solve, so the initial residual still needs no FP64 apply
@@ -902,6 +1020,7 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
     launch_correct(P, h->st);
     const int nb = ew_block_count(P);
     launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
+  launch_fin(h->sc64, P.h.part[PT_D], nb, P.h.part[PT_E], nb, nullptr, 0, FIN_ENERGY, nullptr, h->st);
     ++h->nstep;
   }
   CKH(h, cudaEventRecord(h->ev1, h->st));
@@ -910,7 +1029,8 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
   if (rc) return rc;
   if (info) {
     info->status = status;
-    for (int k = 0; k < 3; ++k) info->reaction[k] = status == WFFT_OK ? h->host_sc[0].react[k] : 0.0;
+    if (status == WFFT_OK) put_reaction(h, h->host_sc[0].react, info->reaction);
+    info->energy = status == WFFT_OK ? step_energy(h, h->host_sc[0], Uv, false) : 0.0;
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     info->ms = ms;
@@ -1024,7 +1144,6 @@ extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol
   fill_info_base(info);
   h->au_valid = false;  // the residual evaluations below overwrite the stored A u
   Plan<double>& P = h->P64;
-  const size_t bytes = (size_t)h->c * h->V * sizeof(double);
   const double t = tol > 0 ? tol : h->opt.tol;
   const int mi = maxit > 0 ? maxit : h->opt.maxit;
   const int saved = h->opt.maxit;
@@ -1033,21 +1152,25 @@ extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol
   CKH(h, cudaEventRecord(h->ev0, h->st));
   launch_begin(h->sc64, U0, 0, t * t, mi, h->st);
   launch_begin(h->sc32, U0, 0, h->opt.inner_tol * h->opt.inner_tol, mi, h->st);
-  CKH(h, cudaMemcpyAsync(P.h.slot[SL_B], b, bytes, cudaMemcpyHostToDevice, h->st));
+  int rcc = field_copy(h, P.h.slot[SL_B], b, cudaMemcpyHostToDevice);
+  if (rcc) return rcc;
   // ref^2 = ||P(b - A x_Gamma)||^2: residual of x with its free DOFs zeroed
-  CKH(h, cudaMemcpyAsync(P.h.slot[SL_X], x, bytes, cudaMemcpyHostToDevice, h->st));
+  rcc = field_copy(h, P.h.slot[SL_X], x, cudaMemcpyHostToDevice);
+  if (rcc) return rcc;
   prof_launch(0, KK_NEWMARK, 16.0 * h->c * h->V, 0.0, h->st,
               [&] { k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]); });
   launch_apply<double>(P, PRE_PLAIN, SL_X, POST_RESID, 0, 1, 1, h->st);
   launch_fin(h->sc64, P.h.part[PT_A], P.g.blk_x, nullptr, 0, nullptr, 0, FIN_REF, nullptr, h->st);
-  CKH(h, cudaMemcpyAsync(P.h.slot[SL_X], x, bytes, cudaMemcpyHostToDevice, h->st));
+  rcc = field_copy(h, P.h.slot[SL_X], x, cudaMemcpyHostToDevice);
+  if (rcc) return rcc;
   int status = solve_core(h, info);
   h->opt.maxit = saved;
   if (h->host_sc[0].zero_free)
     prof_launch(0, KK_NEWMARK, 16.0 * h->c * h->V, 0.0, h->st,
                 [&] { k_keep_gamma<<<ew_block_count(P), 256, 0, h->st>>>(P.d, (double*)P.h.slot[SL_X]); });
   CKH(h, cudaEventRecord(h->ev1, h->st));
-  CKH(h, cudaMemcpyAsync(x, P.h.slot[SL_X], bytes, cudaMemcpyDeviceToHost, h->st));
+  rcc = field_copy(h, x, P.h.slot[SL_X], cudaMemcpyDeviceToHost);
+  if (rcc) return rcc;
   CKH(h, cudaStreamSynchronize(h->st));
   CKH(h, cudaGetLastError());
   if (info) {
@@ -1063,6 +1186,7 @@ extern "C" int wfft_solve(wfft_handle* h, const double* b, double* x, double tol
 extern "C" int wfft_apply(wfft_handle* h, int precision, const void* p_dev, void* q_dev, int masked) {
   ProfScope ps_(h);
   if (!h || !p_dev || !q_dev) return fail(h, WFFT_EINVAL, "null argument");
+  if (h->relabeled) return fail(h, WFFT_EUNSUPPORTED, "field calls on a grid with N1 = 1 (relabeled axes)");
   if (precision == WFFT_FP64) {
     launch_set_done(h->sc64, 0, h->st);
     CKH(h, set_ext(h->P64, p_dev, q_dev, h->st));
@@ -1080,6 +1204,7 @@ extern "C" int wfft_apply(wfft_handle* h, int precision, const void* p_dev, void
 
 extern "C" int wfft_precond(wfft_handle* h, int precision, const void* r_dev, void* z_dev, int masked) {
   ProfScope ps_(h);
+  if (h && h->relabeled) return fail(h, WFFT_EUNSUPPORTED, "field calls on a grid with N1 = 1 (relabeled axes)");
   if (!h || !r_dev || !z_dev) return fail(h, WFFT_EINVAL, "null argument");
   if (precision == WFFT_FP64) {
     launch_set_done(h->sc64, 0, h->st);
@@ -1118,6 +1243,7 @@ static int rfft3_impl(wfft_handle* h, Plan<T>& P, Scalars* sc, int dir, int ncom
 extern "C" int wfft_rfft3(wfft_handle* h, int precision, int dir, int ncomp, const void* in_dev, void* out_dev) {
   ProfScope ps_(h);
   if (!h || !in_dev || !out_dev) return fail(h, WFFT_EINVAL, "null argument");
+  if (h->relabeled) return fail(h, WFFT_EUNSUPPORTED, "field calls on a grid with N1 = 1 (relabeled axes)");
   if (ncomp < 1 || ncomp > h->s || (dir != -1 && dir != 1)) return fail(h, WFFT_EINVAL, "bad ncomp or dir");
   if (precision == WFFT_FP64) return rfft3_impl<double>(h, h->P64, h->sc64, dir, ncomp, in_dev, out_dev);
   if (precision == WFFT_MIXED) return rfft3_impl<float>(h, h->P32, h->sc32, dir, ncomp, in_dev, out_dev);
@@ -1132,7 +1258,7 @@ namespace {
 
 enum FinSlot {
   FJ_REF = 0, FJ_RES0, FJ_RZ0, FJ_ALPHA, FJ_BETA, FJ_OUTER_STORED, FJ_OUTER_RESID, FJ_REACT,
-  FJ_RZ0_32, FJ_ALPHA_32, FJ_BETA_32, FJ_DNORM, FJ_OUTER_INCR, FJ_N
+  FJ_RZ0_32, FJ_ALPHA_32, FJ_BETA_32, FJ_DNORM, FJ_OUTER_INCR, FJ_ENERGY, FJ_N
 };
 
 struct BatchCtx {
@@ -1173,20 +1299,20 @@ cudaError_t build_launch(BatchCtx& B, BatchLaunch<T>& bl, Plan<T> wfft_handle::*
   bl.n = n;
   bl.plans.clear();
   for (wfft_handle* h : B.hs) bl.plans.push_back(&(h->*plan));
-  // common column-tile width: the narrowest of the instances
-  for (int ax = 1; ax <= 2; ++ax)
-    for (int op = 0; op < 5; ++op) {
-      int bx = 8;
-      for (const Plan<T>* q : bl.plans) bx = std::min(bx, std::max(1, q->g.bx[ax][op]));
-      bl.bx[ax][op] = bx;
-    }
+  // every instance keeps its own column-tile widths (its tuned plan): a column class
+  // is one group of instances per distinct width, each group its own grouped launch
+  auto own_bx = [&](int i, int cls) {
+    return std::max(1, bl.plans[i]->g.bx[(cls - GEO_COL0) / 5 + 1][(cls - GEO_COL0) % 5]);
+  };
   std::vector<int> starts((size_t)NGEO * (n + 1));
+  std::vector<std::vector<int>> gstarts;  // prefix sums of the column groups
+  std::vector<std::pair<int, int>> gkey;  // (class, group index) of each gstarts entry
   for (int cls = 0; cls < NGEO; ++cls) {
+    const bool col = cls >= GEO_COL0 && cls < GEO_EW;
     int acc = 0;
     size_t sm = 0;
-    int bx = 1;
-    if (cls >= GEO_COL0 && cls < GEO_EW) bx = bl.bx[(cls - GEO_COL0) / 5 + 1][(cls - GEO_COL0) % 5];
     for (int i = 0; i < n; ++i) {
+      const int bx = col ? own_bx(i, cls) : 1;
       starts[(size_t)cls * (n + 1) + i] = acc;
       acc += geo_blocks<T>(*bl.plans[i], cls, bx);
       sm = std::max(sm, geo_smem<T>(*bl.plans[i], cls, bx));
@@ -1194,14 +1320,44 @@ cudaError_t build_launch(BatchCtx& B, BatchLaunch<T>& bl, Plan<T> wfft_handle::*
     starts[(size_t)cls * (n + 1) + n] = acc;
     bl.total[cls] = acc;
     bl.sm[cls] = sm;
+    if (!col) continue;
+    std::vector<ColGroup<T>>& groups = bl.cols[cls - GEO_COL0];
+    groups.clear();
+    for (int i = 0; i < n; ++i) {
+      const int bx = own_bx(i, cls);
+      bool seen = false;
+      for (const ColGroup<T>& g : groups) seen = seen || g.bx == bx;
+      if (seen) continue;
+      ColGroup<T> g;
+      g.bx = bx;
+      std::vector<int> st(n + 1);
+      int a = 0;
+      for (int j = 0; j < n; ++j) {
+        st[j] = a;
+        if (own_bx(j, cls) != bx) continue;
+        a += geo_blocks<T>(*bl.plans[j], cls, bx);
+        g.sm = std::max(g.sm, geo_smem<T>(*bl.plans[j], cls, bx));
+        g.plans.push_back(bl.plans[j]);
+      }
+      st[n] = a;
+      g.total = a;
+      gkey.push_back({cls, (int)groups.size()});
+      gstarts.push_back(st);
+      groups.push_back(g);
+    }
   }
   void *dstart = nullptr, *ddesc = nullptr;
-  cudaError_t e = cudaMalloc(&dstart, starts.size() * sizeof(int));
+  const size_t nstart = starts.size() + gstarts.size() * (size_t)(n + 1);
+  cudaError_t e = cudaMalloc(&dstart, nstart * sizeof(int));
   if (e != cudaSuccess) return e;
   dev.push_back(dstart);
-  e = cudaMemcpy(dstart, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice);
+  for (const std::vector<int>& st : gstarts) starts.insert(starts.end(), st.begin(), st.end());
+  e = cudaMemcpy(dstart, starts.data(), nstart * sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   for (int cls = 0; cls < NGEO; ++cls) bl.start[cls] = reinterpret_cast<int*>(dstart) + (size_t)cls * (n + 1);
+  for (size_t k = 0; k < gkey.size(); ++k)
+    bl.cols[gkey[k].first - GEO_COL0][gkey[k].second].start =
+        reinterpret_cast<int*>(dstart) + (size_t)(NGEO + k) * (n + 1);
   std::vector<const Desc<T>*> descs;
   for (const Plan<T>* q : bl.plans) descs.push_back(q->d);
   e = cudaMalloc(&ddesc, descs.size() * sizeof(void*));
@@ -1215,7 +1371,7 @@ cudaError_t build_launch(BatchCtx& B, BatchLaunch<T>& bl, Plan<T> wfft_handle::*
 template <typename T>
 int blocks_of(const BatchLaunch<T>& bl, int i, int cls) {
   int bx = 1;
-  if (cls >= GEO_COL0 && cls < GEO_EW) bx = bl.bx[(cls - GEO_COL0) / 5 + 1][(cls - GEO_COL0) % 5];
+  if (cls >= GEO_COL0 && cls < GEO_EW) bx = std::max(1, bl.plans[i]->g.bx[(cls - GEO_COL0) / 5 + 1][(cls - GEO_COL0) % 5]);
   return geo_blocks<T>(*bl.plans[i], cls, bx);
 }
 
@@ -1243,6 +1399,7 @@ int build_batch(std::vector<wfft_handle*>& hs, BatchCtx*& out, std::string& err)
     J(FJ_OUTER_STORED) = {h->sc64, D.part[PT_B], ew, nullptr, 0, nullptr, 0, h->sc32};
     J(FJ_OUTER_RESID) = {h->sc64, D.part[PT_A], bx64, nullptr, 0, nullptr, 0, h->sc32};
     J(FJ_REACT) = {h->sc64, D.part[PT_A], ew, D.part[PT_B], ew, D.part[PT_C], ew, nullptr};
+    J(FJ_ENERGY) = {h->sc64, D.part[PT_D], ew, D.part[PT_E], ew, nullptr, 0, nullptr};
     J(FJ_RZ0_32) = {h->sc32, nullptr, 0, F.part[PT_B], pr32, nullptr, 0, nullptr};
     J(FJ_ALPHA_32) = {h->sc32, F.part[PT_A], bx32, nullptr, 0, nullptr, 0, nullptr};
     J(FJ_BETA_32) = {h->sc32, F.part[PT_A], bx32, F.part[PT_B], pr32, nullptr, 0, nullptr};
@@ -1418,7 +1575,8 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
   for (int i = 0; i < n; ++i) use_au = use_au && hs[i]->au_valid;
   for (int i = 0; i < n; ++i) {
     wfft_handle* h = hs[i];
-    const double Uv[3] = {U[3 * i], h->ndim > 1 ? U[3 * i + 1] : 0.0, h->ndim > 2 ? U[3 * i + 2] : 0.0};
+    double Uv[3];
+    map_U(h, U + 3 * i, Uv);
     BeginJob& b = B.hb64[i];
     b.sc = h->sc64;
     for (int k = 0; k < 3; ++k) {
@@ -1554,6 +1712,7 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
   }
   launch_correct(P0, st, &B.bl64);
   launch_fin_batch(B.fin[FJ_REACT], n, FIN_REACT, st);
+  launch_fin_batch(B.fin[FJ_ENERGY], n, FIN_ENERGY, st);
   CKH(h0, cudaEventRecord(h0->ev1, st));
   if (batch_read(B, st)) return fail(h0, WFFT_ECUDA, "batch solve failed");
   float ms = 0;
@@ -1580,7 +1739,8 @@ extern "C" int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_st
       in.incr_resids = incrs[i];
       in.ref = std::sqrt(s64.ref2);
       in.rel_res = s64.ref2 > 0 ? std::sqrt(s64.rr / s64.ref2) : 0.0;
-      for (int k = 0; k < 3; ++k) in.reaction[k] = st_i == WFFT_OK ? s64.react[k] : 0.0;
+      if (st_i == WFFT_OK) put_reaction(h, s64.react, in.reaction);
+      in.energy = st_i == WFFT_OK ? step_energy(h, s64, B.hb64[i].U, false) : 0.0;
       in.ms = ms;
     }
     if (st_i != WFFT_OK && !first) first = st_i;
@@ -1807,7 +1967,8 @@ extern "C" int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_ste
   if (!Udot) return fail(h, WFFT_EINVAL, "Udot is NULL");
   fill_info_base(info);
   Plan<double>& P = h->P64;
-  const double Uv[3] = {Udot[0], h->ndim > 1 ? Udot[1] : 0.0, h->ndim > 2 ? Udot[2] : 0.0};
+  double Uv[3];
+  map_U(h, Udot, Uv);
   CKH(h, cudaEventRecord(h->ev0, h->st));
   launch_set_done(h->sc64, 0, h->st);
   {
@@ -1820,6 +1981,7 @@ extern "C" int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_ste
   launch_explicit_update(P, Uv, h->st);
   const int nb = ew_block_count(P);
   launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
+  launch_fin(h->sc64, P.h.part[PT_D], nb, P.h.part[PT_E], nb, nullptr, 0, FIN_ENERGY, nullptr, h->st);
   CKH(h, cudaEventRecord(h->ev1, h->st));
   CKH(h, cudaGetLastError());
   int rc = read_scalars(h);
@@ -1829,7 +1991,8 @@ extern "C" int wfft_explicit_step(wfft_handle* h, const double Udot[3], wfft_ste
   if (info) {
     info->status = WFFT_OK;
     info->outer_applies = 1;
-    for (int k = 0; k < 3; ++k) info->reaction[k] = h->host_sc[0].react[k];
+    put_reaction(h, h->host_sc[0].react, info->reaction);
+    info->energy = step_energy(h, h->host_sc[0], Uv, true);
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     info->ms = ms;
@@ -2015,7 +2178,8 @@ extern "C" int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info
   Plan<double>& P = h->P64;
   const Desc<double>& D = P.h;
   const long long n = h->green_n;
-  const double Uv[3] = {U[0], h->ndim > 1 ? U[1] : 0.0, h->ndim > 2 ? U[2] : 0.0};
+  double Uv[3];
+  map_U(h, U, Uv);
   double* b = reinterpret_cast<double*>(D.slot[SL_B]);
   double* x = reinterpret_cast<double*>(D.slot[SL_X]);
   const size_t bytes = (size_t)h->c * h->V * sizeof(double);
@@ -2046,6 +2210,7 @@ extern "C" int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info
   launch_correct(P, h->st);
   const int nb = ew_block_count(P);
   launch_fin(h->sc64, P.h.part[PT_A], nb, P.h.part[PT_B], nb, P.h.part[PT_C], nb, FIN_REACT, nullptr, h->st);
+  launch_fin(h->sc64, P.h.part[PT_D], nb, P.h.part[PT_E], nb, nullptr, 0, FIN_ENERGY, nullptr, h->st);
   CKH(h, cudaEventRecord(h->ev1, h->st));
   CKH(h, cudaGetLastError());
   rc = read_scalars(h);
@@ -2057,7 +2222,8 @@ extern "C" int wfft_green_step(wfft_handle* h, const double U[3], wfft_step_info
     info->status = WFFT_OK;
     info->iters = it1 + it2;
     info->outer_applies = 2;
-    for (int k = 0; k < 3; ++k) info->reaction[k] = h->host_sc[0].react[k];
+    put_reaction(h, h->host_sc[0].react, info->reaction);
+    info->energy = step_energy(h, h->host_sc[0], Uv, false);
     float ms = 0;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     info->ms = ms;

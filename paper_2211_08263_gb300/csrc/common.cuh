@@ -49,6 +49,8 @@ struct Scalars {
   double rbound;    // outer: estimate of the rounding error of the next residual evaluation's
                     // norm (incremental residuals); consumed by that evaluation's finalize
   double dnorm2;    // outer: ||d||^2 of the latest FP32 inner correction
+  double ekin2;     // sum rho |v_n|^2 of the latest committed step (twice the kinetic energy)
+  double esum;      // implicit steps: sum rho u_n . a_n; explicit steps: sum u_n . K u_n
   int iter;         // operator applications inside the Krylov loop
   int maxit;
   int done;         // 1: every kernel of this solve returns immediately
@@ -72,7 +74,7 @@ enum Slot {
 };
 
 // Partial-sum arrays (one double per block of the producing kernel).
-enum PartId { PT_A = 0, PT_B, PT_C, NPART };
+enum PartId { PT_A = 0, PT_B, PT_C, PT_D, PT_E, NPART };  // PT_D / PT_E: energy sums of the corrector
 
 template <typename T>
 struct Desc {

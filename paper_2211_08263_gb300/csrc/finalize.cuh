@@ -5,7 +5,7 @@
 
 namespace wfft {
 
-enum FinMode { FIN_REF = 0, FIN_RES0, FIN_RZ0, FIN_ALPHA, FIN_BETA, FIN_OUTER, FIN_REACT, FIN_CLOSE, FIN_DNORM };
+enum FinMode { FIN_REF = 0, FIN_RES0, FIN_RZ0, FIN_ALPHA, FIN_BETA, FIN_OUTER, FIN_REACT, FIN_CLOSE, FIN_DNORM, FIN_ENERGY };
 
 // Grid size cap of the elementwise FP64 kernels (and so a lower bound on the
 // length of every partial-sum array).

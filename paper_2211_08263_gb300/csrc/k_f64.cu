@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
 }
 
 // Corrector (Eq. Newmark): a_n = (u_n - u~)/(beta dt^2), v_n = v + dt((1-gamma) a + gamma a_n);
-// partial sums of rho a_n per component (total force on the prescribed region).
+// partial sums of rho a_n per component (total force on the prescribed region), of rho |v_n|^2
+// and of rho u_n . a_n (the energy of the step, see FIN_ENERGY's caller).
 __global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict__ dd, BatchArgs<double> ba) {
   int blk;
   const Desc<double>* __restrict__ Dp = pick_ptr<double, 1>(dd, ba, blk);
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict_
   const double* x = reinterpret_cast<const double*>(D.slot[SL_X]);
   const bool zf = sc->zero_free != 0;
   double acc[3] = {0.0, 0.0, 0.0};
+  double ek = 0.0, eua = 0.0;
   const long long tot = (long long)c * V;
   for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
     const int k = (int)(gi / V);
@@ -126,15 +128,22 @@ __global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict_
     u[gi] = xv;
     v[gi] = vn;
     a[gi] = an;
-    const double f = rho_at<double>(D, vox) * an;
+    const double rho = rho_at<double>(D, vox);
+    const double f = rho * an;
     if (k == 0) acc[0] += f;
     else if (k == 1) acc[1] += f;
     else acc[2] += f;
+    ek += rho * vn * vn;
+    eua += xv * f;
   }
   for (int k = 0; k < 3; ++k) {
     const double s = block_sum(acc[k]);
     if (threadIdx.x == 0) D.part[k][blk] = s;
   }
+  const double sk = block_sum(ek);
+  if (threadIdx.x == 0) D.part[PT_D][blk] = sk;
+  const double sua = block_sum(eua);
+  if (threadIdx.x == 0) D.part[PT_E][blk] = sua;
 }
 
 // Unit lifting field E e_j: 1 on the prescribed DOFs of component j, 0 elsewhere.
@@ -178,7 +187,9 @@ __global__ void __launch_bounds__(256) k_explicit_update(const Desc<double>* __r
   double* v = reinterpret_cast<double*>(D.slot[SL_V]);
   double* a = reinterpret_cast<double*>(D.slot[SL_A]);
   const double* q = reinterpret_cast<const double*>(D.slot[SL_Q]);
+  const double* un = reinterpret_cast<const double*>(D.slot[SL_U]);
   double acc[3] = {0.0, 0.0, 0.0};
+  double ek = 0.0, euq = 0.0;
   for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
        gi += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(gi / V);
@@ -197,11 +208,17 @@ __global__ void __launch_bounds__(256) k_explicit_update(const Desc<double>* __r
     if (k == 0) acc[0] += f;
     else if (k == 1) acc[1] += f;
     else acc[2] += f;
+    ek += rho * vn * vn;
+    euq += un[gi] * q[gi];
   }
   for (int k = 0; k < 3; ++k) {
     const double sum = block_sum(acc[k]);
     if (threadIdx.x == 0) D.part[k][blockIdx.x] = sum;
   }
+  const double sk = block_sum(ek);
+  if (threadIdx.x == 0) D.part[PT_D][blockIdx.x] = sk;
+  const double suq = block_sum(euq);
+  if (threadIdx.x == 0) D.part[PT_E][blockIdx.x] = suq;
 }
 
 // ---------------------------------------------------------------------------
@@ -504,7 +521,7 @@ __device__ void fin_body(Scalars* sc, const double* pa, int na, const double* pb
     return;
   }
   // a finished solve is frozen: only the setup / bookkeeping modes still run
-  if (sc->done && mode != FIN_REF && mode != FIN_REACT) return;
+  if (sc->done && mode != FIN_REF && mode != FIN_REACT && mode != FIN_ENERGY) return;
   switch (mode) {
     case FIN_REF:
       sc->ref2 = sa;
@@ -606,6 +623,10 @@ __device__ void fin_body(Scalars* sc, const double* pa, int na, const double* pb
       sc->react[0] = sa;
       sc->react[1] = sb;
       sc->react[2] = scc;
+      break;
+    case FIN_ENERGY:
+      sc->ekin2 = sa;
+      sc->esum = sb;
       break;
     default:
       break;

@@ -33,9 +33,23 @@ struct Plan {
 enum GeoClass { GEO_X = 0, GEO_XM = 1, GEO_COL0 = 2, GEO_EW = GEO_COL0 + 10, NGEO };
 inline int geo_col(int axis, int op) { return GEO_COL0 + (axis - 1) * 5 + op; }
 
+// Instances of a grouped column pass that share one column-tile width: their block
+// prefix sums (n + 1 entries over all instances of the launch; the others have no
+// blocks), total blocks, largest shared memory and plans (for the cost model).
+template <typename T>
+struct ColGroup {
+  int bx = 1;
+  const int* start = nullptr;  // device
+  int total = 0;
+  size_t sm = 0;
+  std::vector<const Plan<T>*> plans;
+};
+
 // A grouped launch over several instances of the same structure (ndim, pass
-// sequence): device array of descriptors, per-class block prefix sums, the
-// common column-tile width and the largest shared memory per class.
+// sequence): device array of descriptors, per-class block prefix sums and the
+// largest shared memory per class.  Each instance keeps its own column-tile widths
+// (its tuned plan): a column pass is one grouped launch per distinct width (cols[]);
+// start / total / sm / bx of a column class then describe the group being launched.
 template <typename T>
 struct BatchLaunch {
   int n = 0;
@@ -45,6 +59,7 @@ struct BatchLaunch {
   size_t sm[NGEO] = {};
   int bx[3][5] = {};
   std::vector<const Plan<T>*> plans;
+  std::vector<ColGroup<T>> cols[GEO_EW - GEO_COL0];  // per column class
 };
 
 // Compute tile geometry from h's sizes (elements budget per block).

@@ -11,10 +11,16 @@
 // constants; no handle is created and nothing is allocated or freed.
 //
 // In host code the array's name is a host-side stand-in, not a device
-// address: the device address is taken with cudaGetSymbolAddress on the first
-// call on each device (with that device current) and cached.  Every call
-// shares the one array, so two calls that overlap on the GPU (different
-// streams, or different host threads) race on it.
+// address: every call takes the device address with cudaGetSymbolAddress,
+// with the caller's device current (once the module is loaded this allocates
+// nothing), so the address stays right even after the context was torn down
+// and created again.  The kernels' shared-memory attributes are set once per
+// CUDA context (keyed on the driver's context id).  Every call shares the one
+// array, so two calls that overlap on the GPU (different streams, or
+// different host threads) race on it.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -40,10 +46,35 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct DevState {
   bool ready = false;
-  unsigned char* base = nullptr;  // device address of g_scratch on that device
+  unsigned long long ctx_id = 0;  // context whose kernel attributes were set
 };
 DevState g_devs[kMaxDevices];
 std::mutex g_mutex;
+
+// Id of the current CUDA context through the driver entry points the runtime
+// exposes (no link against the driver library).  0 when unavailable.
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+  });
+  if (!get_cur || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int na_fail(int code, const char* msg) {
   set_global_error(msg);  // read back with wfft_last_error(NULL)
@@ -106,19 +137,21 @@ extern "C" int wfft_precond_noalloc(const wfft_grid* grid, const double cbar[21]
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(WFFT_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return na_fail(WFFT_EUNSUPPORTED, "device index out of range");
+  // the array's device address in the current context (loads the module on first use)
+  void* sym = nullptr;
+  e = cudaGetSymbolAddress(&sym, g_scratch);
+  if (e != cudaSuccess) return na_fail(WFFT_ECUDA, cudaGetErrorString(e));
   {
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_devs[dev].ready) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_scratch);
-      if (e != cudaSuccess) return na_fail(WFFT_ECUDA, cudaGetErrorString(e));
+    const unsigned long long ctx = current_context_id();
+    if (!g_devs[dev].ready || ctx == 0 || g_devs[dev].ctx_id != ctx) {
       e = init_kernel_attributes<double>();
       if (e != cudaSuccess) return na_fail(WFFT_ECUDA, cudaGetErrorString(e));
-      g_devs[dev].base = reinterpret_cast<unsigned char*>(p);
-      g_devs[dev].ready = true;
+      g_devs[dev].ctx_id = ctx;
+      g_devs[dev].ready = ctx != 0;
     }
   }
-  unsigned char* base = g_devs[dev].base;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sym);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   const double twopi = 6.283185307179586476925286766559;

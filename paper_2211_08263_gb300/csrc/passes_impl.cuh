@@ -360,7 +360,31 @@ static void launch_colop(const Launch<T, B>& L, int axis, cudaStream_t st) {
 }
 
 template <typename T, int B>
+static void launch_col_one(const Launch<T, B>& L, int op, int axis, int ncomp, cudaStream_t st);
+
+// A grouped column pass runs one launch per column-tile width among its instances.
+template <typename T, int B>
 static void launch_col(const Launch<T, B>& L, int op, int axis, int ncomp, cudaStream_t st) {
+  if (B == 0 || !L.bl) {
+    launch_col_one<T, B>(L, op, axis, ncomp, st);
+    return;
+  }
+  const int cls = geo_col(axis, op);
+  for (const ColGroup<T>& g : L.bl->cols[cls - GEO_COL0]) {
+    if (g.total == 0) continue;
+    BatchLaunch<T> v = *L.bl;
+    v.start[cls] = g.start;
+    v.total[cls] = g.total;
+    v.sm[cls] = g.sm;
+    v.bx[axis][op] = g.bx;
+    v.plans = g.plans;
+    const Launch<T, B> Lg{L.P, &v};
+    launch_col_one<T, B>(Lg, op, axis, ncomp, st);
+  }
+}
+
+template <typename T, int B>
+static void launch_col_one(const Launch<T, B>& L, int op, int axis, int ncomp, cudaStream_t st) {
   if (op == OP_FWD || op == OP_INV) {
     switch (L.bx(axis, op)) {
       case 16:

@@ -441,6 +441,37 @@ def config_sphere129(nsteps: int = 6, pulse_steps: float = 12.0) -> Problem:
                    tol=1e-10, extra={"pulse_steps": pulse_steps})
 
 
+FE_E_NU_RHO = (211.4e9, 0.293, 7850.0)
+
+
+def config_plate1025(nsteps: int = 4, framed: bool = False, n: int = 1025, pulse_steps: float = 12.0) -> Problem:
+    """Circular waves in a plate (Sec. 4.1): 0.001 x 1 x 1 m discretised in 1 x n x n voxels
+    (n = 1025 = 5^2 x 41 in the paper), aluminium, or (framed) an aluminium square of
+    0.39 x 0.39 m in the centre of an iron frame; dt = 1.9e-6 s; the bell pulse (Eq.
+    prescribed_displacement, alpha = 4, amplitude 1 mm) on u_1 (perpendicular to the plate)
+    of the voxels whose centres lie within R = 2.5 mm of the plate's centre, u_2 = u_3 = 0
+    there.  The pulse frequency is not printed: omega = pi / (pulse_steps dt)."""
+    shape_xyz = (1, n, n)
+    h = (1e-3, 1.0 / n, 1.0 / n)
+    mats = [AL_E_NU_RHO, FE_E_NU_RHO]
+    Cv = np.stack([voigt21_from_matrix(isotropic_voigt(E, nu)) for E, nu, _ in mats])
+    rho = np.array([r for _, _, r in mats])
+    y = (np.arange(n) + 0.5) / n - 0.5  # centres along x_2 and x_3, origin at the plate's centre
+    phase = np.zeros((n, n, 1), dtype=np.uint16)  # [N3][N2][N1]
+    if framed:
+        inside = (np.abs(y)[:, None] < 0.195) & (np.abs(y)[None, :] < 0.195)
+        phase[:, :, 0] = np.where(inside, 0, 1)
+    r2 = y[:, None] ** 2 + y[None, :] ** 2
+    mask = np.zeros((3, n, n, 1), dtype=np.uint8)
+    mask[:, r2 <= 2.5e-3 ** 2, 0] = 1
+    dt = 1.9e-6
+    t = dt * np.arange(1, nsteps + 1)
+    U = np.zeros((nsteps, 3))
+    U[:, 0] = bell_pulse(t, 1e-3, np.pi / (pulse_steps * dt), 4.0)
+    return Problem(f"plate_{'framed' if framed else 'al'}_{n}", 3, shape_xyz, h, dt, 0.25, 0.5, Cv, rho, phase,
+                   mask, U, tol=1e-10, extra={"pulse_steps": pulse_steps})
+
+
 BATCH_SIZES = (64, 80, 96, 128, 144, 160, 192)
 
 

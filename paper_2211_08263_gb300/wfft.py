@@ -52,12 +52,13 @@ class PlanChoice(C.Structure):
 class StepInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("outer_applies", C.c_int), ("sweeps", C.c_int),
                 ("ref", C.c_double), ("rel_res", C.c_double), ("reaction", C.c_double * 3), ("ms", C.c_double),
-                ("incr_resids", C.c_int)]
+                ("incr_resids", C.c_int), ("energy", C.c_double)]
 
     def as_dict(self):
         return {"status": self.status, "iters": self.iters, "outer_applies": self.outer_applies,
                 "sweeps": self.sweeps, "ref": self.ref, "rel_res": self.rel_res,
-                "reaction": list(self.reaction), "ms": self.ms, "incr_resids": self.incr_resids}
+                "reaction": list(self.reaction), "ms": self.ms, "incr_resids": self.incr_resids,
+                "energy": self.energy}
 
 
 _lib = None
@@ -366,8 +367,21 @@ class Solver:
         return p.value
 
 
+def _check_dev_f64(name: str, t, count: int):
+    """Refuse anything but a contiguous CUDA float64 tensor of `count` elements: the library
+    cannot see the size of a device buffer it is handed."""
+    ok = (hasattr(t, "is_cuda") and t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous()
+          and t.numel() == count)
+    if not ok:
+        raise WfftError(EINVAL, f"{name} must be a contiguous CUDA float64 tensor of {count} elements")
+
+
 def precond_noalloc(ndim: int, n, h, cbar21, rho_bar: float, theta: float, r, z, stream: int = 0):
-    """z = M r (FP64, unmasked) through the allocation-free entry point; r, z are device arrays."""
+    """z = M r (FP64, unmasked) through the allocation-free entry point; r, z are contiguous
+    CUDA float64 tensors of ndim * N1 * N2 * N3 elements (checked here before the call)."""
+    count = int(ndim) * int(n[0]) * int(n[1]) * int(n[2])
+    _check_dev_f64("r", r, count)
+    _check_dev_f64("z", z, count)
     lib = load()
     g = Grid(ndim, (C.c_int * 3)(*[int(v) for v in n]), (C.c_double * 3)(*[float(v) for v in h]))
     cb = (C.c_double * 21)(*[float(v) for v in cbar21])

@@ -138,3 +138,61 @@ def test_batched_mixed_steps_take_the_incremental_residual():
     assert n_incr > 0
     for g, s in zip(grouped, single):
         assert rel(g.get_state()[0], s.get_state()[0]) < 1e-8
+
+
+# ten uneven instances, two with a prime factor above 7 on an axis
+MANY = [(16, 16, 16), (24, 20, 12), (20, 16, 24), (32, 24, 16), (12, 18, 10), (40, 16, 8), (22, 13, 12),
+        (16, 11, 26), (30, 12, 20), (48, 8, 8)]
+
+
+def _own_schedule(wfft, s, precision, i):
+    """Instance i's own plan: column-tile widths cycling through 1, 2, 4 per instance and
+    pass, and on the x axis a radix schedule that differs from the built-in one where the
+    length allows (16 = 4 x 4 or 2 x 8)."""
+    pl = s.get_plan(precision)
+    for a in (1, 2):
+        for o in range(5):
+            trial = [[*r] for r in pl["bx"]]
+            trial[a][o] = (1, 2, 4)[(i + a + o) % 3]
+            try:
+                s.set_plan(precision, {**pl, "bx": trial})
+                pl = s.get_plan(precision)
+            except wfft.WfftError:
+                pass
+    if s.n[0] == 16:
+        cnt = [0, 2, 0, 0, 0, 0, 0] if i % 2 else [1, 0, 1, 0, 0, 0, 0]
+        s.set_radix(precision, 0, cnt)
+    return s.get_plan(precision)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-10)])
+def test_many_instances_with_their_own_schedules_match_single_steps(precision, tol):
+    """Ten instances, each with its own radix schedule and column-tile widths (the grouped
+    column passes then run one launch per width): grouped steps equal single-handle steps
+    with the same plans, and the instances' plans really differ."""
+    torch_cuda()
+    wfft = solver_lib()
+    probs = _problems(21, nsteps=3, sizes=MANY)
+    opt = lambda: wfft.default_options(precision=precision, tol=tol)  # noqa: E731
+    grouped = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
+    single = [wfft.Solver.from_problem(p, options=opt()) for p in probs]
+    precs = (wfft.FP64,) if precision == 0 else (wfft.FP64, wfft.MIXED)
+    widths = set()
+    for i, (g, s) in enumerate(zip(grouped, single)):
+        for pr in precs:
+            pl = _own_schedule(wfft, g, pr, i)
+            s.set_plan(pr, pl)
+            widths.add(tuple(pl["bx"][1]))
+    assert len(widths) > 1
+    for k in range(probs[0].nsteps):
+        U = np.stack([p.U[k] for p in probs])
+        rc, infos = wfft.batch_step(grouped, U)
+        assert rc == wfft.OK, infos
+        for s, p, inf in zip(single, probs, infos):
+            i1 = s.step(p.U[k])
+            assert inf["status"] == wfft.OK and inf["rel_res"] <= tol * 1.0001
+            assert abs(inf["iters"] - i1["iters"]) <= 1
+    for g, s in zip(grouped, single):
+        ug = g.get_state()[0]
+        us = s.get_state()[0]
+        assert rel(ug, us) < (1e-10 if precision == 0 else 1e-7)

@@ -126,3 +126,73 @@ def test_plane_wave_speeds_on_gpu_match_the_oracle_and_table_4(comp):
     v_orc = (orc[nsteps] - orc[n1]) / ((nsteps - n1) * dt)
     assert abs(v_gpu - v_orc) <= 1e-6 * c, (v_gpu, v_orc)
     assert abs(v_gpu - c) / c < 2e-2, (comp, v_gpu, c)
+
+
+def _materials():
+    """E (Pa) and rho of the paper's material table (tests/golden/table1_materials.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_materials.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            p = line.split()
+            if p and not p[0].startswith("#"):
+                out[p[0]] = (float(p[1]) * 1e9, float(p[2]))
+    return out
+
+
+@pytest.mark.parametrize("middle", ["Iron", "Uranium"])
+@pytest.mark.parametrize("ratio", [5, 10])
+def test_layered_bar_on_gpu_equals_the_layered_oracle_and_its_analytic_error(middle, ratio):
+    """Sec. 3.1, Table 3: the bar of Table 2 with iron or uranium between 0.6 and 1.2 m (read
+    in metres), as an N x 2 nu = 0 strip with a middle layer at N = 729; Delta t / CFL of the
+    paper's N = 6561 bar taken on the fastest layer, Table 2's final time.  The GPU's final
+    field equals the 1-D layered oracle's at the same N, and its error against the layered
+    d'Alembert solution (App. C, interfaces at the voxel faces) is the oracle's."""
+    from oracle import analytic, medium, newmark
+    torch_cuda()
+    wfft = solver_lib()
+    mat = _materials()
+    E = [mat[m][0] for m in ("Aluminium", middle, "Aluminium")]
+    rho = [mat[m][1] for m in ("Aluminium", middle, "Aluminium")]
+    c = [np.sqrt(e / r) for e, r in zip(E, rho)]
+    Z = [r * ci for r, ci in zip(rho, c)]
+    L, N = 2.0, 729
+    h = L / N
+    xc = (np.arange(N) + 0.5) * h
+    ph = ((xc >= 0.6) & (xc < 1.2)).astype(np.int64)
+    bounds = [0.0, np.argmax(ph) * h, (N - np.argmax(ph[::-1])) * h, L]
+    Uf = lambda t: inputs.bell_pulse(t, 1e-3, 5 * np.pi * c[0] / L, 4)
+    dt = ratio * (L / 6561) / max(c)
+    nsteps = int(round(3.919e-4 / dt))
+    U = np.zeros((nsteps, 3))
+    U[:, 0] = Uf(dt * np.arange(1, nsteps + 1))
+    # GPU: N x 2 plane-strain strip, nu = 0 in both materials
+    Cs = np.stack([inputs.voigt21_from_matrix(inputs.isotropic_voigt(E[k], 0.0)) for k in (0, 1)])
+    phase = np.broadcast_to(ph.astype(np.uint16), (1, 2, N)).copy()
+    mask = np.zeros((2, 1, 2, N), np.uint8)
+    mask[:, :, :, 0] = 1
+    prob = inputs.Problem(f"layered_{middle}_{N}", 2, (N, 2, 1), (h, h, h), dt, 0.25, 0.5, Cs,
+                          np.array([rho[0], rho[1]]), phase, mask, U, tol=1e-12)
+    s = wfft.Solver.from_problem(prob, options=wfft.default_options(tol=1e-12, maxit=400))
+    for k in range(nsteps):
+        info = s.step(U[k])
+        assert info["status"] == 0
+    u = s.get_state()[0]
+    s.close()
+    ux = u[0, 0]
+    assert np.abs(u[1]).max() <= 1e-12 * np.abs(ux).max()
+    assert np.abs(ux[1] - ux[0]).max() <= 1e-12 * np.abs(ux).max()
+    # oracle: the 1-D layered bar
+    med = medium.Medium(1, (N,), (L,), np.array([E[0], E[1]]).reshape(2, 1, 1, 1, 1), ph,
+                        np.where(ph == 1, rho[1], rho[0]))
+    m1 = np.zeros((1, N), bool)
+    m1[0, 0] = True
+    so, _ = newmark.NewmarkOracle(med, m1, dt, tol=1e-12).run(U)
+    uo = so.u[0]
+    assert np.linalg.norm(ux[0] - uo) / np.linalg.norm(uo) < 1e-9
+    ua = analytic.layered_dalembert_periodic(xc, nsteps * dt, bounds, c, Z, Uf)
+    e_gpu = np.linalg.norm(ux[0] - ua) / np.linalg.norm(ua)
+    e_orc = np.linalg.norm(uo - ua) / np.linalg.norm(ua)
+    assert abs(e_gpu - e_orc) <= 1e-6 * e_orc
+    assert e_gpu < 5e-2

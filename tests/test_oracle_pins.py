@@ -555,6 +555,24 @@ def test_conv_oracle_matches_direct_sum_and_finite_differences():
         assert abs(fd - gx[idx]) <= 1e-6 * max(1.0, abs(fd))
 
 
+def test_masked_mse_on_a_hand_computed_pair():
+    """The training loss of a pair is the mean over its free DOFs of (y - target)^2 (the
+    definition the library's trainer states); worked by hand on four DOFs, one prescribed:
+    ((1 - 0)^2 + (3 - 1)^2 + (4 - 2)^2) / 3 = 3, gradient 2 (y - target) / 3 on the free DOFs
+    and 0 on the prescribed one.  A divisor over all DOFs (9 / 4) or a mask ignored
+    ((1 + 4 + 4 + 25) / 4) would not give 3."""
+    from oracle import conv
+    pred = np.array([1.0, 7.0, 3.0, 4.0]).reshape(1, 1, 2, 2)
+    target = np.array([0.0, 2.0, 1.0, 2.0]).reshape(1, 1, 2, 2)
+    free = np.array([True, False, True, True]).reshape(1, 1, 2, 2)
+    L, g = conv.masked_mse(pred, target, free)
+    assert L == 3.0
+    assert np.array_equal(g.reshape(-1), np.array([2.0 / 3.0, 0.0, 4.0 / 3.0, 4.0 / 3.0]))
+    # no free DOF: the loss is 0 and so is the gradient
+    L0, g0 = conv.masked_mse(pred, target, np.zeros_like(free))
+    assert L0 == 0.0 and not g0.any()
+
+
 # --------------------------------------------------------------------------
 # explicit central-difference scheme (Sec. 2.3)
 # --------------------------------------------------------------------------
