@@ -201,7 +201,8 @@ def net_roofline(prof):
     peak, src = bf16_peak()
     per = d["ms"] / d["timed"]
     ach = d["flops"] / d["timed"] / (per * 1e-3) / 1e12
-    return {"kernel": "net_conv (bf16 mma.sync, f32 accumulate)", "bound": "tensor", "achieved": ach, "peak": peak,
+    return {"kernel": "net_conv (bf16 tcgen05.mma, f32 accumulators in tensor memory)", "bound": "tensor",
+            "achieved": ach, "peak": peak,
             "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src, "ms_per_launch": per,
             "launches": d["timed"], "ms_total": d["ms"], "traffic": None}
 

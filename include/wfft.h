@@ -262,6 +262,14 @@ WFFT_API int wfft_batch_step(wfft_handle** hs, int n, const double* U, wfft_step
  * 3 (dy+1) + (dx+1), output voxel x reads input voxel x + (dx, dy, dz) mod N)
  * followed by the FP32 biases b[cout_l]; cout_4 = 16 (only the first 3 are used).
  */
+/* Kernel of the network's forward convolutions (process-wide): 0 (default) = the tcgen05
+   kernel (5th-generation tensor cores, FP32 accumulators in tensor memory) for H = 32 on
+   grids with N1 % 8 == 0 and N2 % 16 == 0, the mma.sync kernel otherwise; 1 = the mma.sync
+   kernel everywhere (for comparing the two).  Returns the previous setting, or -1 for an
+   unknown kind.  A tcgen05 convolution whose bounded wait expires makes the step that ran
+   it return WFFT_ETIMEOUT without committing (wfft_net_forward / wfft_trainer_fit: the same
+   status). */
+WFFT_API int wfft_net_conv_kernel(int kind);
 /* Bytes of a model blob of hidden width H (0 unless H is 16 or 32). */
 WFFT_API size_t wfft_model_bytes(int hidden);
 /* Seeded initial model: He-normal weights for layers 1-3, zero last layer (so the

@@ -1011,6 +1011,8 @@ extern "C" int wfft_step(wfft_handle* h, const double U[3], wfft_step_info* info
   }
   h->last_resid_on_x = false;
   int status = solve_core(h, info, use_au, inner_guess);
+  // a learned warm start whose tensor-core convolution gave up waiting: not committed
+  if (warm == WFFT_WARM_LEARNED && status == WFFT_OK && net_conv_timed_out()) status = WFFT_ETIMEOUT;
   // the stored A x is A u_n only if the last residual evaluation ran on the final x
   h->au_valid = status == WFFT_OK && mixed && h->last_resid_on_x && !h->host_sc[0].zero_free;
   if (status == WFFT_OK) {

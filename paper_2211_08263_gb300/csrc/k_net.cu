@@ -36,6 +36,9 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
+// Set by a tcgen05 convolution whose bounded wait on the tensor cores expired.
+__device__ int g_conv_tc_err;
+
 constexpr int TX = 16, TY = 8, TZ = 2;            // output tile
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HV = HX * HY * HZ;                   // halo voxels
@@ -340,6 +343,8 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad(ConvArgs p, float* dW, 
   }
 }
 
+#include "conv_tc.cuh"
+
 // ---------------------------------------------------------------------------
 // elementwise kernels
 // ---------------------------------------------------------------------------
@@ -590,6 +595,31 @@ void launch_wgrad(const ConvArgs& p, float* dW, float* db, cudaStream_t st) {
 
 int aux_blocks(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, kAuxBlocks)); }
 
+// Forward layers run on the tcgen05 kernel where the grid splits into its 8 x 16 tiles
+// (wfft_net_conv_kernel(1) selects the mma.sync kernel everywhere, for comparisons).
+int g_conv_kernel = 0;
+bool tc_grid_ok(const ConvArgs& p) { return g_conv_kernel == 0 && p.n1 % tcconv::TX == 0 && p.n2 % tcconv::TY == 0; }
+
+int* conv_tc_err_ptr() {
+  void* q = nullptr;
+  return cudaGetSymbolAddress(&q, g_conv_tc_err) == cudaSuccess ? reinterpret_cast<int*>(q) : nullptr;
+}
+
+template <int CIN, int COUT, int EPI>
+void launch_conv_tc(const ConvArgs& p, cudaStream_t st) {
+  constexpr size_t sm = tcconv::Geo<CIN, COUT>::SMEM;
+  static std::once_flag once;
+  std::call_once(once, [] { set_smem_attr(k_conv_tc<CIN, COUT, EPI>, sm); });
+  const long long units = (long long)(p.n1 / tcconv::TX) * (p.n2 / tcconv::TY) * ((p.n3 + tcconv::ZC - 1) / tcconv::ZC);
+  const long long grid = std::min<long long>(units, num_sms());
+  const int cout_alg = EPI == EPI_WARM || EPI == EPI_LINEAR ? kNetOut : COUT;
+  const double fl = 2.0 * 27 * CIN * cout_alg * (double)p.V;
+  const double by = (double)p.V * (2.0 * CIN + (EPI == EPI_WARM ? 8.0 * p.c : (EPI == EPI_LINEAR ? 16.0 : 2.0 * COUT)));
+  int* err = conv_tc_err_ptr();
+  prof_launch(1, KK_NET_CONV, by, fl, st,
+              [&] { k_conv_tc<CIN, COUT, EPI><<<(int)grid, tcconv::kThreads, sm, st>>>(p, err); });
+}
+
 // Layer l of a network with hidden width H: conv + epilogue.
 template <int H>
 void layer_fwd(const NetDev& n, int l, ConvArgs p, const bf16* in, void* out, int epi, cudaStream_t st) {
@@ -597,6 +627,15 @@ void layer_fwd(const NetDev& n, int l, ConvArgs p, const bf16* in, void* out, in
   p.W = n.wb + n.d.woff[l];
   p.bias = n.theta + n.d.boff[l];
   p.out = out;
+  if constexpr (H == 32) {
+    if (tc_grid_ok(p)) {
+      if (l == 0) launch_conv_tc<kNetIn, H, EPI_RELU>(p, st);
+      else if (l < 3) launch_conv_tc<H, H, EPI_RELU>(p, st);
+      else if (epi == EPI_LINEAR) launch_conv_tc<H, kNetOutPad, EPI_LINEAR>(p, st);
+      else launch_conv_tc<H, kNetOutPad, EPI_WARM>(p, st);
+      return;
+    }
+  }
   if (l == 0) {
     launch_conv<kNetIn, H, EPI_RELU>(p, st);
   } else if (l < 3) {
@@ -696,6 +735,26 @@ cudaError_t dmalloc(T** p, size_t bytes) {
 }
 
 }  // namespace
+
+namespace wfft {
+// Reads and clears the error word of the tcgen05 convolutions (synchronises the device).
+bool net_conv_timed_out() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_conv_tc_err, sizeof(int)) != cudaSuccess) return false;
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_conv_tc_err, &zero, sizeof(int));
+  }
+  return v != 0;
+}
+}  // namespace wfft
+
+extern "C" int wfft_net_conv_kernel(int kind) {
+  if (kind != 0 && kind != 1) return -1;
+  const int prev = g_conv_kernel;
+  g_conv_kernel = kind;
+  return prev;
+}
 
 namespace wfft {
 
@@ -1118,6 +1177,7 @@ extern "C" int wfft_trainer_fit(wfft_trainer* t, int epochs, int batch, double l
     last = nf > 0 ? ls / nf : 0.0;
   }
   TCK(t, cudaGetLastError());
+  if (net_conv_timed_out()) return tfail(t, WFFT_ETIMEOUT, "a tensor-core convolution's wait expired");
   if (loss_out) *loss_out = last;
   return WFFT_OK;
 }
@@ -1163,6 +1223,8 @@ extern "C" int wfft_net_forward(const void* blob, size_t bytes, const int n[3], 
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
       rc = tfail(nullptr, WFFT_ECUDA, cudaGetErrorString(e));
+    } else if (net_conv_timed_out()) {
+      rc = tfail(nullptr, WFFT_ETIMEOUT, "a tensor-core convolution's wait expired");
     } else {
       for (long long i = 0; i < V; ++i)
         for (int k = 0; k < kNetOut; ++k) y[i * kNetOut + k] = y4[i * 4 + k];

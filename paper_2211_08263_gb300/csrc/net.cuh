@@ -81,6 +81,10 @@ struct NetWork {
 int net_work_alloc(NetWork* w, long long V, int hidden);
 void net_work_free(NetWork* w);
 
+// Reads and clears the error word of the tensor-core convolutions (a bounded wait expired);
+// synchronises the device.
+bool net_conv_timed_out();
+
 // delta[k][vox] = dt v + dt^2/2 a (+ s y, y = net(features), when n != null) on free DOFs, 0 on Gamma.
 void net_warm(const NetDev* n, NetWork* w, const WarmArgs& a, float* delta, cudaStream_t st);
 

@@ -157,7 +157,8 @@ struct Cost {
   double xfft(double ncomp) const { return 2.5 * V * lg1 * ncomp; }
   double colfft(int axis, double ncomp) const { return 5.0 * Vh * (axis == 1 ? lg2 : lg3) * ncomp; }
 };
-static inline int prec_index(size_t st) { return st == 8 ? 0 : 1; }
+// profile slot of an arithmetic type: 0 FP64, 1 FP32
+template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? 0 : 1; }
 
 // ---------------------------------------------------------------------------
 // launch helpers: one code path for single-instance and grouped launches
@@ -235,7 +236,7 @@ struct Launch {
 
 template <typename T, int B>
 static void launch_xfwd(const Launch<T, B>& L, int pre, int in_slot, cudaStream_t st) {
-  const int pi = prec_index(sizeof(T));
+  const int pi = prec_of<T>();
   const int nb = L.grid(GEO_X);
   const size_t sm = L.smem(GEO_X);
   const BatchArgs<T> ba = L.args(GEO_X);
@@ -294,7 +295,7 @@ static void launch_colplain_bx(const Launch<T, B>& L, int op, int axis, int ncom
         f = k.colfft(axis, ncomp);
       },
       by, fl);
-  const int pi = prec_index(sizeof(T));
+  const int pi = prec_of<T>();
   if (op == OP_FWD)
     prof_launch(pi, KK_COL_FWD, by, fl, st,
                 [&] { k_colplain<T, OP_FWD, BX, B><<<grid, kColThreadsPlain, sm, st>>>(d, ba, axis); });
@@ -336,7 +337,7 @@ static void launch_colop_bx(const Launch<T, B>& L, int axis, cudaStream_t st) {
   const AxisPlan& ap = L.P.h.ax[axis];
   const bool only16 = ap.cnt[6] > 0 && !ap.cnt[0] && !ap.cnt[1] && !ap.cnt[2] && !ap.cnt[3] && !ap.cnt[4] &&
                       !ap.cnt[5] && !ap.prime;
-  prof_launch(prec_index(sizeof(T)), kind, by, fl, st, [&] {
+  prof_launch(prec_of<T>(), kind, by, fl, st, [&] {
     if (!d3)
       k_colop<T, OP, BX, kSmall, B><<<nb, kColThreadsOp, sm, st>>>(d, ba, axis);
     else if constexpr (B == 0 && sizeof(T) == 4) {
@@ -413,7 +414,7 @@ static bool x_stage_ok(const Launch<T, B>& L) {
 template <typename T, int B>
 static void launch_xinv(const Launch<T, B>& L, int post, int in_slot, int out_slot, int masked, int want_dot,
                         cudaStream_t st) {
-  const int pi = prec_index(sizeof(T));
+  const int pi = prec_of<T>();
   const int nb = L.grid(GEO_X);
   size_t sm = L.smem(GEO_X);
   int stage = 0;
@@ -488,7 +489,7 @@ static void launch_xmid(const Launch<T, B>& L, cudaStream_t st) {
         f = 2 * k.xfft(k.s) + (Q.h.ndim == 3 ? 66.0 : 15.0) * k.V;
       },
       by, fl);
-  prof_launch(prec_index(sizeof(T)), KK_XMID, by, fl, st, [&] { k_xmid<T, B><<<nb, 256, sm, st>>>(d, ba, stage); });
+  prof_launch(prec_of<T>(), KK_XMID, by, fl, st, [&] { k_xmid<T, B><<<nb, 256, sm, st>>>(d, ba, stage); });
 }
 
 template <typename T, int B>
@@ -595,14 +596,14 @@ void launch_rfft3(const Plan<T>& P, int dir, int ncomp, int real_slot, cudaStrea
   const int axes[2] = {1, 2};
   const Launch<T, 0> L{P, nullptr};
   if (dir < 0) {
-    prof_launch(prec_index(sizeof(T)), KK_XFWD_PLAIN, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
+    prof_launch(prec_of<T>(), KK_XFWD_PLAIN, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
                 Cost<T>(D).xfft(ncomp), st, [&] { k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, -1, real_slot); });
     for (int a : axes)
       if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T, 0>(L, OP_FWD, a, ncomp, st);
   } else {
     for (int a : {2, 1})
       if ((a == 1 ? D.n2 : D.n3) > 1) launch_col<T, 0>(L, OP_INV, a, ncomp, st);
-    prof_launch(prec_index(sizeof(T)), KK_XINV_PREC, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
+    prof_launch(prec_of<T>(), KK_XINV_PREC, Cost<T>(D).real(ncomp) + Cost<T>(D).spec(ncomp),
                 Cost<T>(D).xfft(ncomp), st, [&] { k_xplain<T><<<nb, g.thr, sm, st>>>(P.d, lx, ncomp, +1, real_slot); });
   }
 }

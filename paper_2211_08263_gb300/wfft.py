@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
     lib.wfft_operator_bound.argtypes = [i, P(i), P(d), vp, vp, C.c_longlong, d, P(d)]
     lib.wfft_axis_plan.argtypes = [i, P(i), P(i)]
     lib.wfft_precond_noalloc.argtypes = [P(Grid), P(d), d, d, vp, vp, vp]
+    lib.wfft_net_conv_kernel.argtypes = [i]
     lib.wfft_model_bytes.argtypes = [i]
     lib.wfft_model_bytes.restype = C.c_size_t
     lib.wfft_model_init.argtypes = [i, C.c_ulonglong, vp, C.c_size_t]
@@ -412,6 +413,12 @@ _HEADER_INTS = 8
 def _raise_global(rc: int):
     if rc != OK:
         raise WfftError(rc, load().wfft_last_error(None).decode())
+
+
+def net_conv_kernel(kind: int) -> int:
+    """Network forward convolutions: 0 = tcgen05 where the grid allows, 1 = mma.sync
+    (wfft_net_conv_kernel); returns the previous setting."""
+    return load().wfft_net_conv_kernel(int(kind))
 
 
 def model_bytes(hidden: int) -> int:

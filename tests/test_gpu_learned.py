@@ -34,7 +34,7 @@ def oracle_params(wfft, blob):
     return hidden, [(bf16(W), b.astype(np.float64)) for W, b in params]
 
 
-GRIDS = [(20, 12, 6), (5, 3, 1), (32, 16, 4)]
+GRIDS = [(20, 12, 6), (5, 3, 1), (32, 16, 4), (16, 32, 8), (8, 16, 1), (24, 48, 40)]
 
 
 @pytest.mark.parametrize("hidden", [16, 32])
@@ -53,6 +53,34 @@ def test_net_forward_matches_fp64_reference(hidden, n):
     yo = yo.reshape(V, 16)[:, :3]
     assert np.all(np.isfinite(y))
     assert rel(y, yo) < 2e-2, rel(y, yo)
+
+
+@pytest.mark.parametrize("n", [(32, 16, 4), (8, 16, 1), (24, 48, 40), (16, 32, 35)])
+def test_tcgen05_and_mma_sync_forward_kernels_agree(n):
+    """Grids of whole 8 x 16 tiles run the hidden-32 network's forward convolutions on the
+    tcgen05 kernel (z chunks of 32 planes, periodic wrap in every axis); the mma.sync kernel
+    computes the same products in another order: both agree with each other to the BF16
+    rounding of the hidden activations, and with the FP64 reference."""
+    from oracle import conv
+    torch_cuda()
+    wfft = solver_lib()
+    rng = np.random.default_rng(12)
+    V = n[0] * n[1] * n[2]
+    x = bf16(rng.standard_normal((V, 16)))
+    blob = random_blob(wfft, 32, 4)
+    prev = wfft.net_conv_kernel(0)
+    try:
+        y_tc = wfft.net_forward(blob, n, x)
+        wfft.net_conv_kernel(1)
+        y_ms = wfft.net_forward(blob, n, x)
+    finally:
+        wfft.net_conv_kernel(prev)
+    _, P = oracle_params(wfft, blob)
+    yo, _ = conv.net_forward(x.reshape(n[2], n[1], n[0], 16), P)
+    yo = yo.reshape(V, 16)[:, :3]
+    assert np.all(np.isfinite(y_tc))
+    assert rel(y_tc, y_ms) < 1e-2, rel(y_tc, y_ms)
+    assert rel(y_tc, yo) < 2e-2 and rel(y_ms, yo) < 2e-2
 
 
 def bf16_pipeline_grads(conv, X, P, t16, free):
@@ -152,14 +180,16 @@ def test_untrained_model_reproduces_taylor_warm_start_bitwise():
     assert [i["iters"] for i in it_t] == [i["iters"] for i in it_l]
 
 
+@pytest.mark.parametrize("n", [20, 32])
 @pytest.mark.parametrize("precision,bar", [(0, 1e-10), (1, 1e-6)])
-def test_learned_warm_start_keeps_the_solution(precision, bar):
+def test_learned_warm_start_keeps_the_solution(precision, bar, n):
     """Any network (here a random one) only moves the initial guess: the converged
-    displacements match the oracle and the plain solver within the solver bars."""
+    displacements match the oracle and the plain solver within the solver bars (n = 32: the
+    tcgen05 convolutions, n = 20: the mma.sync ones)."""
     from oracle import newmark
     torch_cuda()
     wfft = solver_lib()
-    prob = _traj_problem(20, 6, 8)
+    prob = _traj_problem(n, 6, 8)
     blob = random_blob(wfft, 32, 2, last_scale=3.0)
     tol = 1e-12 if precision == 0 else 1e-10
     u_l, infos = _run(wfft, prob, precision, wfft.WARM_LEARNED, blob, tol=tol)
