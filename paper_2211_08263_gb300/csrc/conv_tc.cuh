@@ -14,10 +14,10 @@
 // in tensor memory, so the MMAs of plane z + 2 run while output plane z - 1 is formed).
 // Row layout: row (dz + 1) COUT + co of the M = 128 rows (96 carry work for COUT = 32, the
 // rest are zero weights).  A warp reads only its own 32-lane quarter of tensor memory, so
-// the epilogue moves each block to shared memory ([dz][channel][voxel], rows padded to
-// 129 floats: the 32 channels a warp writes fall in 32 banks) and every thread then sums
-// the three blocks for its voxel and half of the channels, adds the bias and stores 16-byte
-// vectors of the channels-last output.
+// the epilogue moves each block to shared memory ([dz][voxel][channel], a voxel's row
+// padded to COUT + 4 floats so that 16-byte reads of consecutive voxels spread over the
+// banks) and every thread then sums the three blocks for its voxel and half of the
+// channels, adds the bias and stores 16-byte vectors of the channels-last output.
 //
 // Operand layouts (K-major, no swizzle): a core matrix is 8 rows of 16 bytes (8 BF16).
 //   A (weights): [offset (dx,dy)][K step of 16][chunk of 8][row group][8 rows][16 B];
