@@ -77,6 +77,8 @@ struct Geo {
   // at least 116 KB: one CTA per SM (each holds all 512 tensor-memory columns)
   static constexpr size_t SMEM = USED > 116 * 1024 ? (size_t)USED : (size_t)116 * 1024;
   static_assert(CIN == 16 || CIN == 32, "input channels");
+  // descriptor address fields are in 16-byte units and must not carry past 14 bits
+  static_assert(PLANE % 16 == 0 && ROWB % 16 == 0 && SMEM <= 227 * 1024, "shared-memory layout");
   static_assert(COUT == 16 || COUT == 32, "output channels");
 };
 
@@ -227,7 +229,11 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
   const long long units = (long long)nux * nuy * nzc;
 
   if (warp >= kLoadWarp0 && warp < kMmaWarp) {
-    // ---- loads: input plane j of a unit into stage g % NST once the MMAs of plane g - NST are done
+    // ---- loads: input plane j of a unit into stage g % NST once the MMAs of plane g - NST are done.
+    // A thread copies the same (chunk, halo voxel) slots of every plane of a unit: their
+    // shared-memory offsets and in-plane global offsets are set once per unit.
+    constexpr int NSLOT = HX * HY * G::KCH;
+    constexpr int PER = (NSLOT + kLoadThreads - 1) / kLoadThreads;
     const int lt = tid - kLoadWarp0 * 32;
     long long gp = 0;
     for (long long u = blockIdx.x; u < units; u += gridDim.x) {
@@ -236,22 +242,35 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
       const int uy = (int)(r1 % nuy), zc = (int)(r1 / nuy);
       const int x0 = ux * TX, y0 = uy * TY, zb = zc * ZC;
       const int NP = min(ZC, p.n3 - zb) + 2;
+      uint32_t soff[PER];
+      long long goff[PER];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int id = lt + i * kLoadThreads;
+        soff[i] = 0;
+        goff[i] = -1;
+        if (id < NSLOT) {
+          const int c8 = id % G::KCH, hv = id / G::KCH;
+          const int hx = hv % HX, hy = hv / HX;
+          int x = x0 - 1 + hx, y = y0 - 1 + hy;
+          x += x < 0 ? p.n1 : (x >= p.n1 ? -p.n1 : 0);
+          y += y < 0 ? p.n2 : (y >= p.n2 ? -p.n2 : 0);
+          soff[i] = (uint32_t)(c8 * kChunkStride + (hy * HX + hx) * 16);
+          goff[i] = ((long long)y * p.n1 + x) * CIN + 8 * c8;
+        }
+      }
+      const long long plane_elems = (long long)p.n1 * p.n2 * CIN;
       for (int j = 0; j < NP; ++j) {
         const long long g = gp + j;
         const int st = (int)(g % NST);
         const bool ok = g < NST || mbar_wait(smem_u32(st_empty + st), (uint32_t)(((g - NST) / NST) & 1), abort_flag);
         if (!__all_sync(0xffffffffu, ok)) break;
         const int z = wrapi(zb - 1 + j, p.n3);
-        unsigned char* dst = Ps + (size_t)st * G::PLANE;
-        for (int id = lt; id < HX * HY * G::KCH; id += kLoadThreads) {
-          const int c8 = id % G::KCH, hv = id / G::KCH;
-          const int hx = hv % HX, hy = hv / HX;
-          int x = x0 - 1 + hx, y = y0 - 1 + hy;
-          x += x < 0 ? p.n1 : (x >= p.n1 ? -p.n1 : 0);
-          y += y < 0 ? p.n2 : (y >= p.n2 ? -p.n2 : 0);
-          const long long vox = ((long long)z * p.n2 + y) * p.n1 + x;
-          cp16(smem_u32(dst + c8 * kChunkStride + (hy * HX + hx) * 16), p.in + vox * CIN + 8 * c8);
-        }
+        const uint32_t dst = smem_u32(Ps + (size_t)st * G::PLANE);
+        const bf16* src = p.in + (long long)z * plane_elems;
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+          if (goff[i] >= 0) cp16(dst + soff[i], src + goff[i]);
         cp_arrive(smem_u32(st_full + st));
       }
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
@@ -259,9 +278,13 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
     }
   } else if (warp == kMmaWarp) {
     // ---- MMAs of plane g into accumulator g % NDB (free once output g - NDB has read it);
-    // the whole warp waits, lane 0 issues
+    // the whole warp waits, lane 0 issues.  The descriptors of a plane's MMAs are the stage's
+    // and the weights' base descriptors plus compile-time offsets (address field in 16-byte
+    // units; every shared address is below 256 KB, so the 14-bit field never carries), so
+    // the issue loop is a handful of instructions per MMA and keeps the tensor pipe fed.
     const uint32_t idesc = idesc_bf16_f32(128, NV);
-    const uint32_t ab = smem_u32(As);
+    const uint64_t adesc = smem_desc(smem_u32(As), G::ROWB, 128);
+    const uint64_t bdesc = smem_desc(smem_u32(Ps), kChunkStride, HX * 16);
     long long gp = 0;
     bool run = true;
     for (long long u = blockIdx.x; u < units && run; u += gridDim.x) {
@@ -280,19 +303,15 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
         if (lane == 0) {
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
           tc_fence_after();
-          const uint32_t pb = smem_u32(Ps + (size_t)st * G::PLANE);
+          const uint64_t bd = bdesc + (uint64_t)((st * G::PLANE) >> 4);
           const uint32_t dt = tbase + (uint32_t)(db * NV);
-          int first = 1;
-#pragma unroll 1
+#pragma unroll
           for (int o9 = 0; o9 < 9; ++o9) {
-            const int dy = o9 / 3, dx = o9 % 3;
 #pragma unroll
             for (int kh = 0; kh < G::KH; ++kh) {
-              const uint64_t ad = smem_desc(ab + (uint32_t)((o9 * G::KH + kh) * 2 * G::ROWB), G::ROWB, 128);
-              const uint64_t bd = smem_desc(pb + (uint32_t)((dy * HX + dx) * 16 + kh * 2 * kChunkStride),
-                                            kChunkStride, HX * 16);
-              mma_f16(dt, ad, bd, idesc, first ? 0 : 1);
-              first = 0;
+              const uint32_t aoff = (uint32_t)(((o9 * G::KH + kh) * 2 * G::ROWB) >> 4);
+              const uint32_t boff = (uint32_t)((((o9 / 3) * HX + o9 % 3) * 16 + kh * 2 * kChunkStride) >> 4);
+              mma_f16(dt, adesc + aoff, bd + boff, idesc, (o9 | kh) ? 1 : 0);
             }
           }
           mma_commit(smem_u32(acc_full + db));
