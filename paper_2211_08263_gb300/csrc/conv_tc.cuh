@@ -49,7 +49,7 @@ constexpr int TX = 8, TY = 16;            // output tile of a plane (MMA N = 128
 constexpr int HX = TX + 2, HY = TY + 2;   // halo plane
 constexpr int NV = TX * TY;
 constexpr int ZC = 32;                    // output planes per work unit
-constexpr int NST = 4;                    // input-plane stages
+constexpr int NST = 3;                    // input-plane stages
 constexpr int NDB = 4;                    // accumulator buffers of 128 columns
 constexpr int kThreads = 416;             // warps 0-7 epilogue, 8-11 loads, 12 MMA issue
 constexpr int kEpiThreads = 256;
@@ -71,10 +71,11 @@ struct Geo {
   static constexpr int OFF_A = 0;
   static constexpr int OFF_P = ABYTES;
   static constexpr int OFF_S = OFF_P + NST * PLANE;
-  static constexpr int OFF_BAR = OFF_S + SBYTES;          // mbarriers: acc full / empty, stage full / empty
+  static constexpr int OFF_BAR = OFF_S + 2 * SBYTES;      // mbarriers: acc full / empty, stage full / empty
   static constexpr int OFF_TAB = OFF_BAR + 8 * (2 * NDB + 2 * NST);  // TMEM slot, abort flag
   static constexpr int USED = OFF_TAB + 24;
-  // at least 116 KB: one CTA per SM (each holds all 512 tensor-memory columns)
+  // two exchange buffers (one per epilogue group); at least 116 KB: one CTA per SM (each
+  // holds all 512 tensor-memory columns)
   static constexpr size_t SMEM = USED > 116 * 1024 ? (size_t)USED : (size_t)116 * 1024;
   static_assert(CIN == 16 || CIN == 32, "input channels");
   // descriptor address fields are in 16-byte units and must not carry past 14 bits
@@ -126,21 +127,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint32_t bar, uint32_t count = 1) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar), "r"(count) : "memory");
 }
 // arrive on bar once this thread's earlier cp.async copies have landed
 __device__ __forceinline__ void cp_arrive(uint32_t bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;\n" ::: "memory"); }
-// true on every epilogue thread iff pred holds on all 256 (named barrier 1 with an AND reduction)
-__device__ __forceinline__ bool epi_all(bool pred) {
+// Named barrier `id` of one epilogue group (128 threads).
+__device__ __forceinline__ void epi_sync(uint32_t id) { asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory"); }
+// true on every thread of the group iff pred holds on all 128 (barrier `id` with an AND reduction)
+__device__ __forceinline__ bool epi_all(uint32_t id, bool pred) {
   uint32_t r;
   asm volatile(
-      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, 256, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %2, 0;\nbar.red.and.pred q, %1, 128, p;\nselp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"((uint32_t)pred)
+      : "r"(id), "r"((uint32_t)pred)
       : "memory");
   return r != 0;
 }
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
   if (tid == 0) {
     for (int b = 0; b < NDB; ++b) {
       mbar_init(smem_u32(acc_full + b), 1);
-      mbar_init(smem_u32(acc_empty + b), 1);
+      mbar_init(smem_u32(acc_empty + b), 3);  // the three outputs that read a plane's blocks
     }
     for (int b = 0; b < NST; ++b) {
       mbar_init(smem_u32(st_full + b), kLoadThreads);
@@ -323,13 +325,20 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
       gp += NP;
     }
   } else {
-    // ---- epilogue (warps 0-7): output plane k of a unit from planes k, k + 1, k + 2; warps w
-    // and w + 4 share lane quarter w % 4 and take 64 columns each
-    const int q = warp & 3, half = warp >> 2;
-    constexpr int NB = EPI == EPI_RELU ? COUT / 2 : 4;
+    // ---- epilogue (warps 0-7): two groups of four warps (warps 4G .. 4G + 3, one per lane
+    // quarter) take alternate output planes of a unit (group G: k = G, G + 2, ...), each with
+    // its own exchange buffer and named barrier, so that one group's exchange runs while the
+    // other sums and stores.  Output plane k reads the blocks of the accumulators of planes
+    // k, k + 1, k + 2, and an accumulator is free once its three readers (outputs j, j - 1,
+    // j - 2) have read it: every output arrives on all three after its reads; at the ends of
+    // a unit the first and last outputs arrive for the readers that do not exist.
+    const int q = warp & 3, grp = warp >> 2, gt = tid & 127;
+    const uint32_t barid = 1 + grp;
+    float* Sg = S + (size_t)grp * (G::SBYTES / 4);
+    constexpr int NB = EPI == EPI_RELU ? COUT : 4;
     float bias[NB];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) bias[c] = p.bias[(EPI == EPI_RELU ? (tid / NV) * (COUT / 2) : 0) + c];
+    for (int c = 0; c < NB; ++c) bias[c] = p.bias[c];
     long long gp = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
@@ -338,9 +347,9 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
       const int uy = (int)(r1 % nuy), zc = (int)(r1 / nuy);
       const int x0 = ux * TX, y0 = uy * TY, zb = zc * ZC;
       const int nz = min(ZC, p.n3 - zb);
-      for (int k = 0; k < nz; ++k) {
+      for (int k = grp; k < nz; k += 2) {
         const long long g = gp + k;
-        ok = epi_all(mbar_wait(smem_u32(acc_full + ((g + 2) % NDB)), (uint32_t)(((g + 2) / NDB) & 1), abort_flag));
+        ok = epi_all(barid, mbar_wait(smem_u32(acc_full + ((g + 2) % NDB)), (uint32_t)(((g + 2) / NDB) & 1), abort_flag));
         if (!ok) break;
         tc_fence_after();
         if (32 * q < 3 * COUT) {
@@ -350,14 +359,14 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
 #pragma unroll 1
           for (int bb = (32 * q) / COUT; bb <= (32 * q + 31) / COUT && bb < 3; ++bb) {
             const uint32_t tb = tq + (uint32_t)(((g + bb) % NDB) * NV);
-            {
-              const int c0 = half * 64;
+#pragma unroll 1
+            for (int c0 = 0; c0 < NV; c0 += 64) {
               uint32_t v0[32], v1[32];
               tmem_ld32(tb + c0, v0);
               tmem_ld32(tb + c0 + 32, v1);
               tmem_wait();
               if (b == bb) {
-                float* dst = S + (b * NV + c0) * G::SROW + co;
+                float* dst = Sg + (b * NV + c0) * G::SROW + co;
 #pragma unroll
                 for (int e = 0; e < 32; ++e) dst[e * G::SROW] = __uint_as_float(v0[e]);
 #pragma unroll
@@ -367,52 +376,46 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
           }
         }
         tc_fence_before();
-        epi_sync();
-        // accumulator of plane k is no longer needed (block 0 was its last reader); at the
-        // unit's last output, planes k + 1 and k + 2 are done too
-        if (tid == 0) {
-          mbar_arrive(smem_u32(acc_empty + (g % NDB)));
-          if (k == nz - 1) {
-            mbar_arrive(smem_u32(acc_empty + ((g + 1) % NDB)));
-            mbar_arrive(smem_u32(acc_empty + ((g + 2) % NDB)));
-          }
+        epi_sync(barid);
+        if (gt == 0) {
+          mbar_arrive(smem_u32(acc_empty + (g % NDB)), k == 0 ? 3u : 1u);
+          mbar_arrive(smem_u32(acc_empty + ((g + 1) % NDB)), 1u + (k == 0) + (k == nz - 1));
+          mbar_arrive(smem_u32(acc_empty + ((g + 2) % NDB)), k == nz - 1 ? 3u : 1u);
         }
         {
-          const int v = tid & (NV - 1), part = tid / NV;  // voxel, half of the channels
+          const int v = gt;  // voxel of the tile
           const int x = x0 + (v & 7), y = y0 + (v >> 3), z = zb + k;
           const long long vox = ((long long)z * p.n2 + y) * p.n1 + x;
-          const float* s0 = S + (0 * NV + v) * G::SROW;
-          const float* s1 = S + (1 * NV + v) * G::SROW;
-          const float* s2 = S + (2 * NV + v) * G::SROW;
+          const float* s0 = Sg + (0 * NV + v) * G::SROW;
+          const float* s1 = Sg + (1 * NV + v) * G::SROW;
+          const float* s2 = Sg + (2 * NV + v) * G::SROW;
           if (EPI == EPI_RELU) {
-            constexpr int CH = COUT / 2;
-            uint32_t pk[CH / 2];
+            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(p.out) + vox * COUT);
 #pragma unroll
-            for (int cc = 0; cc < CH; cc += 4) {
-              const int c = part * CH + cc;
-              const float4 a = *reinterpret_cast<const float4*>(s0 + c);
-              const float4 b4 = *reinterpret_cast<const float4*>(s1 + c);
-              const float4 d = *reinterpret_cast<const float4*>(s2 + c);
-              const float y0v = fmaxf(a.x + b4.x + d.x + bias[cc], 0.f), y1v = fmaxf(a.y + b4.y + d.y + bias[cc + 1], 0.f);
-              const float y2v = fmaxf(a.z + b4.z + d.z + bias[cc + 2], 0.f), y3v = fmaxf(a.w + b4.w + d.w + bias[cc + 3], 0.f);
-              __nv_bfloat162 h0 = __floats2bfloat162_rn(y0v, y1v), h1 = __floats2bfloat162_rn(y2v, y3v);
-              pk[cc >> 1] = *reinterpret_cast<uint32_t*>(&h0);
-              pk[(cc >> 1) + 1] = *reinterpret_cast<uint32_t*>(&h1);
+            for (int c8 = 0; c8 < COUT; c8 += 8) {
+              uint32_t pk[4];
+#pragma unroll
+              for (int cc = 0; cc < 8; cc += 4) {
+                const int c = c8 + cc;
+                const float4 a = *reinterpret_cast<const float4*>(s0 + c);
+                const float4 b4 = *reinterpret_cast<const float4*>(s1 + c);
+                const float4 d = *reinterpret_cast<const float4*>(s2 + c);
+                const float y0v = fmaxf(a.x + b4.x + d.x + bias[c], 0.f), y1v = fmaxf(a.y + b4.y + d.y + bias[c + 1], 0.f);
+                const float y2v = fmaxf(a.z + b4.z + d.z + bias[c + 2], 0.f), y3v = fmaxf(a.w + b4.w + d.w + bias[c + 3], 0.f);
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(y0v, y1v), h1 = __floats2bfloat162_rn(y2v, y3v);
+                pk[cc >> 1] = *reinterpret_cast<uint32_t*>(&h0);
+                pk[(cc >> 1) + 1] = *reinterpret_cast<uint32_t*>(&h1);
+              }
+              dst[c8 / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
-            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(p.out) + vox * COUT + part * CH);
-#pragma unroll
-            for (int qq = 0; qq < CH / 8; ++qq)
-              dst[qq] = make_uint4(pk[4 * qq], pk[4 * qq + 1], pk[4 * qq + 2], pk[4 * qq + 3]);
           } else if (EPI == EPI_LINEAR) {
-            if (part == 0) {
-              const float4 a = *reinterpret_cast<const float4*>(s0);
-              const float4 b4 = *reinterpret_cast<const float4*>(s1);
-              const float4 d = *reinterpret_cast<const float4*>(s2);
-              reinterpret_cast<float4*>(p.out)[vox] =
-                  make_float4(a.x + b4.x + d.x + bias[0], a.y + b4.y + d.y + bias[1], a.z + b4.z + d.z + bias[2],
-                              a.w + b4.w + d.w + bias[3]);
-            }
-          } else if (part == 0) {  // EPI_WARM: delta += s (y + b) on free DOFs
+            const float4 a = *reinterpret_cast<const float4*>(s0);
+            const float4 b4 = *reinterpret_cast<const float4*>(s1);
+            const float4 d = *reinterpret_cast<const float4*>(s2);
+            reinterpret_cast<float4*>(p.out)[vox] =
+                make_float4(a.x + b4.x + d.x + bias[0], a.y + b4.y + d.y + bias[1], a.z + b4.z + d.z + bias[2],
+                            a.w + b4.w + d.w + bias[3]);
+          } else {  // EPI_WARM: delta += s (y + b) on free DOFs
             const float s = p.scale[0];
             const uint8_t mk = p.mask ? p.mask[vox] : (uint8_t)0;
             float* delta = reinterpret_cast<float*>(p.out);
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
               if (c < p.c && !((mk >> c) & 1)) delta[(long long)c * p.V + vox] = d3[c] + s * y3[c];
           }
         }
-        epi_sync();  // the exchange buffer is reused by the next output
+        epi_sync(barid);  // the group's exchange buffer is reused by its next output
       }
       gp += nz + 2;
     }
