@@ -29,8 +29,8 @@
 // Roles (one CTA per SM, 13 warps, every hand-off an mbarrier):
 //   loaders (warps 8-11): input plane g of a work unit (an 8 x 16 column of ZC output
 //     planes) into stage g % NST with cp.async, once the MMAs of plane g - NST have
-//     completed; each loader thread arrives on the stage's "full" barrier when its copies
-//     have landed (cp.async.mbarrier.arrive);
+//     completed; after issuing plane g a loader thread waits for its copies of plane g - 1,
+//     takes the generic-to-async proxy fence and arrives on that stage's "full" barrier;
 //   MMA issue (warp 12, one lane): the 9 KH MMAs of plane g into accumulator g % NDB once
 //     the stage is full and output g - NDB has read that accumulator; tcgen05.commit to
 //     the accumulator's "full" and the stage's "empty" barriers;
@@ -129,10 +129,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar, uint32_t count = 1) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar), "r"(count) : "memory");
-}
-// arrive on bar once this thread's earlier cp.async copies have landed
-__device__ __forceinline__ void cp_arrive(uint32_t bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
 }
 // Named barrier `id` of one epilogue group (128 threads).
 __device__ __forceinline__ void epi_sync(uint32_t id) { asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory"); }
@@ -238,7 +234,9 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
     constexpr int PER = (NSLOT + kLoadThreads - 1) / kLoadThreads;
     const int lt = tid - kLoadWarp0 * 32;
     long long gp = 0;
-    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    long long pend = -1;  // plane whose copies are issued but not yet announced
+    bool lok = true;
+    for (long long u = blockIdx.x; u < units && lok; u += gridDim.x) {
       const int ux = (int)(u % nux);
       const long long r1 = u / nux;
       const int uy = (int)(r1 % nuy), zc = (int)(r1 / nuy);
@@ -266,17 +264,33 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
         const long long g = gp + j;
         const int st = (int)(g % NST);
         const bool ok = g < NST || mbar_wait(smem_u32(st_empty + st), (uint32_t)(((g - NST) / NST) & 1), abort_flag);
-        if (!__all_sync(0xffffffffu, ok)) break;
+        if (!__all_sync(0xffffffffu, ok)) {
+          lok = false;
+          break;
+        }
         const int z = wrapi(zb - 1 + j, p.n3);
         const uint32_t dst = smem_u32(Ps + (size_t)st * G::PLANE);
         const bf16* src = p.in + (long long)z * plane_elems;
 #pragma unroll
         for (int i = 0; i < PER; ++i)
           if (goff[i] >= 0) cp16(dst + soff[i], src + goff[i]);
-        cp_arrive(smem_u32(st_full + st));
+        cp_commit();
+        // the previous plane's copies have landed (all groups but the newest): a proxy fence
+        // makes them visible to the tensor cores' reads, then the stage is announced
+        if (pend >= 0) {
+          asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_arrive(smem_u32(st_full + (int)(pend % NST)));
+        }
+        pend = g;
       }
-      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) lok = false;
       gp += NP;
+    }
+    if (lok && pend >= 0) {
+      cp_wait_all();
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_arrive(smem_u32(st_full + (int)(pend % NST)));
     }
   } else if (warp == kMmaWarp) {
     // ---- MMAs of plane g into accumulator g % NDB (free once output g - NDB has read it);
@@ -303,7 +317,7 @@ __global__ void __launch_bounds__(tcconv::kThreads, 1) k_conv_tc(ConvArgs p, int
           break;
         }
         if (lane == 0) {
-          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          // (the loaders took the proxy fence before announcing the stage)
           tc_fence_after();
           const uint64_t bd = bdesc + (uint64_t)((st * G::PLANE) >> 4);
           const uint32_t dt = tbase + (uint32_t)(db * NV);
