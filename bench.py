@@ -517,6 +517,33 @@ def small_grid(wfft, torch, steps=50):
         out["kernels_per_step"] = (s.launch_count() - l0) / steps
         out["krylov_iters_per_step"] = its / steps
         s.close()
+    # launch floor: a CUDA graph of as many one-element kernels as a C1 step launches, replayed
+    # once per step, without and with one host synchronisation per step (a step waits on the
+    # device at least once, for its convergence flag)
+    nk = max(1, int(round(out["kernels_per_step"])))
+    try:
+        x = torch.zeros(1, device="cuda")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(nk):
+                x.add_(1.0)
+        for sync in (False, True):
+            for _ in range(3):
+                graph.replay()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(steps):
+                graph.replay()
+                if sync:
+                    stream.synchronize()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out["launch_floor_us" + ("_sync" if sync else "")] = 1e3 * ev0.elapsed_time(ev1) / steps
+        out["launch_floor_note"] = ("%d one-element kernels per step in one CUDA graph (the step's launch count), "
+                                    "replayed per step; _sync adds one host synchronisation per step" % nk)
+    except RuntimeError as e:  # the floor is context for the C1 figures, not part of them
+        out["launch_floor_error"] = str(e).splitlines()[0]
     return out
 
 
