@@ -1,4 +1,5 @@
-"""The paper's validation workloads on the GPU (Sec. 3.1, Table 2; Sec. 3.2, Table 4).
+"""The paper's validation workloads on the GPU (Sec. 3.1, Tables 2 and 3 and the order of
+accuracy in time; Sec. 3.2, Table 4).
 
 A 1-D bar is run as a 2-D plane-strain strip of N x 2 voxels loaded uniformly across
 its width: for a y-uniform field the spectral y derivative is exactly zero, so with
@@ -78,6 +79,36 @@ def test_1d_aluminium_bar_on_gpu_equals_the_oracle_and_its_analytic_error(N, rat
     e_orc = np.linalg.norm(uo - ua) / np.linalg.norm(ua)
     assert abs(e_gpu - e_orc) <= 1e-6 * e_orc
     assert e_gpu < 2e-2  # 1.6e-2 at N = 729: the source voxel is 9x the paper's
+
+
+def test_order_of_accuracy_in_time_on_gpu():
+    """Sec. 3.1, order of accuracy in time: the Table 2 bar as the N x 2 strip at N = 729, run
+    to the same final time with Delta t = 4, 2, 1 x h / c0.  Each GPU run equals the oracle's
+    bar at the same Delta t, and the differences of successive runs shrink by the factor 4
+    of a second-order scheme (Richardson), as the oracle's do."""
+    torch_cuda()
+    wfft = solver_lib()
+    N, L, T = 729, 2.0, 3.919e-4
+    c0 = np.sqrt(AL_E / AL_RHO)
+    Uf = lambda t: inputs.bell_pulse(t, 1e-3, 5 * np.pi * c0 / L, 4)  # noqa: E731
+    runs = {}
+    for r in (4.0, 2.0, 1.0):
+        nsteps = int(round(T / (r * (L / N) / c0)))
+        dt = T / nsteps
+        U = np.zeros((nsteps, 3))
+        U[:, 0] = Uf(dt * np.arange(1, nsteps + 1))
+        s = wfft.Solver.from_problem(_strip(N, L, AL_E, 0.0, AL_RHO, dt, U),
+                                     options=wfft.default_options(tol=1e-12, maxit=400))
+        for k in range(nsteps):
+            assert s.step(U[k])["status"] == 0
+        ux = s.get_state()[0][0, 0, 0]
+        s.close()
+        uo = _bar_oracle(N, L, dt, U)
+        assert np.linalg.norm(ux - uo) / np.linalg.norm(uo) < 1e-9, r
+        runs[r] = ux
+    ratio = np.linalg.norm(runs[4.0] - runs[2.0]) / np.linalg.norm(runs[2.0] - runs[1.0])
+    print("Richardson ratio (Delta t = 4, 2, 1 h / c0):", ratio)
+    assert 3.3 < ratio < 4.5, ratio
 
 
 @pytest.mark.parametrize("comp", [0, 1])

@@ -327,6 +327,35 @@ def test_1d_aluminium_bar_reproduces_table_2_small_dt(ratio):
     assert paper / 1.5 < err < paper * 1.5, err
 
 
+def _bar_final(N, r, T=3.919e-4):
+    """The Table 2 bar at N voxels run to the final time T with Delta t = T / round(T c0 / (r h)):
+    final u of the FP64 oracle."""
+    L = 2.0
+    E, rho = 70.3e9, 2700.0
+    c0 = np.sqrt(E / rho)
+    h = L / N
+    nsteps = int(round(T / (r * h / c0)))
+    dt = T / nsteps
+    Uf = lambda t: inputs.bell_pulse(t, 1e-3, 5 * np.pi * c0 / L, 4)  # noqa: E731
+    med = medium.Medium(1, (N,), (L,), np.full((1, 1, 1, 1, 1), E), np.zeros(N, np.int64), np.full(N, rho))
+    mask = np.zeros((1, N), bool)
+    mask[0, 0] = True
+    U = np.zeros((nsteps, 3))
+    U[:, 0] = Uf(dt * np.arange(1, nsteps + 1))
+    s, _ = newmark.NewmarkOracle(med, mask, dt, tol=1e-13).run(U)
+    return s.u[0]
+
+
+def test_newmark_bar_is_second_order_in_time():
+    """Sec. 3.1 (order of accuracy in time): the average-acceleration Newmark scheme
+    (beta 1/4, gamma 1/2) is second order, so at a fixed grid the differences of runs at
+    Delta t, Delta t / 2, Delta t / 4 shrink by 4 (Richardson); a first-order slip (a wrong
+    gamma, a dropped acceleration term) gives 2.  N = 729, Delta t = 2, 1, 1/2 x h / c0."""
+    u2, u1, u05 = (_bar_final(729, r) for r in (2.0, 1.0, 0.5))
+    ratio = np.linalg.norm(u2 - u1) / np.linalg.norm(u1 - u05)
+    assert 3.5 < ratio < 4.5, ratio
+
+
 def test_material_table_follows_the_isotropic_closed_forms():
     """Sec. 3.1, material table: lambda and mu from E and nu (the relations the oracle
     uses to build isotropic stiffnesses) and the 1-D speed c0 = sqrt(E / rho) reproduce the
