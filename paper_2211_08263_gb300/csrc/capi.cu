@@ -1893,7 +1893,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
         if (!ops_of_axis(D, a, op)) continue;
         int keep = P.g.bx[a][op];
         float tbest = 1e30f;
-        for (int bx = 1; bx <= 16; bx <<= 1) {
+        for (int bx : {1, 2, 4, 8, 16, kColReg | 4, kColReg | 8, kColReg | 16}) {
           if (!col_bx_feasible<T>(P, a, op, bx)) continue;
           set_col_bx<T>(P, a, op, bx);
           const float t = time_iteration<T>(h, P, reps);

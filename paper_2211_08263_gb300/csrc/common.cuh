@@ -31,6 +31,13 @@ struct AxisPlan {
   int prime;
 };
 
+// Column-tile codes: a plain code is the tile width (kx columns) of the general column
+// kernels; kColReg | w (w = 4, 8, 16) selects the register-stage kernels over 256-point
+// axes (k_col256) with tiles w columns wide.
+constexpr int kColReg = 256;
+__host__ __device__ __forceinline__ constexpr bool col_is_reg(int bx) { return (bx & kColReg) != 0; }
+__host__ __device__ __forceinline__ constexpr int col_width(int bx) { return bx & (kColReg - 1); }
+
 // Scalars of one Krylov solve, updated only by the single-block finalize kernels.
 struct Scalars {
   double ref2;      // ||P(b - A x_Gamma)||^2

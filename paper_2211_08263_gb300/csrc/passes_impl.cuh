@@ -6,6 +6,7 @@
 
 #include "launch.cuh"
 #include "passes.cuh"
+#include "col256.cuh"
 #include "profiler.cuh"
 
 namespace wfft {
@@ -107,6 +108,16 @@ void plan_geometry(Plan<T>& P) {
 // Column-tile width bx of pass (axis, op): feasible when every radix stage fits the
 // per-thread register batch and the tile fits 64 KB of shared memory (the rule
 // plan_geometry applies to its default choice); set_col_bx applies it to the plan.
+// The register-stage kernels (k_col256) take FP32 3-D grids with a 256-point axis: plain
+// transforms on any column axis, the fused passes on the axis hosting the spectral
+// multiply.  They do not depend on the axis' radix schedule.
+template <typename T>
+static bool col256_ok(const Desc<T>& D, int axis, int op) {
+  const int N = axis == 1 ? D.n2 : D.n3;
+  if (sizeof(T) != 4 || D.ndim != 3 || D.c != 3 || D.s != 6 || N != 256) return false;
+  return op == OP_FWD || op == OP_INV || axis == D.opAxis;
+}
+
 template <typename T>
 bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx) {
   const Desc<T>& D = P.h;
@@ -114,6 +125,10 @@ bool col_bx_feasible(const Plan<T>& P, int axis, int op, int bx) {
   const bool plain = op == OP_FWD || op == OP_INV;
   const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
   const int thr = plain ? kColThreadsPlain : kColThreadsOp;
+  if (col_is_reg(bx)) {
+    const int w = col_width(bx);
+    return (w == 4 || w == 8 || w == 16) && bx == (kColReg | w) && col256_ok(D, axis, op);
+  }
   const int maxbx = plain && sizeof(T) == 4 ? 16 : 4;  // 16-wide plain tiles: FP32 only (tuned, not default)
   if (bx < 1 || bx > maxbx || (bx & (bx - 1))) return false;
   const size_t sm = (size_t)(N + col_es(ns, bx, sizeof(T)) * N) * sizeof(cplx<T>);
@@ -128,9 +143,11 @@ void set_col_bx(Plan<T>& P, int axis, int op, int bx) {
   const int nouter = axis == 1 ? D.n3 : D.n2;
   const bool plain = op == OP_FWD || op == OP_INV;
   const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
+  const int w = col_width(bx);
   P.g.bx[axis][op] = bx;
-  P.g.blk_col[axis][op] = ((D.nh + bx - 1) / bx) * nouter;
-  P.g.sm_col[axis][op] = (size_t)(N + col_es(ns, bx, sizeof(T)) * N) * sizeof(cplx<T>);
+  P.g.blk_col[axis][op] = ((D.nh + w - 1) / w) * nouter;
+  P.g.sm_col[axis][op] = col_is_reg(bx) ? col256_smem(plain ? 1 : 3, w)
+                                         : (size_t)(N + col_es(ns, bx, sizeof(T)) * N) * sizeof(cplx<T>);
   P.g.max_blocks = std::max(P.g.max_blocks, P.g.blk_col[axis][op]);
 }
 
@@ -174,7 +191,8 @@ int geo_blocks(const Plan<T>& P, int cls, int bx) {
   }
   const int axis = (cls - GEO_COL0) / 5 + 1;
   const int nouter = axis == 1 ? D.n3 : D.n2;
-  return ((D.nh + bx - 1) / bx) * nouter;
+  const int w = col_width(bx);
+  return ((D.nh + w - 1) / w) * nouter;
 }
 
 template <typename T>
@@ -188,6 +206,7 @@ size_t geo_smem(const Plan<T>& P, int cls, int bx) {
   const int N = axis == 1 ? D.n2 : D.n3;
   const bool plain = op == OP_FWD || op == OP_INV;
   const int ns = plain ? 1 : (op == OP_PREC ? D.c : D.s);
+  if (col_is_reg(bx)) return col256_smem(plain ? 1 : 3, col_width(bx));
   return (size_t)(N + col_es(ns, bx, (int)sizeof(T)) * N) * cs;
 }
 
@@ -304,6 +323,43 @@ static void launch_colplain_bx(const Launch<T, B>& L, int op, int axis, int ncom
                 [&] { k_colplain<T, OP_INV, BX, B><<<grid, kColThreadsPlain, sm, st>>>(d, ba, axis); });
 }
 
+// Register-stage pass over a 256-point axis (FP32): plain transforms of ncomp components
+// (grid.y) or the fused gradient / divergence / preconditioner pass.
+template <typename T, int OP, int BXC, int B>
+static void launch_col256(const Launch<T, B>& L, int axis, int ncomp, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    const int cls = geo_col(axis, OP);
+    const bool plain = OP == OP_FWD || OP == OP_INV;
+    const dim3 grid(L.grid(cls), plain ? ncomp : 1);
+    const size_t sm = L.smem(cls);
+    const BatchArgs<T> ba = L.args(cls);
+    const Desc<T>* d = L.P.d;
+    double by, fl;
+    L.cost(
+        [&](const Plan<T>& Q, double& b, double& f) {
+          const Cost<T> k(Q.h);
+          if (OP == OP_FWD || OP == OP_INV) {
+            b = 2 * k.spec(ncomp);
+            f = k.colfft(axis, ncomp);
+          } else if (OP == OP_GRAD) {
+            b = k.spec(k.c) + k.spec(k.s);
+            f = k.colfft(axis, k.c + k.s) + 42.0 * k.Vh;
+          } else if (OP == OP_DIV) {
+            b = k.spec(k.s) + k.spec(k.c);
+            f = k.colfft(axis, k.c + k.s) + 36.0 * k.Vh;
+          } else {
+            b = 2 * k.spec(k.c);
+            f = k.colfft(axis, 2 * k.c) + 100.0 * k.Vh;
+          }
+        },
+        by, fl);
+    const int kind = OP == OP_FWD ? KK_COL_FWD : OP == OP_INV ? KK_COL_INV
+                   : OP == OP_GRAD ? KK_COL_GRAD : (OP == OP_DIV ? KK_COL_DIV : KK_COL_PREC);
+    prof_launch(prec_of<T>(), kind, by, fl, st,
+                [&] { k_col256<OP, BXC, B><<<grid, 16 * BXC, sm, st>>>(d, ba, axis); });
+  }
+}
+
 template <typename T, int OP, int BX, int B>
 static void launch_colop_bx(const Launch<T, B>& L, int axis, cudaStream_t st) {
   const int cls = geo_col(axis, OP);
@@ -354,6 +410,9 @@ static void launch_colop_bx(const Launch<T, B>& L, int axis, cudaStream_t st) {
 template <typename T, int OP, int B>
 static void launch_colop(const Launch<T, B>& L, int axis, cudaStream_t st) {
   switch (L.bx(axis, OP)) {
+    case kColReg | 16: launch_col256<T, OP, 16, B>(L, axis, 1, st); break;
+    case kColReg | 8: launch_col256<T, OP, 8, B>(L, axis, 1, st); break;
+    case kColReg | 4: launch_col256<T, OP, 4, B>(L, axis, 1, st); break;
     case 4: launch_colop_bx<T, OP, 4, B>(L, axis, st); break;
     case 2: launch_colop_bx<T, OP, 2, B>(L, axis, st); break;
     default: launch_colop_bx<T, OP, 1, B>(L, axis, st); break;
@@ -388,6 +447,18 @@ template <typename T, int B>
 static void launch_col_one(const Launch<T, B>& L, int op, int axis, int ncomp, cudaStream_t st) {
   if (op == OP_FWD || op == OP_INV) {
     switch (L.bx(axis, op)) {
+      case kColReg | 16:
+        if (op == OP_FWD) launch_col256<T, OP_FWD, 16, B>(L, axis, ncomp, st);
+        else launch_col256<T, OP_INV, 16, B>(L, axis, ncomp, st);
+        break;
+      case kColReg | 8:
+        if (op == OP_FWD) launch_col256<T, OP_FWD, 8, B>(L, axis, ncomp, st);
+        else launch_col256<T, OP_INV, 8, B>(L, axis, ncomp, st);
+        break;
+      case kColReg | 4:
+        if (op == OP_FWD) launch_col256<T, OP_FWD, 4, B>(L, axis, ncomp, st);
+        else launch_col256<T, OP_INV, 4, B>(L, axis, ncomp, st);
+        break;
       case 16:
         if constexpr (sizeof(T) == 4) launch_colplain_bx<T, 16, B>(L, op, axis, ncomp, st);
         break;
@@ -659,6 +730,16 @@ cudaError_t init_kernel_attributes_impl() {
   if constexpr (sizeof(T) == 4) {
     WFFT_SETATTR((k_colplain<T, OP_FWD, 16, B>));
     WFFT_SETATTR((k_colplain<T, OP_INV, 16, B>));
+#define WFFT_SETATTR_REG(BXC)                \
+  WFFT_SETATTR((k_col256<OP_FWD, BXC, B>));  \
+  WFFT_SETATTR((k_col256<OP_INV, BXC, B>));  \
+  WFFT_SETATTR((k_col256<OP_GRAD, BXC, B>)); \
+  WFFT_SETATTR((k_col256<OP_DIV, BXC, B>));  \
+  WFFT_SETATTR((k_col256<OP_PREC, BXC, B>));
+    WFFT_SETATTR_REG(4)
+    WFFT_SETATTR_REG(8)
+    WFFT_SETATTR_REG(16)
+#undef WFFT_SETATTR_REG
   }
 #undef WFFT_SETATTR_BX
 #undef WFFT_SETATTR
