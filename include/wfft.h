@@ -345,9 +345,13 @@ WFFT_API int wfft_set_radix(wfft_handle* h, int precision, int axis, const int c
 /* The plan choices of one precision: radix[axis][r] stage counts (as wfft_set_radix),
    bx[axis][op] column-tile widths (axes 1, 2; op 0 forward, 1 inverse, 2 gradient, 3
    divergence, 4 preconditioner; powers of two up to 4, or 16 for the FP32 plain passes;
-   entries of passes the grid does not run are ignored) and
+   256 | w with w = 4, 8 or 16 selects the register-stage kernels over a 256-point axis
+   (FP32 3-D plans; tiles w columns wide); entries of passes the grid does not run are
+   ignored) and
    xelems, the complex elements per x-pass tile (0 = the default 2048; 256..8192, capped
-   by the register batch of the radix schedule).
+   by the register batch of the radix schedule); xelems | 65536 selects the
+   register-stage x passes over 256-point rows (FP32 3-D plans, single-instance solves;
+   at most 10 lines per tile of the 3-component passes and 5 of the middle pass).
    wfft_get_plan reads them (e.g. after wfft_autotune); wfft_set_plan applies them to a
    handle of the same grid, so a tuned plan can be kept and reused without timing.  A
    choice that does not fit the grid, the register batch, 64 KB of shared memory or the

@@ -1872,7 +1872,7 @@ int tune_plan(wfft_handle* h, Plan<T>& P, int prec, int reps, int* changed) {
       const int keep0 = P.g.xelems;
       int keep = keep0;
       float tbest = 1e30f;
-      for (int xe : {1024, 2048, 4096}) {
+      for (int xe : {1024, 2048, 4096, kXReg | 2048, kXReg | 4096}) {
         P.g.xelems = xe;
         plan_geometry<T>(P);
         if (!P.g.fits || P.g.max_blocks > h->nparts) continue;
@@ -2265,8 +2265,9 @@ int set_plan(wfft_handle* h, Plan<T>& P, const wfft_plan_choice* in) {
       return fail(h, WFFT_EINVAL,
                   "a radix schedule (times the prime factor above 7, if any) does not multiply to its axis length");
   }
-  if (in->xelems != 0 && (in->xelems < 256 || in->xelems > 8192))
-    return fail(h, WFFT_EINVAL, "the x-pass tile size must be 0 or 256..8192 elements");
+  const int xe = in->xelems & ~kXReg;
+  if (xe != 0 && (xe < 256 || xe > 8192))
+    return fail(h, WFFT_EINVAL, "the x-pass tile size must be 0 or 256..8192 elements (optionally | 65536)");
   const Desc<T> saved = D;
   const PassGeo gsaved = P.g;
   for (int a = 0; a < 3; ++a) D.ax[a] = ax[a];

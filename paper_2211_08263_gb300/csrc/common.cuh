@@ -38,6 +38,11 @@ constexpr int kColReg = 256;
 __host__ __device__ __forceinline__ constexpr bool col_is_reg(int bx) { return (bx & kColReg) != 0; }
 __host__ __device__ __forceinline__ constexpr int col_width(int bx) { return bx & (kColReg - 1); }
 
+// x-pass tile code: xelems | kXReg selects the register-stage x passes over 256-point
+// rows (k_xmid256, k_xinv256, k_xfwd256_rupd) for the single-instance FP32 passes of a
+// 3-D grid; the low bits are the tile size as for the general x passes.
+constexpr int kXReg = 1 << 16;
+
 // Scalars of one Krylov solve, updated only by the single-block finalize kernels.
 struct Scalars {
   double ref2;      // ||P(b - A x_Gamma)||^2

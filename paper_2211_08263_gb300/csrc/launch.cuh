@@ -20,6 +20,7 @@ struct PassGeo {
   int max_blocks;
   int xelems = 0;       // complex elements per x-pass tile (0: the default 2048; capped by the register batch)
   bool fits = true;     // every tile within its stages' register batch and the opt-in shared memory
+  bool xreg = false;    // register-stage x passes (xelems carries kXReg and the grid allows them)
 };
 
 template <typename T>

@@ -7,6 +7,7 @@
 #include "launch.cuh"
 #include "passes.cuh"
 #include "col256.cuh"
+#include "xreg256.cuh"
 #include "profiler.cuh"
 
 namespace wfft {
@@ -60,7 +61,8 @@ void plan_geometry(Plan<T>& P) {
   Desc<T>& D = P.h;
   PassGeo& g = P.g;
   g.thr = 256;
-  const int budget = g.xelems > 0 ? g.xelems : 2048;  // target complex elements per x-pass tile
+  const int xe = g.xelems & (kXReg - 1);
+  const int budget = xe > 0 ? xe : 2048;  // target complex elements per x-pass tile
   const long long nsp = (long long)D.n2 * D.n3;
   // x passes: npairs * N1 <= elems, LX * nc even
   const int ex = std::min(budget, max_tile_elems<T>(D.ax[0], g.thr));
@@ -74,6 +76,15 @@ void plan_geometry(Plan<T>& P) {
   const size_t cs = sizeof(cplx<T>);
   g.sm_x = (size_t)(D.n1 + (g.LX * D.c / 2) * row_stride(D.n1)) * cs;
   g.sm_xm = (size_t)(D.n1 + (g.LXm * D.s / 2) * row_stride(D.n1)) * cs;
+  // register-stage x passes: FP32 3-D grids with 256-point rows, at most 256 threads per
+  // block (16 per line pair: 24 LX for the c-component passes, 48 LXm for the middle pass)
+  g.xreg = false;
+  if (g.xelems & kXReg) {
+    const bool ok = sizeof(T) == 4 && D.ndim == 3 && D.c == 3 && D.s == 6 && D.n1 == 256 && g.LX % 2 == 0 &&
+                    24 * g.LX <= 256 && 48 * g.LXm <= 256 && xreg_smem_mid(g.LXm) <= kMaxDynSmem;
+    if (ok) g.xreg = true;
+    else g.fits = false;
+  }
   // column passes: per axis and op, the widest tile (kx columns) whose every
   // radix stage fits the register batch and whose slots fit 64 KB of shared memory
   const int maxbx = sizeof(T) == 4 ? 8 : 4;
@@ -284,6 +295,15 @@ static void launch_xfwd(const Launch<T, B>& L, int pre, int in_slot, cudaStream_
       prof_launch(pi, KK_XFWD_PUPD, by, fl, st, [&] { k_xfwd<T, PRE_PUPD, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
     case PRE_RUPD:
+      if constexpr (B == 0 && sizeof(T) == 4) {
+        if (L.P.g.xreg) {
+          const int lx = L.P.h.lx;
+          prof_launch(pi, KK_XFWD_RUPD, by, fl, st, [&] {
+            k_xfwd256_rupd<B><<<nb, 24 * lx, xreg_smem(3 * lx / 2), st>>>(d, ba);
+          });
+          break;
+        }
+      }
       prof_launch(pi, KK_XFWD_RUPD, by, fl, st, [&] { k_xfwd<T, PRE_RUPD, B><<<nb, 256, sm, st>>>(d, ba, in_slot); });
       break;
     case PRE_CONV:
@@ -517,6 +537,24 @@ static void launch_xinv(const Launch<T, B>& L, int post, int in_slot, int out_sl
         }
       },
       by, fl);
+  if constexpr (B == 0 && sizeof(T) == 4) {
+    if (L.P.g.xreg && (post == POST_APPLY || post == POST_PREC_PUPD)) {
+      const Desc<T>& D = L.P.h;
+      const int lx = D.lx;
+      size_t smr = xreg_smem(3 * lx / 2);
+      if (post == POST_APPLY)
+        prof_launch(pi, KK_XINV_APPLY, by, fl, st, [&] {
+          k_xinv256<POST_APPLY, B><<<nb, 24 * lx, smr + (stage ? xinv_stage_layout(POST_APPLY, 3, lx, 256,
+                                                                                         D.phase != nullptr).total : 0),
+                                     st>>>(d, ba, in_slot, out_slot, masked, want_dot, stage);
+        });
+      else
+        prof_launch(pi, KK_XINV_PUPD, by, fl, st, [&] {
+          k_xinv256<POST_PREC_PUPD, B><<<nb, 24 * lx, smr, st>>>(d, ba, in_slot, out_slot, masked, 0, 0);
+        });
+      return;
+    }
+  }
   switch (post) {
     case POST_APPLY:
       prof_launch(pi, KK_XINV_APPLY, by, fl, st, [&] {
@@ -560,6 +598,14 @@ static void launch_xmid(const Launch<T, B>& L, cudaStream_t st) {
         f = 2 * k.xfft(k.s) + (Q.h.ndim == 3 ? 66.0 : 15.0) * k.V;
       },
       by, fl);
+  if constexpr (B == 0 && sizeof(T) == 4) {
+    if (L.P.g.xreg) {
+      const int lxm = L.P.h.lxm;
+      prof_launch(prec_of<T>(), KK_XMID, by, fl, st,
+                  [&] { k_xmid256<B><<<nb, 48 * lxm, xreg_smem_mid(lxm), st>>>(d, ba); });
+      return;
+    }
+  }
   prof_launch(prec_of<T>(), KK_XMID, by, fl, st, [&] { k_xmid<T, B><<<nb, 256, sm, st>>>(d, ba, stage); });
 }
 
@@ -699,6 +745,12 @@ cudaError_t init_kernel_attributes_impl() {
   WFFT_SETATTR((k_xinv<T, POST_PREC, B>));
   if constexpr (B == 0) WFFT_SETATTR((k_xinv<T, POST_PREC_PUPD, B>));
   WFFT_SETATTR((k_xmid<T, B>));
+  if constexpr (B == 0 && sizeof(T) == 4) {
+    WFFT_SETATTR((k_xmid256<B>));
+    WFFT_SETATTR((k_xinv256<POST_APPLY, B>));
+    WFFT_SETATTR((k_xinv256<POST_PREC_PUPD, B>));
+    WFFT_SETATTR((k_xfwd256_rupd<B>));
+  }
   if (!B) WFFT_SETATTR((k_xplain<T>));
 #define WFFT_SETATTR_BX(BXV)                  \
   WFFT_SETATTR((k_colop<T, OP_GRAD, BXV, 3, B>));  \
