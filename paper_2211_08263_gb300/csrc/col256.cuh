@@ -90,14 +90,12 @@ __device__ __forceinline__ void gstore(const F2 (&v)[16], F2* p, int est16, bool
 }  // namespace c256
 
 // Blocks per SM the fused passes are compiled for (registers per thread follow): three
-// 128-thread blocks (at most 170 registers) for the gradient and preconditioner passes
-// over 8-column tiles, one block otherwise.  Measured at 256^3: the gradient and
-// preconditioner passes take 0.22 / 0.19 ms with three blocks against 0.26 / 0.22 ms with
-// two (255 registers); the divergence pass, whose 96 accumulators stay live while its
-// second round of stresses loads, spills at 170 registers and is slower (0.27 against
-// 0.26 ms), and at 128 registers every fused pass spills and runs 20-45 % slower.
+// 128-thread blocks (at most 170 registers) over 8-column tiles, one block otherwise.
+// Measured at 256^3: the gradient and preconditioner passes take 0.22 / 0.19 ms with three
+// blocks against 0.26 / 0.22 ms with two (255 registers); at 128 registers every fused
+// pass spills and runs 20-45 % slower.
 __host__ __device__ constexpr int col256_fused_minb(int op, int bxc) {
-  return (bxc == 8 && op != OP_DIV) ? 3 : 1;
+  return (bxc == 8 && op >= OP_GRAD) ? 3 : 1;
 }
 
 template <int OP, int BXC, int BATCH>
@@ -245,17 +243,26 @@ __global__ void __launch_bounds__(16 * BXC, (OP == OP_FWD || OP == OP_INV) ? 64 
         __syncthreads();
       }
     } else {  // OP_DIV
-      F2 Tq[3][16];
-      // round 1: sigma_11, sigma_22, sigma_33; round 2: sigma_23, sigma_13, sigma_12
-      // (each round's three loads in flight before its first transform)
+      // t_i = sum_j xi_j sigma_ij, one output completed per round so that at most two
+      // accumulators stay live while stresses load: round 0 reads s11, s12, s13 (t_1
+      // complete), round 1 s22, s23 (t_2), round 2 s33 (t_3); a completed t_i takes its
+      // first inverse stage into buffer i at once (spectral components: 11, 22, 33, 23, 13, 12)
+      const float f = D.mthetaInvV;
+      F2 t2[16], t3[16];
+      auto finish = [&](F2 (&tv)[16], int c) {
 #pragma unroll
-      for (int round = 0; round < 2; ++round) {
+        for (int kb = 0; kb < 16; ++kb) tv[kb] = cmuli<float>(cscale<float>(tv[kb], f), +1);
+        stage1<+1, BXC>(tv, j, b, tw, S + c * kBuf);
+      };
+      {
         F2 in[3][16];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) gload(in[q], D.spec + (3 * round + q) * D.Vh + off, est16, ok);
+        gload(in[0], D.spec + 0 * D.Vh + off, est16, ok);  // s11
+        gload(in[1], D.spec + 5 * D.Vh + off, est16, ok);  // s12
+        gload(in[2], D.spec + 4 * D.Vh + off, est16, ok);  // s13
 #pragma unroll
         for (int q = 0; q < 3; ++q) stage1<-1, BXC>(in[q], j, b, tw, S + q * kBuf);
         __syncthreads();
+        F2 t1[16];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           stage2<-1, BXC>(v, j, b, S + q * kBuf);
@@ -264,32 +271,58 @@ __global__ void __launch_bounds__(16 * BXC, (OP == OP_FWD || OP == OP_INV) ? 64 
             float x1, x2, x3;
             xi3(j + 16 * kb, x1, x2, x3);
             const F2 sg = v[kb];
-            if (round == 0) {
-              // t_1 = xi1 s11 + ..., t_2 = xi2 s22 + ..., t_3 = xi3 s33 + ...
-              if (q == 0) Tq[0][kb] = cscale<float>(sg, x1);
-              else if (q == 1) Tq[1][kb] = cscale<float>(sg, x2);
-              else Tq[2][kb] = cscale<float>(sg, x3);
-            } else if (q == 0) {  // s23
-              Tq[1][kb] = cadd<float>(Tq[1][kb], cscale<float>(sg, x3));
-              Tq[2][kb] = cadd<float>(Tq[2][kb], cscale<float>(sg, x2));
-            } else if (q == 1) {  // s13
-              Tq[0][kb] = cadd<float>(Tq[0][kb], cscale<float>(sg, x3));
-              Tq[2][kb] = cadd<float>(Tq[2][kb], cscale<float>(sg, x1));
-            } else {  // s12
-              Tq[0][kb] = cadd<float>(Tq[0][kb], cscale<float>(sg, x2));
-              Tq[1][kb] = cadd<float>(Tq[1][kb], cscale<float>(sg, x1));
+            if (q == 0) {
+              t1[kb] = cscale<float>(sg, x1);
+            } else if (q == 1) {  // s12
+              t1[kb] = cadd<float>(t1[kb], cscale<float>(sg, x2));
+              t2[kb] = cscale<float>(sg, x1);
+            } else {  // s13
+              t1[kb] = cadd<float>(t1[kb], cscale<float>(sg, x3));
+              t3[kb] = cscale<float>(sg, x1);
             }
           }
         }
         __syncthreads();
+        finish(t1, 0);
       }
-      const float f = D.mthetaInvV;
+      {
+        F2 in[2][16];
+        gload(in[0], D.spec + 1 * D.Vh + off, est16, ok);  // s22
+        gload(in[1], D.spec + 3 * D.Vh + off, est16, ok);  // s23
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+        for (int q = 0; q < 2; ++q) stage1<-1, BXC>(in[q], j, b, tw, S + (q + 1) * kBuf);
+        __syncthreads();
 #pragma unroll
-        for (int kb = 0; kb < 16; ++kb) Tq[c][kb] = cmuli<float>(cscale<float>(Tq[c][kb], f), +1);
-        stage1<+1, BXC>(Tq[c], j, b, tw, S + c * kBuf);
+        for (int q = 0; q < 2; ++q) {
+          stage2<-1, BXC>(v, j, b, S + (q + 1) * kBuf);
+#pragma unroll
+          for (int kb = 0; kb < 16; ++kb) {
+            float x1, x2, x3;
+            xi3(j + 16 * kb, x1, x2, x3);
+            const F2 sg = v[kb];
+            if (q == 0) {
+              t2[kb] = cadd<float>(t2[kb], cscale<float>(sg, x2));
+            } else {  // s23
+              t2[kb] = cadd<float>(t2[kb], cscale<float>(sg, x3));
+              t3[kb] = cadd<float>(t3[kb], cscale<float>(sg, x2));
+            }
+          }
+        }
+        __syncthreads();
+        finish(t2, 1);
       }
+      gload(v, D.spec + 2 * D.Vh + off, est16, ok);  // s33
+      stage1<-1, BXC>(v, j, b, tw, S + 2 * kBuf);
+      __syncthreads();
+      stage2<-1, BXC>(v, j, b, S + 2 * kBuf);
+#pragma unroll
+      for (int kb = 0; kb < 16; ++kb) {
+        float x1, x2, x3;
+        xi3(j + 16 * kb, x1, x2, x3);
+        t3[kb] = cadd<float>(t3[kb], cscale<float>(v[kb], x3));
+      }
+      __syncthreads();
+      finish(t3, 2);
       __syncthreads();
 #pragma unroll
       for (int c = 0; c < 3; ++c) {

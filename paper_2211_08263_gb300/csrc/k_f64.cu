@@ -47,9 +47,11 @@ __global__ void __launch_bounds__(256) k_predict(const Desc<double>* __restrict_
   double* r64 = reinterpret_cast<double*>(D.slot[SL_R64]);
   double acc = 0.0, accr = 0.0;
   const long long tot = (long long)c * V;
-  for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
-    const int k = (int)(gi / V);
-    const long long vox = gi - (long long)k * V;
+  // component by component (no 64-bit division per element), voxels grid-strided
+  const long long first = (long long)blk * blockDim.x + threadIdx.x, stride = (long long)nblk * blockDim.x;
+  for (int k = 0; k < c; ++k)
+  for (long long vox = first; vox < V; vox += stride) {
+    const long long gi = (long long)k * V + vox;
     const double uu = u[gi], vv = v[gi], aa = a[gi];
     const double ut = uu + dt * vv + dt * dt * (0.5 - beta) * aa;
     const double bv = rho_at<double>(D, vox) * ut;
@@ -115,10 +117,11 @@ __global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict_
   const bool zf = sc->zero_free != 0;
   double acc[3] = {0.0, 0.0, 0.0};
   double ek = 0.0, eua = 0.0;
-  const long long tot = (long long)c * V;
-  for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
-    const int k = (int)(gi / V);
-    const long long vox = gi - (long long)k * V;
+  // component by component (no 64-bit division per element), voxels grid-strided
+  const long long first = (long long)blk * blockDim.x + threadIdx.x, stride = (long long)nblk * blockDim.x;
+  for (int k = 0; k < c; ++k)
+  for (long long vox = first; vox < V; vox += stride) {
+    const long long gi = (long long)k * V + vox;
     const double uu = u[gi], vv = v[gi], aa = a[gi];
     const double ut = uu + dt * vv + dt * dt * (0.5 - beta) * aa;
     double xv = x[gi];
@@ -150,11 +153,11 @@ __global__ void __launch_bounds__(256) k_correct(const Desc<double>* __restrict_
 __global__ void k_fill_unit(const Desc<double>* __restrict__ dd, int j, double* dst) {
   const Desc<double>& D = *dd;
   const long long V = D.V;
-  const long long tot = (long long)D.c * V;
-  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
-       gi += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(gi / V);
-    const long long vox = gi - (long long)k * V;
+  const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                  stride = (long long)gridDim.x * blockDim.x;
+  for (int k = 0; k < D.c; ++k)
+  for (long long vox = first; vox < V; vox += stride) {
+    const long long gi = (long long)k * V + vox;
     dst[gi] = (k == j && ((D.mask[vox] >> k) & 1)) ? 1.0 : 0.0;
   }
 }
@@ -182,7 +185,6 @@ __global__ void __launch_bounds__(256) k_explicit_update(const Desc<double>* __r
                                                          double U2) {
   const Desc<double>& D = *dd;
   const long long V = D.V;
-  const long long tot = (long long)D.c * V;
   const double dt = D.dt;
   double* v = reinterpret_cast<double*>(D.slot[SL_V]);
   double* a = reinterpret_cast<double*>(D.slot[SL_A]);
@@ -190,10 +192,11 @@ __global__ void __launch_bounds__(256) k_explicit_update(const Desc<double>* __r
   const double* un = reinterpret_cast<const double*>(D.slot[SL_U]);
   double acc[3] = {0.0, 0.0, 0.0};
   double ek = 0.0, euq = 0.0;
-  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < tot;
-       gi += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(gi / V);
-    const long long vox = gi - (long long)k * V;
+  const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                  stride = (long long)gridDim.x * blockDim.x;
+  for (int k = 0; k < D.c; ++k)
+  for (long long vox = first; vox < V; vox += stride) {
+    const long long gi = (long long)k * V + vox;
     const double rho = rho_at<double>(D, vox);
     const double vv = v[gi], aa = a[gi];
     const double vb = vv + 0.5 * dt * aa + dt / (2.0 * rho) * (-q[gi]);
@@ -461,10 +464,11 @@ __global__ void __launch_bounds__(256) k_resid_incr(const Desc<double>* __restri
   double* au = reinterpret_cast<double*>(D.slot[SL_AU]);
   double* r = reinterpret_cast<double*>(D.slot[SL_R64]);
   double acc = 0.0;
-  const long long tot = (long long)D.c * V;
-  for (long long gi = (long long)blk * blockDim.x + threadIdx.x; gi < tot; gi += (long long)nblk * blockDim.x) {
-    const int k = (int)(gi / V);
-    const long long vox = gi - (long long)k * V;
+  // component by component (no 64-bit division per element), voxels grid-strided
+  const long long first = (long long)blk * blockDim.x + threadIdx.x, stride = (long long)nblk * blockDim.x;
+  for (int k = 0; k < D.c; ++k)
+  for (long long vox = first; vox < V; vox += stride) {
+    const long long gi = (long long)k * V + vox;
     x[gi] = x[gi] + xc * (double)d[gi];
     const double ax = au[gi] + xc * (double)q32[gi];
     au[gi] = ax;
