@@ -80,6 +80,7 @@ def parse():
                     help="mixed modes: stop an inner solve at this fraction of the outer target")
     ap.add_argument("--inner-tol", type=float, default=None, help="mixed mode: FP32 inner-solve reduction")
     ap.add_argument("--nz", type=int, default=None, help="z extent of an n x n x nz slab instead of the cube")
+    ap.add_argument("--ny", type=int, default=None, help="y extent (n x ny x nz) instead of the cube's")
     ap.add_argument("--xelems", type=int, default=None,
                     help="x-pass tile size (complex elements) applied after tuning / plan loading")
     ap.add_argument("--no-incr-resid", action="store_true",
@@ -205,6 +206,24 @@ def net_roofline(prof):
             "achieved": ach, "peak": peak,
             "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src, "ms_per_launch": per,
             "launches": d["timed"], "ms_total": d["ms"], "traffic": None}
+
+
+def pcg_roofline(prof, V, hbm_peak, peak_kind):
+    """The FP32 operator and preconditioner passes of the inner Krylov solve taken together
+    (every FP32 pass kind but the network's): their algorithmic bytes over their summed
+    CUDA-event time, against the measured HBM bandwidth, and per operator application
+    (one x middle pass per application)."""
+    kinds = {k: d for (prec, k), d in prof.items() if prec == "fp32" and not k.startswith("net") and d["timed"]}
+    if not kinds:
+        return None
+    ms = sum(d["ms"] for d in kinds.values())
+    by = sum(d["bytes"] for d in kinds.values())
+    napp = kinds.get("xmid", {}).get("timed", 0)
+    ach = by / (ms * 1e-3) / 1e9
+    return {"kernels": "FP32 operator + preconditioner passes of the inner PCG (all kinds)", "bound": "hbm",
+            "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_kind,
+            "ms_per_application": ms / napp if napp else None,
+            "alg_bytes_per_voxel_application": by / napp / V if napp else None}
 
 
 # FP64 FMA throughput of a GB300, measured with an FMA-chain microbenchmark
@@ -745,7 +764,7 @@ def main():
     rank, world, local = dist_env()
     from paper_2211_08263_gb300 import inputs
     W, K = args.warmup, args.steps
-    prob = inputs.config_c3(nsteps=max(args.nsteps, 2 * (W + K + PROF_STEPS) + K), n=args.n, nz=args.nz)
+    prob = inputs.config_c3(nsteps=max(args.nsteps, 2 * (W + K + PROF_STEPS) + K), n=args.n, nz=args.nz, ny=args.ny)
     if args.impl == "reference":
         return run_reference(args, prob, rank, world)
 
@@ -832,6 +851,9 @@ def main():
         nr = net_roofline(results["learned"]["profile"])
         if nr:
             line["roofline_net"] = nr
+    pr = pcg_roofline(head["profile"], V, hbm_peak, peak_kind)
+    if pr:
+        line["roofline_pcg"] = pr
     line["plans"] = PLANS_USED
     if args.save_plan and rank == 0:
         with open(args.save_plan, "w") as f:

@@ -17,7 +17,7 @@
 // stores it straight to global memory.  Each element crosses shared memory twice per
 // transform (one write, one read), against a load, a store and two stage round trips
 // in the general column kernels, and all index arithmetic is compile-time.  The
-// twiddles W256^m are one 256-entry table per block (sincospif of m / 128).
+// twiddles W256^(j k) are one 256-entry table per block (sincospif of j k / 128).
 //
 // Passes (one block per BXC-column tile; `axis` is 1 (y) or 2 (z)):
 //   k_col256<OP_FWD / OP_INV>: plain transform of component blockIdx.y
@@ -58,7 +58,7 @@ __device__ __forceinline__ void stage1(F2 (&v)[16], int j, int b, const F2* tw, 
   Dft<float, 16>::run(v, SG, nullptr, 0);
 #pragma unroll
   for (int k = 1; k < 16; ++k) {
-    F2 w = tw[j * k];
+    F2 w = tw[k * 16 + j];  // W256^(j k), row k of the table
     if (SG > 0) w.y = -w.y;
     v[k] = cmul<float>(v[k], w);
   }
@@ -113,10 +113,12 @@ __global__ void __launch_bounds__(16 * BXC, (OP == OP_FWD || OP == OP_INV) ? 64 
   const ColGeo<float> g = col_geo<float>(D, axis, BXC, blk);
   const int t = threadIdx.x;
   const int b = t % BXC, j = t / BXC;
+  // twiddle table by stage-1 output k (row) and thread j (column): entry 16 k + j holds
+  // W256^(j k), so the 16 threads of a row read 16 consecutive entries (no bank conflicts)
   for (int m = t; m < 256; m += 16 * BXC) {
     float s, c;
-    sincospif((float)m * (1.0f / 128.0f), &s, &c);
-    tw[m] = cmake<float>(c, -s);  // W256^m
+    sincospif((float)((m >> 4) * (m & 15)) * (1.0f / 128.0f), &s, &c);
+    tw[m] = cmake<float>(c, -s);
   }
   const bool ok = g.kx0 + b < D.nh;
   const long long est = g.est;

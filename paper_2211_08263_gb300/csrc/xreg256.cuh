@@ -39,7 +39,7 @@ __device__ __forceinline__ void stage1(F2 (&v)[16], int j, const F2* tw, F2* buf
   Dft<float, 16>::run(v, SG, nullptr, 0);
 #pragma unroll
   for (int k = 1; k < 16; ++k) {
-    F2 w = tw[j * k];
+    F2 w = tw[k * 16 + j];  // W256^(j k), row k of the table
     if (SG > 0) w.y = -w.y;
     v[k] = cmul<float>(v[k], w);
   }
@@ -84,11 +84,13 @@ __device__ __forceinline__ void store_half(const F2* nat, F2* da, F2* db, int j,
   }
 }
 
+// twiddle table by stage-1 output k (row) and thread j (column): entry 16 k + j holds
+// W256^(j k), so the 16 threads of a pair read 16 consecutive entries (no bank conflicts)
 __device__ __forceinline__ void init_tw(F2* tw) {
   for (int m = threadIdx.x; m < 256; m += blockDim.x) {
     float s, c;
-    sincospif((float)m * (1.0f / 128.0f), &s, &c);
-    tw[m] = cmake<float>(c, -s);  // W256^m
+    sincospif((float)((m >> 4) * (m & 15)) * (1.0f / 128.0f), &s, &c);
+    tw[m] = cmake<float>(c, -s);
   }
 }
 
@@ -346,31 +348,46 @@ __global__ void __launch_bounds__(256, 4) k_xfwd256_rupd(const Desc<float>* __re
   const float alpha = (float)sc->alpha;
   const long long V = D.V;
   const long long ga = (long long)P.ka * V + P.la * 256 + j, gb = (long long)P.kb * V + P.lb * 256 + j;
-  const float* pp = reinterpret_cast<const float*>(D.slot[SL_P]);
-  const float* qq = reinterpret_cast<const float*>(D.slot[SL_Q]);
-  float* rr = reinterpret_cast<float*>(D.slot[SL_R]);
-  float* dd32 = reinterpret_cast<float*>(D.slot[SL_D]);
+  // the four vectors are distinct arrays (restrict): each chunk's loads of all four are
+  // issued before its stores, kChunk points of both lines at a time
+  const float* __restrict__ pp = reinterpret_cast<const float*>(D.slot[SL_P]);
+  const float* __restrict__ qq = reinterpret_cast<const float*>(D.slot[SL_Q]);
+  float* __restrict__ rr = reinterpret_cast<float*>(D.slot[SL_R]);
+  float* __restrict__ dd32 = reinterpret_cast<float*>(D.slot[SL_D]);
+  constexpr int kChunk = 2;
   DotAcc<float> acc;
   F2 v[16];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int o = 16 * r;
-    float ra = 0.f, rb = 0.f;
-    if (P.va) {
-      const float pv = pp[ga + o], qv = qq[ga + o], rv = rr[ga + o], dv = dd32[ga + o];
-      dd32[ga + o] = dv + alpha * pv;
-      ra = rv - alpha * qv;
-      rr[ga + o] = ra;
-      acc.add_prod(ra, ra);
+  for (int r0 = 0; r0 < 16; r0 += kChunk) {
+    float pa[kChunk], qa[kChunk], ra_[kChunk], da[kChunk], pb[kChunk], qb[kChunk], rb_[kChunk], db[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int o = 16 * (r0 + u);
+      pa[u] = P.va ? pp[ga + o] : 0.f;
+      qa[u] = P.va ? qq[ga + o] : 0.f;
+      ra_[u] = P.va ? rr[ga + o] : 0.f;
+      da[u] = P.va ? dd32[ga + o] : 0.f;
+      pb[u] = P.vb ? pp[gb + o] : 0.f;
+      qb[u] = P.vb ? qq[gb + o] : 0.f;
+      rb_[u] = P.vb ? rr[gb + o] : 0.f;
+      db[u] = P.vb ? dd32[gb + o] : 0.f;
     }
-    if (P.vb) {
-      const float pv = pp[gb + o], qv = qq[gb + o], rv = rr[gb + o], dv = dd32[gb + o];
-      dd32[gb + o] = dv + alpha * pv;
-      rb = rv - alpha * qv;
-      rr[gb + o] = rb;
-      acc.add_prod(rb, rb);
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int o = 16 * (r0 + u);
+      const float ra = ra_[u] - alpha * qa[u], rb = rb_[u] - alpha * qb[u];
+      if (P.va) {
+        dd32[ga + o] = da[u] + alpha * pa[u];
+        rr[ga + o] = ra;
+        acc.add_prod(ra, ra);
+      }
+      if (P.vb) {
+        dd32[gb + o] = db[u] + alpha * pb[u];
+        rr[gb + o] = rb;
+        acc.add_prod(rb, rb);
+      }
+      v[r0 + u] = cmake<float>(ra, rb);
     }
-    v[r] = cmake<float>(ra, rb);
   }
   {
     const double s = block_sum(acc.value());  // contains barriers (the twiddles are ready)

@@ -359,18 +359,19 @@ def polycrystal(n_xyz, ngrains, seed):
 
 
 def config_c3(nsteps: int = 400, n: int = 256, ngrains: int = 500, seed: int = 3,
-              width_steps: float = 50.0, nz: Optional[int] = None) -> Problem:
+              width_steps: float = 50.0, nz: Optional[int] = None, ny: Optional[int] = None) -> Problem:
     """3-D nickel polycrystal: periodic Voronoi grains with uniformly random
     orientations of a cubic crystal (C11=168.4, C12=121.4, C44=75.4 GPa,
     rho=8960); Gaussian pulse (sigma = 50 dt, centre 4 sigma) on u_x of the
-    4-voxel x-face slab.  nz: a slab of n x n x nz voxels instead of the cube
-    (smaller cases with the same x and y transforms, e.g. for profiler captures)."""
-    shape = (n, n, nz if nz else n)
+    4-voxel x-face slab.  ny, nz: n x ny x nz voxels instead of the cube
+    (smaller cases with some of the cube's transforms, e.g. for profiler captures)."""
+    shape = (n, ny if ny else n, nz if nz else n)
     ids, Cv, rho = polycrystal(shape, ngrains, seed)
     dt = 2e-7
     w = width_steps * dt
     U = _U_series(nsteps, dt, lambda t: gaussian_pulse(t, 1e-6, w, 4 * w))
-    name = f"c3_polycrystal_{n}" if shape[2] == n else f"c3_polycrystal_{n}x{n}x{shape[2]}"
+    name = (f"c3_polycrystal_{n}" if shape[1] == n and shape[2] == n
+            else f"c3_polycrystal_{n}x{shape[1]}x{shape[2]}")
     return Problem(name, 3, shape, (1e-3,) * 3, dt, 0.25, 0.5, Cv, rho, ids,
                    slab_mask(3, shape, 4), U, tol=1e-10, extra={"seed": seed, "ngrains": ngrains})
 
