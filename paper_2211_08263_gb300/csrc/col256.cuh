@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(16 * BXC, (OP == OP_FWD || OP == OP_INV) ? 64 
       for (int c = 0; c < 3; ++c) stage2<-1, BXC>(U[c], j, b, S + c * kBuf);
       __syncthreads();
       const float iv = D.invV;
-      // round 1: gamma_11, gamma_12, gamma_13 (slots 0, 5, 4: every term with u1)
-      // round 2: gamma_22, gamma_33, gamma_23 (slots 1, 2, 3)
+      // round 0: gamma_11, gamma_12, gamma_13 (slots 0, 5, 4: every term with u1)
+      // round 1: gamma_22, gamma_33, gamma_23 (slots 1, 2, 3)
 #pragma unroll
       for (int round = 0; round < 2; ++round) {
 #pragma unroll
